@@ -1,0 +1,205 @@
+"""FP64 CPU oracle for the EpicFlow sparse-to-dense interpolator.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The library and its
+Python binding never import this package; it shares no code with them.
+
+The arithmetic lives in ``epic_oracle.c`` (plain C, FP64, one thread per
+call); this module compiles it with gcc on first use and wraps each step with
+numpy arrays.  Functions follow the paper's Algorithm 1 (LA form, Sec. 3.4):
+
+  geodesic(C, matches)            -> D, L      assignment map (Sec. 3.4, Eq. 3)
+  graph(C, D, L, matches)         -> em, en, ew    match graph G (Sec. 3.4)
+  knn(N, em, en, ew, K)           -> idx, dist, count   N_K by Dijkstra on G
+  fit(matches, idx, dist, count, a)  -> model, fallback, detratio  (Eq. 2)
+  writeout(L, matches, model)     -> flow      (Algorithm 1, steps 7-8)
+  nw(matches, idx, dist, count, a)   -> Nadaraya-Watson estimate (Eq. 1)
+  interp(C, matches, K, a)        -> dict with every intermediate
+
+Parity status of each function and the pins that check it are listed in the
+test files ``tests/test_oracle_*.py``; every function here is pinned.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "epic_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ORACLE_OK = 0
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call([
+        "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+        "-Wall", "-Wextra", "-Wno-unused-parameter", "-o", tmp, _SRC, "-lm",
+    ])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        Lg = ctypes.c_long
+        D = ctypes.c_double
+        lib.epic_oracle_geodesic.argtypes = [P, I, I, P, I, P, P]
+        lib.epic_oracle_geodesic.restype = I
+        lib.epic_oracle_graph.argtypes = [P, I, I, P, P, P, I, P, P, P, Lg]
+        lib.epic_oracle_graph.restype = Lg
+        lib.epic_oracle_knn.argtypes = [I, Lg, P, P, P, I, P, P, P]
+        lib.epic_oracle_knn.restype = I
+        lib.epic_oracle_fit.argtypes = [I, P, I, P, P, P, D, I, P, P, P]
+        lib.epic_oracle_fit.restype = I
+        lib.epic_oracle_writeout.argtypes = [I, I, P, I, P, P, P]
+        lib.epic_oracle_writeout.restype = I
+        lib.epic_oracle_nw.argtypes = [I, P, I, P, P, P, D, P]
+        lib.epic_oracle_nw.restype = I
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, what):
+    if rc != ORACLE_OK:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def geodesic(C, matches):
+    """D float64 [H, W], L int32 [H, W] (Sec. 3.4 assignment, Eq. 3)."""
+    lib = _load()
+    C = _f32(C)
+    matches = _f32(matches).reshape(-1, 4)
+    H, W = C.shape
+    D = np.empty((H, W), np.float64)
+    L = np.empty((H, W), np.int32)
+    _check(lib.epic_oracle_geodesic(_ptr(C), H, W, _ptr(matches),
+                                    matches.shape[0], _ptr(D), _ptr(L)),
+           "geodesic")
+    return D, L
+
+
+def graph(C, D, L, matches):
+    """Edges (em < en, ew) of G sorted by (em, en)."""
+    lib = _load()
+    C = _f32(C)
+    H, W = C.shape
+    D = np.ascontiguousarray(D, np.float64)
+    L = np.ascontiguousarray(L, np.int32)
+    matches = _f32(matches).reshape(-1, 4)
+    N = matches.shape[0]
+    cap = 4 * H * W + N + 1
+    em = np.empty(cap, np.int32)
+    en = np.empty(cap, np.int32)
+    ew = np.empty(cap, np.float64)
+    ne = lib.epic_oracle_graph(_ptr(C), H, W, _ptr(D), _ptr(L), _ptr(matches),
+                               N, _ptr(em), _ptr(en), _ptr(ew), cap)
+    if ne < 0:
+        raise RuntimeError(f"oracle graph failed with code {ne}")
+    return em[:ne].copy(), en[:ne].copy(), ew[:ne].copy()
+
+
+def knn(N, em, en, ew, K):
+    """idx int32 [N, K], dist float64 [N, K], count int32 [N]."""
+    lib = _load()
+    em = np.ascontiguousarray(em, np.int32)
+    en = np.ascontiguousarray(en, np.int32)
+    ew = np.ascontiguousarray(ew, np.float64)
+    idx = np.full((N, K), -1, np.int32)
+    dist = np.full((N, K), np.inf, np.float64)
+    count = np.zeros(N, np.int32)
+    _check(lib.epic_oracle_knn(N, len(em), _ptr(em), _ptr(en), _ptr(ew), K,
+                               _ptr(idx), _ptr(dist), _ptr(count)), "knn")
+    return idx, dist, count
+
+
+def fit(matches, idx, dist, count, a, weight_squared=True):
+    """model float64 [N, 6] = (c_u, c_v, b11, b12, b21, b22), fallback int32
+    [N], detratio float64 [N]."""
+    lib = _load()
+    matches = _f32(matches).reshape(-1, 4)
+    N = matches.shape[0]
+    idx = np.ascontiguousarray(idx, np.int32)
+    dist = np.ascontiguousarray(dist, np.float64)
+    count = np.ascontiguousarray(count, np.int32)
+    K = idx.shape[1]
+    model = np.empty((N, 6), np.float64)
+    fb = np.empty(N, np.int32)
+    dr = np.empty(N, np.float64)
+    _check(lib.epic_oracle_fit(N, _ptr(matches), K, _ptr(idx), _ptr(dist),
+                               _ptr(count), float(a), int(bool(weight_squared)),
+                               _ptr(model), _ptr(fb), _ptr(dr)), "fit")
+    return model, fb, dr
+
+
+def writeout(L, matches, model):
+    """flow float64 [H, W, 2] = c_L + B_L (p - p_L)."""
+    lib = _load()
+    L = np.ascontiguousarray(L, np.int32)
+    H, W = L.shape
+    matches = _f32(matches).reshape(-1, 4)
+    model = np.ascontiguousarray(model, np.float64)
+    flow = np.empty((H, W, 2), np.float64)
+    _check(lib.epic_oracle_writeout(H, W, _ptr(L), matches.shape[0],
+                                    _ptr(matches), _ptr(model), _ptr(flow)),
+           "writeout")
+    return flow
+
+
+def nw(matches, idx, dist, count, a):
+    """Nadaraya-Watson target estimate at every match, float64 [N, 2]."""
+    lib = _load()
+    matches = _f32(matches).reshape(-1, 4)
+    N = matches.shape[0]
+    idx = np.ascontiguousarray(idx, np.int32)
+    dist = np.ascontiguousarray(dist, np.float64)
+    count = np.ascontiguousarray(count, np.int32)
+    out = np.empty((N, 2), np.float64)
+    _check(lib.epic_oracle_nw(N, _ptr(matches), idx.shape[1], _ptr(idx),
+                              _ptr(dist), _ptr(count), float(a), _ptr(out)),
+           "nw")
+    return out
+
+
+def interp(C, matches, K, a, weight_squared=True):
+    """The whole interpolator (Algorithm 1, LA form) with every intermediate."""
+    matches = _f32(matches).reshape(-1, 4)
+    N = matches.shape[0]
+    K = int(min(K, N))
+    D, L = geodesic(C, matches)
+    em, en, ew = graph(C, D, L, matches)
+    idx, dist, count = knn(N, em, en, ew, K)
+    model, fb, dr = fit(matches, idx, dist, count, a, weight_squared)
+    flow = writeout(L, matches, model)
+    return dict(D=D, L=L, em=em, en=en, ew=ew, idx=idx, dist=dist,
+                count=count, model=model, fallback=fb, detratio=dr,
+                flow=flow, K=K)
