@@ -1,0 +1,178 @@
+/*
+ * epic_interp — EpicFlow's sparse-to-dense interpolator on one GB300 GPU.
+ *
+ * Given an edge-cost map C and a sparse match set M = {(p_m, p'_m)}, the
+ * library produces the dense flow field of Algorithm 1 (LA form) of Revaud et
+ * al., "EpicFlow: Edge-Preserving Interpolation of Correspondences for Optical
+ * Flow" (arXiv:1501.02565):
+ *   (a) the geodesic assignment map L(p) = argmin_m D_G(p, p_m) and the
+ *       distance D(p) = D_G(p, L(p))     (Sec. 3.4 "Geodesic Voronoi diagram";
+ *       D_G of Eq. 3 on the 8-connected pixel grid, step p->q costing
+ *       |p-q| (C(p)+C(q))/2);
+ *   (b) the match graph G joining matches whose cells touch, weighted by the
+ *       geodesic distance restricted to the two cells (Sec. 3.4);
+ *   (c) for every match, its K nearest matches on G (Algorithm 1, step 5, the
+ *       approximation D~ of Eq. 4) and a locally-weighted affine fit with
+ *       kernel exp(-a D) (Eq. 1-2, restricted to N_K as in Sec. 3.2);
+ *   (d) the dense write-out F(p) = A_{L(p)} p + t_{L(p)} (Algorithm 1, steps
+ *       7-8, LA form), returned as flow F(p) - p.
+ *
+ * Conventions shared by every entry point
+ *   - Images are row-major, x = column, y = row; pixel centres are integer.
+ *   - cost_map: float32 [H*W], finite and >= 0.
+ *   - matches:  float32 [N*4], rows (x, y, x', y').  The source pixel of match
+ *     m is (floor(x+0.5), floor(y+0.5)) and must lie inside the image; two
+ *     matches may share a source pixel (the smaller index owns it).
+ *   - flow_out: float32 [H*W*2], (u, v) = F(p) - p interleaved per pixel.
+ *   - Distances and weighted sums are float32; the per-match 3x3 normal
+ *     equations are solved in float64.
+ *   - Ties go to the smallest match index (labels, K-th neighbour).
+ *   - All device pointers are caller-owned and must stay valid until the
+ *     work enqueued on `stream` has finished.  The handle owns every scratch
+ *     buffer (a single device arena, grown on demand).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; entry points do not synchronise
+ *     unless stated.
+ *
+ * Errors: every function returns an epic_status_t.  Argument errors are
+ * reported immediately; errors found on the device (a match outside the
+ * image, a capacity or pass limit) are recorded in a device status word and
+ * returned by epic_interp_sync().  epic_interp_last_error() gives a message.
+ * A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef EPIC_INTERP_H
+#define EPIC_INTERP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EPIC_OK = 0,
+    EPIC_ERR_INVALID = 1,        /* bad argument or bad match coordinate */
+    EPIC_ERR_OOM = 2,            /* device or pinned-host allocation failed */
+    EPIC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    EPIC_ERR_NOT_CONVERGED = 4,  /* relaxation hit max_passes */
+    EPIC_ERR_TIMEOUT = 5,        /* a bounded grid-barrier wait expired */
+    EPIC_ERR_CAPACITY = 6        /* a fixed-capacity structure overflowed
+                                    (edge table, node degree, K-NN frontier) */
+} epic_status_t;
+
+typedef struct epic_interp epic_interp_t;
+
+typedef struct {
+    int max_H, max_W;     /* largest frame the arena is first sized for */
+    int max_N, max_K;     /* largest match count / neighbourhood size */
+    int max_pairs;        /* largest batch the arena is first sized for */
+    int max_passes;       /* cap on relaxation verification passes */
+    int weight_squared;   /* 1: Eq. 2 rows scaled by k, i.e. minimise
+                             sum k^2 |r|^2 (default); 0: minimise sum k |r|^2 */
+    float fallback_eps;   /* fit is degenerate when det M <= eps (tr M/3)^3
+                             or fewer than 3 neighbours; then the NW estimate
+                             of Eq. 1 at p_m is used as a constant flow */
+    int tile_w, tile_h;   /* relaxation tile (0 = chosen per frame size) */
+    int apron;            /* extra context around a tile in the first
+                             relaxation pass (-1 = chosen per frame size) */
+    int keep_intermediates; /* 1: keep K-NN lists for epic_interp_get_knn */
+    int max_degree;       /* match-graph adjacency row capacity (default 32) */
+} epic_config_t;
+
+/* One frame pair of a batch; pointers are device pointers. */
+typedef struct {
+    const float *cost_map;  /* [H*W] */
+    const float *matches;   /* [N*4] */
+    int H, W, N, K;
+    float a;
+    float *flow_out;        /* [H*W*2] */
+} epic_pair_desc_t;
+
+/* Fill *cfg with defaults (sizes for a 1024x436 frame, 5000 matches,
+ * K = 100, squared weights, eps = 1e-10, max_passes = 4096). */
+void epic_config_default(epic_config_t *cfg);
+
+/* Create a handle on CUDA device `device` and allocate its scratch arena for
+ * the sizes in *cfg (NULL = defaults).  Returns EPIC_ERR_OOM if the arena
+ * cannot be allocated, EPIC_ERR_CUDA for other runtime failures. */
+int epic_interp_create(epic_interp_t **h, int device, const epic_config_t *cfg);
+
+/* Interpolate one pair (Algorithm 1, LA form).  Device pointers; K is
+ * clamped to N; requires H, W, N >= 1, K >= 1, a > 0.  Enqueues the whole
+ * path on `stream` and returns without waiting. */
+int epic_interp_run(epic_interp_t *h, const float *cost_map,
+                    const float *matches, int H, int W, int N, int K, float a,
+                    float *flow_out, void *stream);
+
+/* Interpolate n independent pairs of any sizes in one batched launch
+ * sequence.  Same rules as epic_interp_run for every descriptor. */
+int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *pairs,
+                          int n, void *stream);
+
+/* Same as epic_interp_run but with HOST buffers: copies cost_map and matches
+ * to the device, runs, copies the flow back and waits for completion.
+ * Returns the device status (as epic_interp_sync would). */
+int epic_interp_run_host(epic_interp_t *h, const float *cost_map,
+                         const float *matches, int H, int W, int N, int K,
+                         float a, float *flow_out, void *stream);
+
+/* Wait for the last run's stream and return its device status (then clear
+ * it).  EPIC_OK when every stage completed within its limits. */
+int epic_interp_sync(epic_interp_t *h);
+
+/* Stage (a) of pair `pair` of the last run: labels L [H*W] int32 and
+ * distances D [H*W] float32 (device pointers; either may be NULL). */
+int epic_interp_get_labels(epic_interp_t *h, int pair, int *labels_out,
+                           float *dist_out, void *stream);
+
+/* Stage (b): number of undirected edges of G of pair `pair` of the last run
+ * (waits for the stream). */
+int epic_interp_get_edge_count(epic_interp_t *h, int pair, int *n_edges);
+
+/* Stage (b): the edges (m < n, weight) in unspecified order into device
+ * buffers of capacity `cap` each; *n_edges receives the count (waits). */
+int epic_interp_get_graph(epic_interp_t *h, int pair, int *em, int *en,
+                          float *ew, int cap, int *n_edges);
+
+/* Stage (c): K-NN lists of pair `pair` (requires keep_intermediates = 1):
+ * idx [N*K] int32 and dist [N*K] float32 in settle order, count [N] int32
+ * (device pointers). */
+int epic_interp_get_knn(epic_interp_t *h, int pair, int *idx, float *dist,
+                        int *count, void *stream);
+
+/* Stage (c): per-match models [N*8] float32 (c_u, c_v, b11, b12, b21, b22,
+ * x_m, y_m), flow(p) = c + B (p - p_m); and fallback flags [N] int32
+ * (1 = NW fallback).  Device pointers; either may be NULL. */
+int epic_interp_get_models(epic_interp_t *h, int pair, float *models,
+                           int *fallback, void *stream);
+
+/* Number of relaxation verification passes the last run needed for its
+ * whole batch (waits for the stream). */
+int epic_interp_get_passes(epic_interp_t *h, int *passes);
+
+/* Stage timing.  While enabled, every run records CUDA events on its
+ * stream between its six kernels (prepare, relaxation, edges, scatter,
+ * K-NN + fit, write-out).  Enabling (again) clears the accumulated times. */
+int epic_interp_enable_stage_timing(epic_interp_t *h, int enable);
+
+/* Sum over the runs since timing was enabled of each stage's elapsed time in
+ * milliseconds, into ms_out[0..n_stages) (n_stages <= 6); *n_runs receives
+ * the number of runs summed.  Waits for the last timed run. */
+int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages,
+                                int *n_runs);
+
+/* Number of kernel launches one run of `n` pairs enqueues. */
+int epic_interp_launches_per_run(epic_interp_t *h, int n);
+
+/* Message describing the last error on this handle (never NULL). */
+const char *epic_interp_last_error(epic_interp_t *h);
+
+/* Release the arena and the handle (waits for outstanding work). */
+void epic_interp_destroy(epic_interp_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPIC_INTERP_H */

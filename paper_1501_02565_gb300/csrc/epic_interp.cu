@@ -1,0 +1,649 @@
+// C ABI of the interpolator: handle, scratch arena, batch tables, launches.
+//
+// A run enqueues, on the caller's stream:
+//   table upload (pinned staging -> device), prepare, relaxation
+//   (cooperative, all passes in one launch), edge insertion, adjacency
+//   scatter, K-NN + fit, write-out.
+// The handle owns one device arena that is carved per run into every pair's
+// scratch (keys, seed bins, edge table, adjacency, models, optional K-NN
+// lists); it grows (after waiting for earlier work) when a batch needs more.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "epic_internal.cuh"
+
+using epic::BatchArgs;
+using epic::PairDev;
+using epic::RunState;
+using epic::pkey_t;
+
+struct epic_interp {
+    int device = 0;
+    int num_sms = 0;
+    int smem_optin = 0;
+    epic_config_t cfg{};
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    RunState *state = nullptr;      // device
+    RunState *state_host = nullptr; // pinned mirror for reads
+    int *scratch_count = nullptr;   // device int for getters
+    char *table_dev = nullptr;
+    char *table_host = nullptr;     // pinned staging
+    size_t table_cap = 0;
+    cudaEvent_t table_ev = nullptr;
+    bool table_ev_pending = false;
+    std::vector<PairDev> pairs;     // last run's descriptors
+    cudaStream_t last_stream = nullptr;
+    // device staging for epic_interp_run_host
+    float *io_C = nullptr, *io_M = nullptr, *io_F = nullptr;
+    size_t io_C_n = 0, io_M_n = 0, io_F_n = 0;
+    // stage timing: NSTAGE+1 events per timed run, reused across enablements
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    int timed_runs = 0;
+    std::string err;
+};
+
+static constexpr int NSTAGE = 6;
+
+namespace {
+
+const char *status_name(int s) {
+    switch (s) {
+    case EPIC_OK: return "ok";
+    case EPIC_ERR_INVALID: return "invalid input (argument or match outside the image)";
+    case EPIC_ERR_OOM: return "out of device memory";
+    case EPIC_ERR_CUDA: return "CUDA runtime error";
+    case EPIC_ERR_NOT_CONVERGED: return "relaxation did not converge within max_passes";
+    case EPIC_ERR_TIMEOUT: return "grid barrier wait timed out";
+    case EPIC_ERR_CAPACITY: return "capacity exceeded (edge table, node degree or K-NN frontier)";
+    default: return "unknown status";
+    }
+}
+
+int fail(epic_interp_t *h, int code, const std::string &msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(epic_interp_t *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(h, EPIC_ERR_OOM, m);
+    return fail(h, EPIC_ERR_CUDA, m);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int next_pow2(long long x) {
+    long long p = 1;
+    while (p < x) p <<= 1;
+    return (int)p;
+}
+
+// Tile shape for the relaxation of an H x W frame.
+void choose_tiles(const epic_config_t &c, int H, int W, int *tw, int *th, int *ap) {
+    int w = c.tile_w > 0 ? c.tile_w : 64;
+    int t = c.tile_h > 0 ? c.tile_h : 32;
+    int a = c.apron >= 0 ? c.apron : 4;
+    (void)H;
+    (void)W;
+    *tw = w;
+    *th = t;
+    *ap = a;
+}
+
+struct Layout {
+    size_t keys, tile_start, tile_fill, tile_seeds, hkeys, hw, deg, adj, models,
+        fallback, knn_idx, knn_dist, knn_count, info, end;
+};
+
+Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep) {
+    Layout L;
+    size_t o = align_up(base, 256);
+    const size_t npx = (size_t)P.H * P.W;
+    const size_t T = (size_t)P.tiles_x * P.tiles_y;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.keys = take(npx * sizeof(pkey_t));
+    L.tile_start = take((T + 1) * sizeof(int));
+    L.tile_fill = take(T * sizeof(int));
+    L.tile_seeds = take((size_t)P.N * sizeof(int));
+    L.hkeys = take((size_t)P.hash_cap * sizeof(pkey_t));
+    L.hw = take((size_t)P.hash_cap * sizeof(unsigned));
+    L.deg = take((size_t)P.N * sizeof(int));
+    L.adj = take((size_t)P.N * max_degree * sizeof(pkey_t));
+    L.models = take((size_t)P.N * 2 * sizeof(float4));
+    L.fallback = take((size_t)P.N * sizeof(int));
+    L.knn_idx = keep ? take((size_t)P.N * P.K * sizeof(int)) : 0;
+    L.knn_dist = keep ? take((size_t)P.N * P.K * sizeof(float)) : 0;
+    L.knn_count = keep ? take((size_t)P.N * sizeof(int)) : 0;
+    L.info = take(4 * sizeof(int));
+    L.end = o;
+    return L;
+}
+
+PairDev make_pair_desc(const epic_config_t &c, const epic_pair_desc_t &d) {
+    PairDev P{};
+    P.C = d.cost_map;
+    P.matches = reinterpret_cast<const float4 *>(d.matches);
+    P.flow = d.flow_out;
+    P.H = d.H;
+    P.W = d.W;
+    P.N = d.N;
+    P.K = std::min(d.K, d.N);
+    P.a = d.a;
+    choose_tiles(c, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron);
+    P.tiles_x = (d.W + P.tile_w - 1) / P.tile_w;
+    P.tiles_y = (d.H + P.tile_h - 1) / P.tile_h;
+    P.hash_cap = std::max(1024, next_pow2(8LL * d.N));
+    P.flow_vec_ok = ((uintptr_t)d.flow_out % 16) == 0;
+    return P;
+}
+
+int validate(epic_interp_t *h, const epic_pair_desc_t &d, int i) {
+    char buf[256];
+    if (!d.cost_map || !d.matches || !d.flow_out) {
+        snprintf(buf, sizeof buf, "pair %d: null pointer", i);
+        return fail(h, EPIC_ERR_INVALID, buf);
+    }
+    if (d.H < 1 || d.W < 1 || d.N < 1 || d.K < 1 || !(d.a > 0.f) || !std::isfinite(d.a)) {
+        snprintf(buf, sizeof buf,
+                 "pair %d: need H, W, N, K >= 1 and finite a > 0 (H=%d W=%d N=%d K=%d a=%g)",
+                 i, d.H, d.W, d.N, d.K, (double)d.a);
+        return fail(h, EPIC_ERR_INVALID, buf);
+    }
+    if ((long long)d.H * d.W > (1LL << 30) || d.N > (1 << 26)) {
+        snprintf(buf, sizeof buf, "pair %d: frame or match count too large", i);
+        return fail(h, EPIC_ERR_INVALID, buf);
+    }
+    if (((uintptr_t)d.matches % 16) != 0) {
+        snprintf(buf, sizeof buf, "pair %d: matches must be 16-byte aligned", i);
+        return fail(h, EPIC_ERR_INVALID, buf);
+    }
+    return EPIC_OK;
+}
+
+int wait_last(epic_interp_t *h) {
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return EPIC_OK;
+}
+
+int ensure_arena(epic_interp_t *h, size_t need) {
+    if (need <= h->arena_bytes) return EPIC_OK;
+    int rc = wait_last(h);
+    if (rc) return rc;
+    if (h->arena) cudaFree(h->arena);
+    h->arena = nullptr;
+    h->arena_bytes = 0;
+    size_t sz = align_up(need + need / 4, 1 << 20);
+    cudaError_t e = cudaMalloc(&h->arena, sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(h, e, "arena cudaMalloc");
+    }
+    h->arena_bytes = sz;
+    return EPIC_OK;
+}
+
+int ensure_table(epic_interp_t *h, size_t need) {
+    if (need <= h->table_cap) return EPIC_OK;
+    int rc = wait_last(h);
+    if (rc) return rc;
+    if (h->table_dev) cudaFree(h->table_dev);
+    if (h->table_host) cudaFreeHost(h->table_host);
+    h->table_dev = nullptr;
+    h->table_host = nullptr;
+    h->table_cap = 0;
+    h->table_ev_pending = false;
+    size_t sz = align_up(need * 2, 4096);
+    cudaError_t e = cudaMalloc(&h->table_dev, sz);
+    if (e != cudaSuccess) return cuda_fail(h, e, "table cudaMalloc");
+    e = cudaMallocHost(&h->table_host, sz);
+    if (e != cudaSuccess) return cuda_fail(h, e, "table cudaMallocHost");
+    h->table_cap = sz;
+    return EPIC_OK;
+}
+
+int read_state(epic_interp_t *h) {
+    cudaError_t e = cudaMemcpyAsync(h->state_host, h->state, sizeof(RunState),
+                                    cudaMemcpyDeviceToHost, h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state read");
+    e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return EPIC_OK;
+}
+
+int check_pair(epic_interp_t *h, int pair) {
+    if (!h) return EPIC_ERR_INVALID;
+    if (pair < 0 || pair >= (int)h->pairs.size())
+        return fail(h, EPIC_ERR_INVALID, "pair index out of range of the last run");
+    return EPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void epic_config_default(epic_config_t *c) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->max_H = 436;
+    c->max_W = 1024;
+    c->max_N = 5000;
+    c->max_K = 100;
+    c->max_pairs = 1;
+    c->max_passes = 4096;
+    c->weight_squared = 1;
+    c->fallback_eps = 1e-10f;
+    c->tile_w = 0;
+    c->tile_h = 0;
+    c->apron = -1;
+    c->keep_intermediates = 0;
+    c->max_degree = 32;
+}
+
+int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg) {
+    if (!out) return EPIC_ERR_INVALID;
+    *out = nullptr;
+    epic_interp_t *h = new epic_interp_t();
+    if (cfg) h->cfg = *cfg; else epic_config_default(&h->cfg);
+    epic_config_t &c = h->cfg;
+    if (c.max_passes <= 0) c.max_passes = 4096;
+    if (c.max_degree <= 0) c.max_degree = 32;
+    if (!(c.fallback_eps > 0.f)) c.fallback_eps = 1e-10f;
+    if (c.max_pairs <= 0) c.max_pairs = 1;
+    if ((c.tile_w > 0 && c.tile_w < 8) || (c.tile_h > 0 && c.tile_h < 8) ||
+        c.tile_w > 256 || c.tile_h > 256) {
+        int r = fail(h, EPIC_ERR_INVALID, "tile sides must be in [8, 256]");
+        delete h;
+        return r;
+    }
+    h->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete h; return EPIC_ERR_CUDA; }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { delete h; return EPIC_ERR_CUDA; }
+    h->num_sms = prop.multiProcessorCount;
+    h->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    e = cudaMalloc(&h->state, sizeof(RunState) + 64);
+    if (e != cudaSuccess) { delete h; return EPIC_ERR_OOM; }
+    h->scratch_count = reinterpret_cast<int *>(reinterpret_cast<char *>(h->state) + sizeof(RunState) + 32);
+    cudaMemset(h->state, 0, sizeof(RunState) + 64);
+    e = cudaMallocHost(&h->state_host, sizeof(RunState));
+    if (e != cudaSuccess) { epic_interp_destroy(h); return EPIC_ERR_OOM; }
+    e = cudaEventCreateWithFlags(&h->table_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { epic_interp_destroy(h); return EPIC_ERR_CUDA; }
+    // size the arena for the configured maxima
+    epic_pair_desc_t d{};
+    d.cost_map = reinterpret_cast<const float *>(16);
+    d.matches = reinterpret_cast<const float *>(16);
+    d.flow_out = reinterpret_cast<float *>(16);
+    d.H = std::max(1, c.max_H);
+    d.W = std::max(1, c.max_W);
+    d.N = std::max(1, c.max_N);
+    d.K = std::max(1, c.max_K);
+    d.a = 1.f;
+    PairDev P = make_pair_desc(c, d);
+    size_t per = layout_pair(0, P, c.max_degree, c.keep_intermediates != 0).end;
+    int rc = ensure_arena(h, per * (size_t)c.max_pairs);
+    if (rc) { epic_interp_destroy(h); return rc; }
+    rc = ensure_table(h, 4096);
+    if (rc) { epic_interp_destroy(h); return rc; }
+    *out = h;
+    return EPIC_OK;
+}
+
+int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n,
+                          void *stream_) {
+    if (!h) return EPIC_ERR_INVALID;
+    if (!descs || n < 1) return fail(h, EPIC_ERR_INVALID, "empty batch");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const epic_config_t &c = h->cfg;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(h, descs[i], i);
+        if (rc) return rc;
+    }
+    // descriptors and arena layout
+    std::vector<PairDev> P(n);
+    std::vector<Layout> L(n);
+    size_t off = 0;
+    int max_tw = 8, max_th = 8, max_ap = 0, max_K = 1;
+    for (int i = 0; i < n; ++i) {
+        P[i] = make_pair_desc(c, descs[i]);
+        if (P[i].apron + 1 > std::min(P[i].tile_w, P[i].tile_h))
+            return fail(h, EPIC_ERR_INVALID, "apron must be smaller than the tile sides");
+        L[i] = layout_pair(off, P[i], c.max_degree, c.keep_intermediates != 0);
+        off = L[i].end;
+        max_tw = std::max(max_tw, P[i].tile_w);
+        max_th = std::max(max_th, P[i].tile_h);
+        max_ap = std::max(max_ap, P[i].apron);
+        max_K = std::max(max_K, P[i].K);
+    }
+    int rc = ensure_arena(h, off);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        char *b = h->arena;
+        P[i].keys = reinterpret_cast<pkey_t *>(b + L[i].keys);
+        P[i].tile_start = reinterpret_cast<int *>(b + L[i].tile_start);
+        P[i].tile_fill = reinterpret_cast<int *>(b + L[i].tile_fill);
+        P[i].tile_seeds = reinterpret_cast<int *>(b + L[i].tile_seeds);
+        P[i].hkeys = reinterpret_cast<pkey_t *>(b + L[i].hkeys);
+        P[i].hw = reinterpret_cast<unsigned *>(b + L[i].hw);
+        P[i].deg = reinterpret_cast<int *>(b + L[i].deg);
+        P[i].adj = reinterpret_cast<pkey_t *>(b + L[i].adj);
+        P[i].models = reinterpret_cast<float4 *>(b + L[i].models);
+        P[i].fallback = reinterpret_cast<int *>(b + L[i].fallback);
+        if (c.keep_intermediates) {
+            P[i].knn_idx = reinterpret_cast<int *>(b + L[i].knn_idx);
+            P[i].knn_dist = reinterpret_cast<float *>(b + L[i].knn_dist);
+            P[i].knn_count = reinterpret_cast<int *>(b + L[i].knn_count);
+        }
+        P[i].info = reinterpret_cast<int *>(b + L[i].info);
+    }
+    // batch table: PairDev[n] then 5 prefix arrays of n+1 ints
+    std::vector<int> tile_base(n + 1), match_base(n + 1), chunk_base(n + 1),
+        hash_base(n + 1), clear_base(n + 1);
+    long long tt = 0, tm = 0, tc = 0, th = 0, tcl = 0;
+    for (int i = 0; i < n; ++i) {
+        tile_base[i] = (int)tt;
+        match_base[i] = (int)tm;
+        chunk_base[i] = (int)tc;
+        hash_base[i] = (int)th;
+        clear_base[i] = (int)tcl;
+        tt += (long long)P[i].tiles_x * P[i].tiles_y;
+        tm += P[i].N;
+        tc += ((long long)P[i].H * P[i].W + epic::WRITEOUT_CHUNK - 1) / epic::WRITEOUT_CHUNK;
+        th += P[i].hash_cap;
+        tcl += ((long long)P[i].hash_cap + (long long)P[i].N * c.max_degree +
+                epic::CLEAR_CHUNK - 1) / epic::CLEAR_CHUNK;
+    }
+    if (tt > INT32_MAX || tm > INT32_MAX || tc > INT32_MAX || th > INT32_MAX || tcl > INT32_MAX)
+        return fail(h, EPIC_ERR_INVALID, "batch too large");
+    tile_base[n] = (int)tt;
+    match_base[n] = (int)tm;
+    chunk_base[n] = (int)tc;
+    hash_base[n] = (int)th;
+    clear_base[n] = (int)tcl;
+    const size_t pd_bytes = align_up(sizeof(PairDev) * n, 256);
+    const size_t pre_bytes = sizeof(int) * (n + 1);
+    const size_t table_bytes = pd_bytes + 5 * align_up(pre_bytes, 256);
+    rc = ensure_table(h, table_bytes);
+    if (rc) return rc;
+    if (h->table_ev_pending) {
+        e = cudaEventSynchronize(h->table_ev);  // staging reuse
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    }
+    char *hs = h->table_host;
+    memcpy(hs, P.data(), sizeof(PairDev) * n);
+    const int *pres[5] = {tile_base.data(), match_base.data(), chunk_base.data(),
+                          hash_base.data(), clear_base.data()};
+    for (int k = 0; k < 5; ++k)
+        memcpy(hs + pd_bytes + k * align_up(pre_bytes, 256), pres[k], pre_bytes);
+    e = cudaMemcpyAsync(h->table_dev, hs, table_bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "table upload");
+    e = cudaEventRecord(h->table_ev, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    h->table_ev_pending = true;
+
+    BatchArgs a{};
+    a.pairs = reinterpret_cast<const PairDev *>(h->table_dev);
+    auto pre_dev = [&](int k) {
+        return reinterpret_cast<const int *>(h->table_dev + pd_bytes + k * align_up(pre_bytes, 256));
+    };
+    a.npairs = n;
+    a.tile_base = pre_dev(0);
+    a.match_base = pre_dev(1);
+    a.chunk_base = pre_dev(2);
+    a.hash_base = pre_dev(3);
+    a.clear_base = pre_dev(4);
+    a.total_tiles = (int)tt;
+    a.total_matches = (int)tm;
+    a.total_chunks = (int)tc;
+    a.total_hash = (int)th;
+    a.total_clear = (int)tcl;
+    a.max_degree = c.max_degree;
+    epic::knn_table_sizes(max_K, &a.knn_hs, &a.knn_fs);
+    a.knn_kmax = max_K;
+    a.max_passes = c.max_passes;
+    a.weight_squared = c.weight_squared ? 1 : 0;
+    a.fallback_eps = c.fallback_eps;
+    a.state = h->state;
+    if (epic::knn_warps_per_cta(max_K, h->smem_optin) < 1)
+        return fail(h, EPIC_ERR_INVALID, "K too large for the per-warp search tables");
+    if (epic::dt_smem_bytes(max_tw, max_th, max_ap) > (size_t)h->smem_optin)
+        return fail(h, EPIC_ERR_INVALID, "relaxation tile does not fit in shared memory");
+
+    epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
+    cudaEvent_t *ev = nullptr;
+    if (h->timing) {
+        size_t need = (size_t)(h->timed_runs + 1) * (NSTAGE + 1);
+        while (h->tev.size() < need) {
+            cudaEvent_t x;
+            if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+            h->tev.push_back(x);
+        }
+        ev = &h->tev[(size_t)h->timed_runs * (NSTAGE + 1)];
+        h->timed_runs++;
+    }
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], stream);
+    };
+    mark(0);
+    if ((e = epic::launch_prepare(a, lc)) != cudaSuccess) return cuda_fail(h, e, "prepare launch");
+    mark(1);
+    int grid = 0;
+    if ((e = epic::launch_dt(a, lc, max_tw, max_th, max_ap, &grid)) != cudaSuccess)
+        return cuda_fail(h, e, "relaxation launch");
+    mark(2);
+    if ((e = epic::launch_edges(a, lc)) != cudaSuccess) return cuda_fail(h, e, "edge launch");
+    mark(3);
+    if ((e = epic::launch_scatter(a, lc)) != cudaSuccess) return cuda_fail(h, e, "scatter launch");
+    mark(4);
+    if ((e = epic::launch_knn_fit(a, lc, max_K)) != cudaSuccess) return cuda_fail(h, e, "knn launch");
+    mark(5);
+    if ((e = epic::launch_writeout(a, lc)) != cudaSuccess) return cuda_fail(h, e, "write-out launch");
+    mark(6);
+    h->pairs = P;
+    h->last_stream = stream;
+    return EPIC_OK;
+}
+
+int epic_interp_run(epic_interp_t *h, const float *cost_map, const float *matches,
+                    int H, int W, int N, int K, float a, float *flow_out, void *stream) {
+    epic_pair_desc_t d{cost_map, matches, H, W, N, K, a, flow_out};
+    return epic_interp_run_batch(h, &d, 1, stream);
+}
+
+int epic_interp_run_host(epic_interp_t *h, const float *cost_map, const float *matches,
+                         int H, int W, int N, int K, float a, float *flow_out,
+                         void *stream_) {
+    if (!h) return EPIC_ERR_INVALID;
+    if (!cost_map || !matches || !flow_out || H < 1 || W < 1 || N < 1)
+        return fail(h, EPIC_ERR_INVALID, "run_host: bad arguments");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t nC = (size_t)H * W, nM = (size_t)N * 4, nF = (size_t)H * W * 2;
+    auto grow = [&](float **p, size_t *cap, size_t need) -> int {
+        if (need <= *cap) return EPIC_OK;
+        int rc = wait_last(h);
+        if (rc) return rc;
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+        cudaError_t ee = cudaMalloc(p, need * sizeof(float));
+        if (ee != cudaSuccess) return cuda_fail(h, ee, "run_host cudaMalloc");
+        *cap = need;
+        return EPIC_OK;
+    };
+    int rc = grow(&h->io_C, &h->io_C_n, nC);
+    if (!rc) rc = grow(&h->io_M, &h->io_M_n, nM);
+    if (!rc) rc = grow(&h->io_F, &h->io_F_n, nF);
+    if (rc) return rc;
+    if ((e = cudaMemcpyAsync(h->io_C, cost_map, nC * 4, cudaMemcpyHostToDevice, stream)) ||
+        (e = cudaMemcpyAsync(h->io_M, matches, nM * 4, cudaMemcpyHostToDevice, stream)))
+        return cuda_fail(h, e, "run_host upload");
+    rc = epic_interp_run(h, h->io_C, h->io_M, H, W, N, K, a, h->io_F, stream_);
+    if (rc) return rc;
+    if ((e = cudaMemcpyAsync(flow_out, h->io_F, nF * 4, cudaMemcpyDeviceToHost, stream)))
+        return cuda_fail(h, e, "run_host download");
+    return epic_interp_sync(h);
+}
+
+int epic_interp_sync(epic_interp_t *h) {
+    if (!h) return EPIC_ERR_INVALID;
+    int rc = read_state(h);
+    if (rc) return rc;
+    int s = h->state_host->status;
+    if (s != 0) {
+        cudaMemsetAsync(&h->state->status, 0, sizeof(int), h->last_stream);
+        cudaStreamSynchronize(h->last_stream);
+        return fail(h, s, status_name(s));
+    }
+    return EPIC_OK;
+}
+
+int epic_interp_get_labels(epic_interp_t *h, int pair, int *labels, float *dist,
+                           void *stream) {
+    int rc = check_pair(h, pair);
+    if (rc) return rc;
+    cudaError_t e = epic::launch_split_keys(&h->pairs[pair], labels, dist,
+                                            reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : cuda_fail(h, e, "get_labels");
+}
+
+int epic_interp_get_edge_count(epic_interp_t *h, int pair, int *n_edges) {
+    int rc = check_pair(h, pair);
+    if (rc) return rc;
+    if (!n_edges) return fail(h, EPIC_ERR_INVALID, "null output");
+    rc = wait_last(h);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(n_edges, h->pairs[pair].info, sizeof(int), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? EPIC_OK : cuda_fail(h, e, "get_edge_count");
+}
+
+int epic_interp_get_graph(epic_interp_t *h, int pair, int *em, int *en, float *ew,
+                          int cap, int *n_edges) {
+    int rc = check_pair(h, pair);
+    if (rc) return rc;
+    if (!em || !en || !ew || !n_edges || cap < 0) return fail(h, EPIC_ERR_INVALID, "null output");
+    cudaError_t e = epic::launch_collect_edges(&h->pairs[pair], em, en, ew, cap,
+                                               h->scratch_count, h->last_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->state_host, h->scratch_count, sizeof(int),
+                            cudaMemcpyDeviceToHost, h->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_graph");
+    *n_edges = *reinterpret_cast<int *>(h->state_host);
+    return *n_edges <= cap ? EPIC_OK : fail(h, EPIC_ERR_CAPACITY, "edge buffer too small");
+}
+
+int epic_interp_get_knn(epic_interp_t *h, int pair, int *idx, float *dist, int *count,
+                        void *stream_) {
+    int rc = check_pair(h, pair);
+    if (rc) return rc;
+    const PairDev &P = h->pairs[pair];
+    if (!P.knn_idx) return fail(h, EPIC_ERR_INVALID, "K-NN lists need keep_intermediates = 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    size_t nk = (size_t)P.N * P.K;
+    cudaError_t e = cudaSuccess;
+    if (idx) e = cudaMemcpyAsync(idx, P.knn_idx, nk * 4, cudaMemcpyDeviceToDevice, s);
+    if (!e && dist) e = cudaMemcpyAsync(dist, P.knn_dist, nk * 4, cudaMemcpyDeviceToDevice, s);
+    if (!e && count) e = cudaMemcpyAsync(count, P.knn_count, (size_t)P.N * 4, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? EPIC_OK : cuda_fail(h, e, "get_knn");
+}
+
+int epic_interp_get_models(epic_interp_t *h, int pair, float *models, int *fallback,
+                           void *stream_) {
+    int rc = check_pair(h, pair);
+    if (rc) return rc;
+    const PairDev &P = h->pairs[pair];
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e = cudaSuccess;
+    if (models)
+        e = cudaMemcpyAsync(models, P.models, (size_t)P.N * 32, cudaMemcpyDeviceToDevice, s);
+    if (!e && fallback)
+        e = cudaMemcpyAsync(fallback, P.fallback, (size_t)P.N * 4, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? EPIC_OK : cuda_fail(h, e, "get_models");
+}
+
+int epic_interp_get_passes(epic_interp_t *h, int *passes) {
+    if (!h || !passes) return EPIC_ERR_INVALID;
+    int rc = read_state(h);
+    if (rc) return rc;
+    *passes = h->state_host->passes;
+    return EPIC_OK;
+}
+
+int epic_interp_enable_stage_timing(epic_interp_t *h, int enable) {
+    if (!h) return EPIC_ERR_INVALID;
+    if (h->timed_runs > 0) {
+        int rc = wait_last(h);
+        if (rc) return rc;
+    }
+    h->timing = enable != 0;
+    h->timed_runs = 0;
+    return EPIC_OK;
+}
+
+int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages, int *n_runs) {
+    if (!h || !ms_out || n_stages < 0 || n_stages > NSTAGE) return EPIC_ERR_INVALID;
+    for (int s = 0; s < n_stages; ++s) ms_out[s] = 0.f;
+    if (n_runs) *n_runs = h->timed_runs;
+    if (h->timed_runs == 0) return EPIC_OK;
+    cudaError_t e = cudaEventSynchronize(h->tev[(size_t)h->timed_runs * (NSTAGE + 1) - 1]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    for (int r = 0; r < h->timed_runs; ++r) {
+        const cudaEvent_t *ev = &h->tev[(size_t)r * (NSTAGE + 1)];
+        for (int s = 0; s < n_stages; ++s) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventElapsedTime");
+            ms_out[s] += ms;
+        }
+    }
+    return EPIC_OK;
+}
+
+int epic_interp_launches_per_run(epic_interp_t *h, int n) {
+    (void)h;
+    (void)n;
+    return 6;  // prepare, relaxation, edges, scatter, K-NN + fit, write-out
+}
+
+const char *epic_interp_last_error(epic_interp_t *h) {
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+void epic_interp_destroy(epic_interp_t *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->arena) cudaFree(h->arena);
+    if (h->state) cudaFree(h->state);
+    if (h->state_host) cudaFreeHost(h->state_host);
+    if (h->table_dev) cudaFree(h->table_dev);
+    if (h->table_host) cudaFreeHost(h->table_host);
+    if (h->table_ev) cudaEventDestroy(h->table_ev);
+    if (h->io_C) cudaFree(h->io_C);
+    if (h->io_M) cudaFree(h->io_M);
+    if (h->io_F) cudaFree(h->io_F);
+    for (cudaEvent_t x : h->tev) cudaEventDestroy(x);
+    delete h;
+}
+
+}  // extern "C"

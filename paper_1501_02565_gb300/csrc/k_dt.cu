@@ -1,0 +1,402 @@
+// Stage (a): geodesic assignment map L and distance D (Sec. 3.4 "Geodesic
+// Voronoi diagram"; D_G of Eq. 3 on the 8-connected grid).
+//
+// Each pixel's packed key (D, L) is the minimum over all matches m and all
+// grid paths from p_m of (path cost, m), where the path cost is accumulated
+// in float32 from the seed outwards, one step at a time:
+//     D <- D + |p-q| (C(p)+C(q))/2.
+// Any order of such relaxation steps that ends when no step improves any key
+// reaches the same keys bit for bit, because every step is monotone in its
+// input and each key is the exact float32 fold along some path.  The kernel
+// exploits that freedom:
+//
+//   phase 1  every tile is solved alone in shared memory on its region
+//            (tile + apron + 1-px ring), with the seeds of that region, and
+//            writes its tile's keys;
+//   phase 2  repeated passes: a tile whose border can be improved from the
+//            current keys of the pixels just outside it reloads
+//            (tile + ring) and re-solves; the passes end when no tile is
+//            dirty, i.e. no step improves any key anywhere.
+//
+// The in-tile solver runs directional sweeps (down, up, right, left), each
+// relaxing a pixel from its three neighbours on the side the sweep comes
+// from; a warp sweeps 32 adjacent lines in lock step.  One kernel launch
+// holds all passes: it is a cooperative launch (all CTAs co-resident) and the
+// passes are separated by a grid barrier whose wait is bounded in time.
+#include "epic_internal.cuh"
+
+namespace epic {
+
+namespace {
+
+constexpr unsigned long long BARRIER_LIMIT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-free generation barrier over all CTAs of a cooperative launch.  The
+// wait gives up after BARRIER_LIMIT_NS (or as soon as another CTA has given
+// up) and reports EPIC_ERR_TIMEOUT instead of spinning forever.
+__device__ bool grid_sync(RunState *st) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        GridBarrier *b = &st->barrier;
+        int ok = 1;
+        unsigned g = ld_acquire(&b->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&b->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            b->count = 0;
+            __threadfence();
+            st_release(&b->gen, g + 1);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (ld_acquire(&b->gen) == g) {
+                if (get_status(st) == EPIC_ERR_TIMEOUT) { ok = 0; break; }
+                if (global_ns() - t0 > BARRIER_LIMIT_NS) {
+                    set_status(st, EPIC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Shared-memory solve region.  Region cell (c, r) is image pixel
+// (x0 + c, y0 + r); row pitch P is odd so that a warp reading one column
+// (32 rows) of 8-byte keys touches every bank pair once.
+struct Region {
+    int x0, y0, RW, RH, P;
+    int bx0, bx1, by0, by1;  // updatable cells: interior and inside the image
+};
+
+__device__ __forceinline__ int odd_pitch(int w) { return w | 1; }
+
+__device__ __forceinline__ Region make_region(const PairDev &P, int gx0,
+                                              int gy0, int tw, int th,
+                                              int apron) {
+    Region g;
+    g.x0 = gx0 - apron - 1;
+    g.y0 = gy0 - apron - 1;
+    g.RW = tw + 2 * apron + 2;
+    g.RH = th + 2 * apron + 2;
+    g.P = odd_pitch(g.RW);
+    g.bx0 = max(1, -g.x0);
+    g.bx1 = min(g.RW - 2, P.W - 1 - g.x0);
+    g.by0 = max(1, -g.y0);
+    g.by1 = min(g.RH - 2, P.H - 1 - g.y0);
+    return g;
+}
+
+// Best of the current key and the three candidates reached from the
+// neighbours at offsets ax (axis step) and d1, d2 (diagonal steps).
+__device__ __forceinline__ int relax3(pkey_t *K, const float *h, int idx,
+                                      int ax, int d1, int d2) {
+    const pkey_t kp = K[idx];
+    const float hp = h[idx];
+    pkey_t best = kp;
+    pkey_t kq = K[idx + ax];
+    pkey_t c = make_key(__fadd_rn(key_dist(kq), step_axis(hp, h[idx + ax])),
+                       key_label(kq));
+    best = c < best ? c : best;
+    kq = K[idx + d1];
+    c = make_key(__fadd_rn(key_dist(kq), step_diag(hp, h[idx + d1])), key_label(kq));
+    best = c < best ? c : best;
+    kq = K[idx + d2];
+    c = make_key(__fadd_rn(key_dist(kq), step_diag(hp, h[idx + d2])), key_label(kq));
+    best = c < best ? c : best;
+    if (best < kp) {
+        K[idx] = best;
+        return 1;
+    }
+    return 0;
+}
+
+// Sweep the region to its fixed point.  Returns 1 if any key changed.
+__device__ int local_solve(pkey_t *K, const float *h, const Region &g,
+                           RunState *st) {
+    const int ncols = g.bx1 - g.bx0 + 1, nrows = g.by1 - g.by0 + 1;
+    if (ncols <= 0 || nrows <= 0) return 0;
+    const int T = blockDim.x, tid = threadIdx.x, P = g.P;
+    // vertical sweeps: a thread owns a column segment
+    const int nsegV = max(1, T / ncols);
+    const int segV = (nrows + nsegV - 1) / nsegV;
+    const bool vu = tid < ncols * nsegV;
+    const int vx = g.bx0 + tid % ncols;
+    const int vy0 = g.by0 + (tid / ncols) * segV;
+    const int vy1 = min(g.by1, vy0 + segV - 1);
+    // horizontal sweeps: a thread owns a row segment
+    const int nsegH = max(1, T / nrows);
+    const int segH = (ncols + nsegH - 1) / nsegH;
+    const bool hu = tid < nrows * nsegH;
+    const int hy = g.by0 + tid % nrows;
+    const int hx0 = g.bx0 + (tid / nrows) * segH;
+    const int hx1 = min(g.bx1, hx0 + segH - 1);
+
+    const int cap = g.RW * g.RH;  // Bellman-Ford bound on useful iterations
+    int any = 0;
+    for (int it = 0; it < cap; ++it) {
+        int ch = 0;
+        for (int s = 0; s < segV; ++s) {  // down: from the row above
+            int y = vy0 + s;
+            if (vu && y <= vy1) ch |= relax3(K, h, y * P + vx, -P, -P - 1, -P + 1);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int s = 0; s < segV; ++s) {  // up: from the row below
+            int y = vy1 - s;
+            if (vu && y >= vy0) ch |= relax3(K, h, y * P + vx, P, P - 1, P + 1);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int s = 0; s < segH; ++s) {  // right: from the column on the left
+            int x = hx0 + s;
+            if (hu && x <= hx1) ch |= relax3(K, h, hy * P + x, -1, -1 - P, -1 + P);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int s = 0; s < segH; ++s) {  // left: from the column on the right
+            int x = hx1 - s;
+            if (hu && x >= hx0) ch |= relax3(K, h, hy * P + x, 1, 1 - P, 1 + P);
+            __syncwarp();
+        }
+        if (!__syncthreads_or(ch)) return any;
+        any = 1;
+    }
+    if (tid == 0) set_status(st, EPIC_ERR_NOT_CONVERGED);
+    return any;
+}
+
+__device__ __forceinline__ void load_costs(const PairDev &P, const Region &g,
+                                           float *h) {
+    for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
+        int r = i / g.RW, c = i - r * g.RW;
+        int gx = g.x0 + c, gy = g.y0 + r;
+        bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+        h[r * g.P + c] = in ? __fmul_rn(0.5f, __ldg(P.C + (size_t)gy * P.W + gx)) : 0.f;
+    }
+}
+
+// Phase 1: solve tile (tx, ty) on its region from its seeds alone.
+__device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
+                            float *h, RunState *st) {
+    const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
+    const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, P.apron);
+    load_costs(P, g, h);
+    for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
+        int r = i / g.RW, c = i - r * g.RW;
+        K[r * g.P + c] = KEY_INF;
+    }
+    __syncthreads();
+    // seeds: the region lies within the 3x3 tiles around (tx, ty)
+    const int ctx0 = max(0, g.x0) / P.tile_w;
+    const int ctx1 = min(P.W - 1, g.x0 + g.RW - 1) / P.tile_w;
+    const int cty0 = max(0, g.y0) / P.tile_h;
+    const int cty1 = min(P.H - 1, g.y0 + g.RH - 1) / P.tile_h;
+    for (int cy = cty0; cy <= cty1; ++cy) {
+        for (int cx = ctx0; cx <= ctx1; ++cx) {
+            int t = cy * P.tiles_x + cx;
+            int s0 = P.tile_start[t], s1 = P.tile_start[t + 1];
+            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+                int m = P.tile_seeds[s];
+                float4 mt = __ldg(P.matches + m);
+                int px = (int)floorf(mt.x + 0.5f) - g.x0;
+                int py = (int)floorf(mt.y + 0.5f) - g.y0;
+                if (px >= 0 && px < g.RW && py >= 0 && py < g.RH)
+                    atomicMin(&K[py * g.P + px], make_key(0.f, (unsigned)m));
+            }
+        }
+    }
+    __syncthreads();
+    local_solve(K, h, g, st);
+    // write the tile's own pixels
+    const int off = P.apron + 1;
+    for (int i = threadIdx.x; i < P.tile_w * P.tile_h; i += blockDim.x) {
+        int ly = i / P.tile_w, lx = i - ly * P.tile_w;
+        int gx = gx0 + lx, gy = gy0 + ly;
+        if (gx < P.W && gy < P.H)
+            P.keys[(size_t)gy * P.W + gx] = K[(ly + off) * g.P + lx + off];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ pkey_t ld_key(const pkey_t *p) { return __ldcg(p); }
+
+// Can a border pixel of the tile be improved by a step from a pixel outside
+// it?  Keys of other tiles may be rewritten during the launch, so they are
+// read through L2 (ld.global.cg), never from a stale L1 line.
+__device__ bool border_dirty(const PairDev &P, int tx, int ty) {
+    const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
+    const int gx1 = min(P.W - 1, gx0 + P.tile_w - 1);
+    const int gy1 = min(P.H - 1, gy0 + P.tile_h - 1);
+    const int w = gx1 - gx0 + 1, hgt = gy1 - gy0 + 1;
+    const int n_top = w, n_bot = hgt > 1 ? w : 0;
+    const int n_side = max(0, hgt - 2);
+    const int n_left = n_side, n_right = w > 1 ? n_side : 0;
+    const int total = n_top + n_bot + n_left + n_right;
+    int dirty = 0;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        int x, y;
+        if (i < n_top) { x = gx0 + i; y = gy0; }
+        else if (i < n_top + n_bot) { x = gx0 + (i - n_top); y = gy1; }
+        else if (i < n_top + n_bot + n_left) { x = gx0; y = gy0 + 1 + (i - n_top - n_bot); }
+        else { x = gx1; y = gy0 + 1 + (i - n_top - n_bot - n_left); }
+        const size_t p = (size_t)y * P.W + x;
+        const pkey_t kp = ld_key(P.keys + p);
+        const float hp = __fmul_rn(0.5f, __ldg(P.C + p));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int dx = (k == 0 || k == 4 || k == 6) ? 1 : (k == 1 || k == 5 || k == 7) ? -1 : 0;
+            const int dy = (k == 2 || k == 4 || k == 5) ? 1 : (k == 3 || k == 6 || k == 7) ? -1 : 0;
+            const int qx = x + dx, qy = y + dy;
+            if (qx < 0 || qx >= P.W || qy < 0 || qy >= P.H) continue;
+            if (qx >= gx0 && qx <= gx1 && qy >= gy0 && qy <= gy1) continue;
+            const size_t q = (size_t)qy * P.W + qx;
+            const pkey_t kq = ld_key(P.keys + q);
+            const float hq = __fmul_rn(0.5f, __ldg(P.C + q));
+            const float st = (dx != 0 && dy != 0) ? step_diag(hp, hq) : step_axis(hp, hq);
+            const pkey_t c = make_key(__fadd_rn(key_dist(kq), st), key_label(kq));
+            dirty |= c < kp;
+        }
+    }
+    return __syncthreads_or(dirty) != 0;
+}
+
+// Phase 2 re-solve of tile (tx, ty) from the current keys (tile + ring).
+__device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
+                            float *h, RunState *st) {
+    const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
+    const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, 0);
+    load_costs(P, g, h);
+    for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
+        int r = i / g.RW, c = i - r * g.RW;
+        int gx = g.x0 + c, gy = g.y0 + r;
+        bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+        K[r * g.P + c] = in ? ld_key(P.keys + (size_t)gy * P.W + gx) : KEY_INF;
+    }
+    __syncthreads();
+    if (local_solve(K, h, g, st)) {
+        for (int i = threadIdx.x; i < P.tile_w * P.tile_h; i += blockDim.x) {
+            int ly = i / P.tile_w, lx = i - ly * P.tile_w;
+            int gx = gx0 + lx, gy = gy0 + ly;
+            if (gx < P.W && gy < P.H)
+                P.keys[(size_t)gy * P.W + gx] = K[(ly + 1) * g.P + lx + 1];
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(DT_THREADS) dt_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    RunState *st = a.state;
+    if (get_status(st) != 0) return;  // same decision in every CTA
+    __shared__ int s_pair, s_local;
+
+    // phase 1
+    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            s_pair = find_pair(a.tile_base, a.npairs, t);
+            s_local = t - a.tile_base[s_pair];
+        }
+        __syncthreads();
+        const PairDev &P = a.pairs[s_pair];
+        const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, P.apron);
+        pkey_t *K = reinterpret_cast<pkey_t *>(smem);
+        float *h = reinterpret_cast<float *>(smem + sizeof(pkey_t) * g.RH * g.P);
+        solve_fresh(P, s_local % P.tiles_x, s_local / P.tiles_x, K, h, st);
+    }
+    if (!grid_sync(st)) return;
+
+    // phase 2
+    for (int pass = 0;; ++pass) {
+        if (pass >= a.max_passes) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                set_status(st, EPIC_ERR_NOT_CONVERGED);
+                st->passes = pass;
+            }
+            return;
+        }
+        unsigned *cnt = &st->changed[pass % 3];
+        for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+            if (threadIdx.x == 0) {
+                s_pair = find_pair(a.tile_base, a.npairs, t);
+                s_local = t - a.tile_base[s_pair];
+            }
+            __syncthreads();
+            const PairDev &P = a.pairs[s_pair];
+            const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
+            if (border_dirty(P, tx, ty)) {
+                const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
+                pkey_t *K = reinterpret_cast<pkey_t *>(smem);
+                float *h = reinterpret_cast<float *>(smem + sizeof(pkey_t) * g.RH * g.P);
+                solve_again(P, tx, ty, K, h, st);
+                if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+            }
+        }
+        if (!grid_sync(st)) return;
+        const unsigned dirty = ld_acquire(cnt);
+        // the counter of pass-1 (== pass+2 mod 3) was read by every CTA
+        // before this barrier; clear it for pass+2
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->changed[(pass + 2) % 3] = 0;
+        if (dirty == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->passes = pass + 1;
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+size_t dt_smem_bytes(int tile_w, int tile_h, int apron) {
+    int RW = tile_w + 2 * apron + 2, RH = tile_h + 2 * apron + 2;
+    int P = RW | 1;
+    return (size_t)RH * P * (sizeof(pkey_t) + sizeof(float));
+}
+
+cudaError_t launch_dt(const BatchArgs &a, const LaunchCfg &lc, int max_tile_w,
+                      int max_tile_h, int max_apron, int *grid_used) {
+    size_t smem = dt_smem_bytes(max_tile_w, max_tile_h, max_apron);
+    cudaError_t e = cudaFuncSetAttribute(
+        dt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dt_kernel,
+                                                      DT_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = per_sm * lc.num_sms;
+    if (grid > a.total_tiles) grid = a.total_tiles;
+    if (grid < 1) grid = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(DT_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = lc.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (grid_used) *grid_used = grid;
+    return cudaLaunchKernelEx(&cfg, dt_kernel, a);
+}
+
+}  // namespace epic

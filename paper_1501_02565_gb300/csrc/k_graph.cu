@@ -1,0 +1,223 @@
+// Stage (b): the match graph G (Sec. 3.4 "Approximated geodesic distance").
+//
+// Matches m and n are joined when their geodesic Voronoi cells touch, i.e.
+// some 8-adjacent pixels p, q have L(p) = m, L(q) = n.  The edge weight is
+// the geodesic distance from p_m to p_n restricted to the two cells, which
+// is the minimum over touching pairs (p, q) of D(p) + step(p, q) + D(q): the
+// shortest path from a seed to a pixel of its own cell stays in that cell,
+// and a path inside the union crosses from one cell to the other at some
+// touching pair.  Each candidate is evaluated in float32 as
+// (D(p_small) + step) + D(p_large), p_small being the pixel whose label is
+// the smaller index, so every kernel forms the same value for the same pair.
+//
+// edges_kernel   every pixel looks at its four forward neighbours (right,
+//                down-left, down, down-right: each unordered pixel pair once)
+//                and inserts (min label, max label, weight) into an
+//                open-addressing table with atomicMin on the weight; lanes of
+//                a warp holding the same label pair are merged first.  A
+//                match whose source pixel is owned by a smaller index (a
+//                duplicate) is joined to the owner at distance D = 0.
+// scatter_kernel every occupied slot appends (w, n) to row m and (w, m) to
+//                row n of a fixed-capacity adjacency array.
+#include "epic_internal.cuh"
+
+namespace epic {
+
+namespace {
+
+__device__ __forceinline__ unsigned hash_slot(pkey_t k, int cap) {
+    unsigned long long h = k * 0x9E3779B97F4A7C15ull;
+    return (unsigned)(h >> 32) & (unsigned)(cap - 1);
+}
+
+__device__ __forceinline__ void table_insert(const PairDev &P, pkey_t k,
+                                             unsigned wbits, RunState *st) {
+    unsigned s = hash_slot(k, P.hash_cap);
+    for (int probe = 0; probe < P.hash_cap; ++probe) {
+        pkey_t prev = atomicCAS(P.hkeys + s, EMPTY64, k);
+        if (prev == EMPTY64 || prev == k) {
+            atomicMin(P.hw + s, wbits);  // weights are >= 0: bit order = value order
+            return;
+        }
+        s = (s + 1) & (unsigned)(P.hash_cap - 1);
+    }
+    set_status(st, EPIC_ERR_CAPACITY);
+}
+
+// Insert one candidate per active lane, merging equal label pairs in the warp.
+__device__ __forceinline__ void warp_insert(const PairDev &P, bool have,
+                                            pkey_t k, unsigned wbits,
+                                            RunState *st) {
+    const unsigned lane = threadIdx.x & 31;
+    unsigned pend = __ballot_sync(0xffffffffu, have);
+    while (pend) {
+        const int leader = __ffs(pend) - 1;
+        const pkey_t lk = __shfl_sync(0xffffffffu, k, leader);
+        const bool mine = have && k == lk;
+        const unsigned grp = __ballot_sync(0xffffffffu, mine);
+        const unsigned wmin = __reduce_min_sync(0xffffffffu, mine ? wbits : 0xFFFFFFFFu);
+        if (lane == (unsigned)leader) table_insert(P, lk, wmin, st);
+        pend &= ~grp;
+        if (mine) have = false;
+    }
+}
+
+__global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(BatchArgs a) {
+    RunState *st = a.state;
+    if (get_status(st) != 0) return;
+    __shared__ int s_pair, s_local;
+    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            s_pair = find_pair(a.tile_base, a.npairs, t);
+            s_local = t - a.tile_base[s_pair];
+        }
+        __syncthreads();
+        const PairDev &P = a.pairs[s_pair];
+        const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
+        const int npx = P.tile_w * P.tile_h;
+        const int W = P.W, H = P.H;
+        for (int i0 = 0; i0 < npx; i0 += blockDim.x) {  // warp-uniform trip count
+            const int i = i0 + threadIdx.x;
+            const int ly = i / P.tile_w, lx = i - ly * P.tile_w;
+            const int x = tx * P.tile_w + lx, y = ty * P.tile_h + ly;
+            const bool act = i < npx && x < W && y < H;
+            pkey_t kp = 0;
+            float hp = 0.f;
+            if (act) {
+                kp = __ldg(P.keys + (size_t)y * W + x);
+                hp = __fmul_rn(0.5f, __ldg(P.C + (size_t)y * W + x));
+            }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const int dx = d == 0 ? 1 : d == 1 ? -1 : d == 2 ? 0 : 1;
+                const int dy = d == 0 ? 0 : 1;
+                const int qx = x + dx, qy = y + dy;
+                bool have = act && qx >= 0 && qx < W && qy < H;
+                pkey_t k = 0;
+                unsigned wb = 0;
+                if (have) {
+                    const size_t q = (size_t)qy * W + qx;
+                    const pkey_t kq = __ldg(P.keys + q);
+                    const unsigned lp = key_label(kp), lq = key_label(kq);
+                    have = lp != lq;
+                    if (have && (lp >= (unsigned)P.N || lq >= (unsigned)P.N)) {
+                        // an unreached pixel: the cost map was not finite and >= 0
+                        set_status(st, EPIC_ERR_INVALID);
+                        have = false;
+                    }
+                    if (have) {
+                        const float hq = __fmul_rn(0.5f, __ldg(P.C + q));
+                        const float stp = (dx != 0 && dy != 0) ? step_diag(hp, hq)
+                                                               : step_axis(hp, hq);
+                        const bool ps = lp < lq;
+                        const float dsm = ps ? key_dist(kp) : key_dist(kq);
+                        const float dlg = ps ? key_dist(kq) : key_dist(kp);
+                        const float w = __fadd_rn(__fadd_rn(dsm, stp), dlg);
+                        k = ps ? (((pkey_t)lp << 32) | lq) : (((pkey_t)lq << 32) | lp);
+                        wb = __float_as_uint(w);
+                    }
+                }
+                warp_insert(P, have, k, wb, st);
+            }
+        }
+        __syncthreads();
+    }
+    // duplicate source pixels: join an ownerless match to its pixel's owner
+    for (int gm = blockIdx.x * blockDim.x + threadIdx.x; gm < a.total_matches;
+         gm += gridDim.x * blockDim.x) {
+        const int p = find_pair(a.match_base, a.npairs, gm);
+        const PairDev &P = a.pairs[p];
+        const int m = gm - a.match_base[p];
+        const float4 mt = __ldg(P.matches + m);
+        const int x = (int)floorf(mt.x + 0.5f), y = (int)floorf(mt.y + 0.5f);
+        const pkey_t kp = __ldg(P.keys + (size_t)y * P.W + x);
+        const unsigned l = key_label(kp);
+        if (l != (unsigned)m && l < (unsigned)P.N) {
+            const unsigned lo = min(l, (unsigned)m), hi = max(l, (unsigned)m);
+            table_insert(P, ((pkey_t)lo << 32) | hi, __float_as_uint(key_dist(kp)), st);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(BatchArgs a) {
+    RunState *st = a.state;
+    if (get_status(st) != 0) return;
+    const int md = a.max_degree;
+    for (int gs = blockIdx.x * blockDim.x + threadIdx.x; gs < a.total_hash;
+         gs += gridDim.x * blockDim.x) {
+        const int p = find_pair(a.hash_base, a.npairs, gs);
+        const PairDev &P = a.pairs[p];
+        const int s = gs - a.hash_base[p];
+        const pkey_t k = P.hkeys[s];
+        if (k == EMPTY64) continue;
+        const unsigned m = (unsigned)(k >> 32), n = (unsigned)k;
+        if (m >= (unsigned)P.N || n >= (unsigned)P.N) {
+            set_status(st, EPIC_ERR_INVALID);
+            continue;
+        }
+        const pkey_t wb = (pkey_t)P.hw[s] << 32;
+        const int pm = atomicAdd(P.deg + m, 1);
+        const int pn = atomicAdd(P.deg + n, 1);
+        if (pm < md) P.adj[(size_t)m * md + pm] = wb | n;
+        if (pn < md) P.adj[(size_t)n * md + pn] = wb | m;
+        if (pm >= md || pn >= md) set_status(st, EPIC_ERR_CAPACITY);
+        atomicAdd(P.info + 0, 1);
+        atomicMax(P.info + 1, max(pm, pn) + 1);
+    }
+}
+
+__global__ void split_kernel(const pkey_t *keys, int P, int *labels, float *dist) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        pkey_t k = keys[i];
+        if (labels) labels[i] = (int)key_label(k);
+        if (dist) dist[i] = key_dist(k);
+    }
+}
+
+__global__ void collect_kernel(const pkey_t *hkeys, const unsigned *hw, int cap_slots,
+                               int *em, int *en, float *ew, int cap, int *count) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < cap_slots;
+         s += gridDim.x * blockDim.x) {
+        pkey_t k = hkeys[s];
+        if (k == EMPTY64) continue;
+        int i = atomicAdd(count, 1);
+        if (i < cap) {
+            em[i] = (int)(k >> 32);
+            en[i] = (int)(unsigned)k;
+            ew[i] = __uint_as_float(hw[s]);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_edges(const BatchArgs &a, const LaunchCfg &lc) {
+    edges_kernel<<<lc.num_sms * 8, EDGE_THREADS, 0, lc.stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const BatchArgs &a, const LaunchCfg &lc) {
+    scatter_kernel<<<lc.num_sms * 4, 256, 0, lc.stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_keys(const PairDev *P, int *labels, float *dist,
+                              cudaStream_t stream) {
+    int n = P->H * P->W;
+    split_kernel<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, stream>>>(
+        P->keys, n, labels, dist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collect_edges(const PairDev *P, int *em, int *en, float *ew,
+                                 int cap, int *count, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    int blocks = (P->hash_cap + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    collect_kernel<<<blocks, 256, 0, stream>>>(P->hkeys, P->hw, P->hash_cap, em, en,
+                                               ew, cap, count);
+    return cudaGetLastError();
+}
+
+}  // namespace epic

@@ -1,0 +1,296 @@
+"""ctypes binding of ``libepic_interp.so`` (declared in include/epic_interp.h).
+
+Argument marshalling only: every step of the interpolator runs in the CUDA
+library.  Function names mirror the C ABI; ``EpicInterp`` is a small
+convenience wrapper that takes torch CUDA tensors for device buffers and the
+current torch stream.  Importing raises if the library has not been built
+(``python -m paper_1501_02565_gb300.build``); there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+EPIC_OK = 0
+EPIC_ERR_INVALID = 1
+EPIC_ERR_OOM = 2
+EPIC_ERR_CUDA = 3
+EPIC_ERR_NOT_CONVERGED = 4
+EPIC_ERR_TIMEOUT = 5
+EPIC_ERR_CAPACITY = 6
+
+STATUS_NAMES = {
+    0: "EPIC_OK", 1: "EPIC_ERR_INVALID", 2: "EPIC_ERR_OOM", 3: "EPIC_ERR_CUDA",
+    4: "EPIC_ERR_NOT_CONVERGED", 5: "EPIC_ERR_TIMEOUT", 6: "EPIC_ERR_CAPACITY",
+}
+
+# Every symbol include/epic_interp.h declares.
+EXPORTED = (
+    "epic_config_default", "epic_interp_create", "epic_interp_run",
+    "epic_interp_run_batch", "epic_interp_run_host", "epic_interp_sync",
+    "epic_interp_get_labels", "epic_interp_get_edge_count",
+    "epic_interp_get_graph", "epic_interp_get_knn", "epic_interp_get_models",
+    "epic_interp_get_passes", "epic_interp_enable_stage_timing",
+    "epic_interp_get_stage_times", "epic_interp_launches_per_run",
+    "epic_interp_last_error", "epic_interp_destroy",
+)
+
+
+class epic_config_t(ctypes.Structure):
+    _fields_ = [
+        ("max_H", ctypes.c_int), ("max_W", ctypes.c_int),
+        ("max_N", ctypes.c_int), ("max_K", ctypes.c_int),
+        ("max_pairs", ctypes.c_int), ("max_passes", ctypes.c_int),
+        ("weight_squared", ctypes.c_int), ("fallback_eps", ctypes.c_float),
+        ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
+        ("apron", ctypes.c_int), ("keep_intermediates", ctypes.c_int),
+        ("max_degree", ctypes.c_int),
+    ]
+
+
+class epic_pair_desc_t(ctypes.Structure):
+    _fields_ = [
+        ("cost_map", ctypes.c_void_p), ("matches", ctypes.c_void_p),
+        ("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int),
+        ("K", ctypes.c_int), ("a", ctypes.c_float),
+        ("flow_out", ctypes.c_void_p),
+    ]
+
+
+class EpicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the shared library (raises OSError if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise OSError(
+            f"{path} not found: build it with `python -m paper_1501_02565_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    pi = ctypes.POINTER(ctypes.c_int)
+    lib.epic_config_default.argtypes = [ctypes.POINTER(epic_config_t)]
+    lib.epic_config_default.restype = None
+    lib.epic_interp_create.argtypes = [pp, I, ctypes.POINTER(epic_config_t)]
+    lib.epic_interp_create.restype = I
+    lib.epic_interp_run.argtypes = [P, P, P, I, I, I, I, F, P, P]
+    lib.epic_interp_run.restype = I
+    lib.epic_interp_run_batch.argtypes = [P, ctypes.POINTER(epic_pair_desc_t), I, P]
+    lib.epic_interp_run_batch.restype = I
+    lib.epic_interp_run_host.argtypes = [P, P, P, I, I, I, I, F, P, P]
+    lib.epic_interp_run_host.restype = I
+    lib.epic_interp_sync.argtypes = [P]
+    lib.epic_interp_sync.restype = I
+    lib.epic_interp_get_labels.argtypes = [P, I, P, P, P]
+    lib.epic_interp_get_labels.restype = I
+    lib.epic_interp_get_edge_count.argtypes = [P, I, pi]
+    lib.epic_interp_get_edge_count.restype = I
+    lib.epic_interp_get_graph.argtypes = [P, I, P, P, P, I, pi]
+    lib.epic_interp_get_graph.restype = I
+    lib.epic_interp_get_knn.argtypes = [P, I, P, P, P, P]
+    lib.epic_interp_get_knn.restype = I
+    lib.epic_interp_get_models.argtypes = [P, I, P, P, P]
+    lib.epic_interp_get_models.restype = I
+    lib.epic_interp_get_passes.argtypes = [P, pi]
+    lib.epic_interp_get_passes.restype = I
+    lib.epic_interp_enable_stage_timing.argtypes = [P, I]
+    lib.epic_interp_enable_stage_timing.restype = I
+    lib.epic_interp_get_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), I, pi]
+    lib.epic_interp_get_stage_times.restype = I
+    lib.epic_interp_launches_per_run.argtypes = [P, I]
+    lib.epic_interp_launches_per_run.restype = I
+    lib.epic_interp_last_error.argtypes = [P]
+    lib.epic_interp_last_error.restype = ctypes.c_char_p
+    lib.epic_interp_destroy.argtypes = [P]
+    lib.epic_interp_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def epic_config_default() -> epic_config_t:
+    cfg = epic_config_t()
+    load().epic_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class EpicInterp:
+    """Handle over one device; buffers are torch CUDA tensors (float32)."""
+
+    def __init__(self, device: int = 0, **cfg_overrides):
+        self.lib = load()
+        cfg = epic_config_default()
+        for k, v in cfg_overrides.items():
+            if not hasattr(cfg, k):
+                raise TypeError(f"unknown config field {k}")
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.epic_interp_create(ctypes.byref(h), device, ctypes.byref(cfg))
+        if rc != EPIC_OK:
+            raise EpicError(rc, "epic_interp_create failed")
+        self.h = h
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != EPIC_OK:
+            msg = self.lib.epic_interp_last_error(self.h)
+            raise EpicError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.epic_interp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points --------------------------------------------------------
+    def run(self, C, matches, K, a, flow=None, stream=None):
+        """Enqueue one pair; C [H, W], matches [N, 4] float32 CUDA tensors."""
+        import torch
+        H, W = C.shape
+        N = matches.shape[0]
+        if flow is None:
+            flow = torch.empty((H, W, 2), dtype=torch.float32, device=C.device)
+        rc = self.lib.epic_interp_run(self.h, _ptr(C), _ptr(matches), H, W, N,
+                                      int(K), float(a), _ptr(flow),
+                                      _stream_handle(stream))
+        self._check(rc, "epic_interp_run")
+        return flow
+
+    def run_batch(self, items, stream=None):
+        """items: list of (C, matches, K, a, flow) with CUDA tensors."""
+        n = len(items)
+        arr = (epic_pair_desc_t * n)()
+        for i, (C, M, K, a, F) in enumerate(items):
+            arr[i] = epic_pair_desc_t(C.data_ptr(), M.data_ptr(), C.shape[0],
+                                      C.shape[1], M.shape[0], int(K), float(a),
+                                      F.data_ptr())
+        rc = self.lib.epic_interp_run_batch(self.h, arr, n, _stream_handle(stream))
+        self._check(rc, "epic_interp_run_batch")
+
+    def run_host(self, C, matches, K, a, flow, stream=None):
+        """Host buffers (contiguous float32 numpy arrays or CPU tensors)."""
+        def addr(x):
+            return ctypes.c_void_p(x.ctypes.data if hasattr(x, "ctypes") else x.data_ptr())
+        H, W = C.shape
+        rc = self.lib.epic_interp_run_host(self.h, addr(C), addr(matches), H, W,
+                                           matches.shape[0], int(K), float(a),
+                                           addr(flow), _stream_handle(stream))
+        self._check(rc, "epic_interp_run_host")
+
+    def sync(self):
+        self._check(self.lib.epic_interp_sync(self.h), "device status")
+
+    def sync_status(self) -> int:
+        return self.lib.epic_interp_sync(self.h)
+
+    def get_labels(self, pair=0, H=None, W=None, stream=None):
+        import torch
+        P = self._last_shape(pair, H, W)
+        L = torch.empty(P, dtype=torch.int32, device=f"cuda:{self.device}")
+        D = torch.empty(P, dtype=torch.float32, device=f"cuda:{self.device}")
+        self._check(self.lib.epic_interp_get_labels(self.h, pair, _ptr(L), _ptr(D),
+                                                    _stream_handle(stream)),
+                    "get_labels")
+        return L, D
+
+    def _last_shape(self, pair, H, W):
+        if H is None or W is None:
+            raise ValueError("pass H and W of the pair")
+        return (H, W)
+
+    def get_edge_count(self, pair=0):
+        n = ctypes.c_int()
+        self._check(self.lib.epic_interp_get_edge_count(self.h, pair, ctypes.byref(n)),
+                    "get_edge_count")
+        return n.value
+
+    def get_graph(self, pair=0):
+        import torch
+        n = self.get_edge_count(pair)
+        dev = f"cuda:{self.device}"
+        em = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        en = torch.empty_like(em)
+        ew = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+        cnt = ctypes.c_int()
+        self._check(self.lib.epic_interp_get_graph(self.h, pair, _ptr(em), _ptr(en),
+                                                   _ptr(ew), max(n, 1),
+                                                   ctypes.byref(cnt)), "get_graph")
+        k = cnt.value
+        return em[:k], en[:k], ew[:k]
+
+    def get_knn(self, pair, N, K, stream=None):
+        import torch
+        dev = f"cuda:{self.device}"
+        K = min(K, N)
+        idx = torch.empty((N, K), dtype=torch.int32, device=dev)
+        dist = torch.empty((N, K), dtype=torch.float32, device=dev)
+        cnt = torch.empty(N, dtype=torch.int32, device=dev)
+        self._check(self.lib.epic_interp_get_knn(self.h, pair, _ptr(idx), _ptr(dist),
+                                                 _ptr(cnt), _stream_handle(stream)),
+                    "get_knn")
+        return idx, dist, cnt
+
+    def get_models(self, pair, N, stream=None):
+        import torch
+        dev = f"cuda:{self.device}"
+        models = torch.empty((N, 8), dtype=torch.float32, device=dev)
+        fb = torch.empty(N, dtype=torch.int32, device=dev)
+        self._check(self.lib.epic_interp_get_models(self.h, pair, _ptr(models), _ptr(fb),
+                                                    _stream_handle(stream)),
+                    "get_models")
+        return models, fb
+
+    def get_passes(self):
+        n = ctypes.c_int()
+        self._check(self.lib.epic_interp_get_passes(self.h, ctypes.byref(n)), "get_passes")
+        return n.value
+
+    STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout")
+
+    def enable_stage_timing(self, enable=True):
+        self._check(self.lib.epic_interp_enable_stage_timing(self.h, int(enable)),
+                    "enable_stage_timing")
+
+    def stage_times(self):
+        """{stage: summed ms} over the timed runs, and the run count."""
+        arr = (ctypes.c_float * 6)()
+        n = ctypes.c_int()
+        self._check(self.lib.epic_interp_get_stage_times(self.h, arr, 6, ctypes.byref(n)),
+                    "get_stage_times")
+        return dict(zip(self.STAGES, list(arr))), n.value
+
+    def launches_per_run(self, n=1):
+        return self.lib.epic_interp_launches_per_run(self.h, n)

@@ -1,0 +1,258 @@
+"""Parity checks of the CUDA path against the FP64 oracle.
+
+Tolerances (stated once, used by every GPU test):
+  * labels   L_gpu(p) == L_ref(p), or the two matches are a near tie:
+             D_ref(p, p_{L_gpu}) - D_ref(p) <= 1e-5 * D_ref(p)
+  * distance |D_gpu - D_ref| <= 1e-4 * D_ref + 1e-6
+  * graph    same edge set as the oracle's graph built on the GPU labels;
+             |w_gpu - w_ref| <= 1e-4 * w_ref + 1e-6
+  * K-NN     on the GPU graph: same ordered neighbour lists except where the
+             K-th and (K+1)-th keys are within 1e-5 relative; distances
+             within 1e-5 * d + 1e-6
+  * flow     |flow_gpu - flow_ref| <= 1e-3 px per component, except for
+             pixels whose match has a K-th / (K+1)-th near tie in the oracle's
+             lists, whose fit is within 10x of the degeneracy threshold, or
+             whose fit is ill-conditioned: its exact (FP64) flow moves by more
+             than half the tolerance when its neighbour distances are
+             perturbed by 1e-6 relative, the size of the float32 error the
+             GPU's distances carry (measured and asserted below).  Counts of
+             every exclusion are reported.
+
+Labels at near ties are not unique (float32 and float64 break a tie
+differently), and the match graph of Sec. 3.4 is a function of the labels: a
+tie pixel decides whether two cells touch.  So stages (b)-(d) are compared
+with the oracle run on the GPU's own labelling, after checking that this
+labelling is valid (every differing label is a near tie).  The difference to
+the oracle's end-to-end result is reported too, as the method's sensitivity
+to tie breaking.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.sparse.csgraph import dijkstra
+
+import oracle
+from helpers import grid_graph, seed_pixels
+
+D_RTOL, D_ATOL = 1e-4, 1e-6
+TIE_RTOL = 1e-5
+W_RTOL, W_ATOL = 1e-4, 1e-6
+KNN_TIE = 1e-5
+FLOW_TOL = 1e-3
+DET_EPS = 1e-10
+SENS_REL = 1e-6          # relative perturbation of neighbour distances
+SENS_ABS = 2e-7          # absolute slack for near-zero distances
+SENS_PX = FLOW_TOL / 2   # a fit moving more than this is ill-conditioned
+
+
+def run_gpu(pair_or_arrays, K=None, a=None, eng=None, **cfg):
+    """Run one pair through the C ABI and fetch every intermediate."""
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    if hasattr(pair_or_arrays, "C"):
+        C, M = pair_or_arrays.C, pair_or_arrays.matches
+        K = pair_or_arrays.K if K is None else K
+        a = pair_or_arrays.a if a is None else a
+    else:
+        C, M = pair_or_arrays
+    H, W = C.shape
+    N = M.shape[0]
+    own = eng is None
+    if own:
+        cfg.setdefault("keep_intermediates", 1)
+        eng = EpicInterp(0, **cfg)
+    Ct = torch.from_numpy(np.ascontiguousarray(C, np.float32)).cuda()
+    Mt = torch.from_numpy(np.ascontiguousarray(M, np.float32)).cuda()
+    flow = eng.run(Ct, Mt, K, a)
+    eng.sync()
+    L, D = eng.get_labels(0, H, W)
+    em, en, ew = eng.get_graph(0)
+    out = dict(flow=flow.cpu().numpy(), L=L.cpu().numpy(), D=D.cpu().numpy(),
+               em=em.cpu().numpy(), en=en.cpu().numpy(), ew=ew.cpu().numpy(),
+               passes=eng.get_passes())
+    if eng.cfg.keep_intermediates:
+        idx, dist, cnt = eng.get_knn(0, N, K)
+        out.update(idx=idx.cpu().numpy(), dist=dist.cpu().numpy(),
+                   count=cnt.cpu().numpy())
+    models, fb = eng.get_models(0, N)
+    out.update(models=models.cpu().numpy(), fallback=fb.cpu().numpy())
+    torch.cuda.synchronize()
+    if own:
+        eng.close()
+    return out
+
+
+def check_labels_and_distances(C, M, g, ref, report):
+    Lg, Dg = g["L"], g["D"].astype(np.float64)
+    Lr, Dr = ref["L"], ref["D"]
+    derr = np.abs(Dg - Dr)
+    bad_d = derr > D_RTOL * Dr + D_ATOL
+    assert not bad_d.any(), (
+        f"{bad_d.sum()} distances off; worst {derr.max():.3g} at D={Dr.ravel()[derr.argmax()]:.4g}")
+    diff = Lg != Lr
+    excused = np.zeros_like(diff)
+    if diff.any():
+        H, W = C.shape
+        ys, xs = np.nonzero(diff)
+        limit = float(Dr[diff].max()) * (1 + 2 * TIE_RTOL) + 1e-9
+        G = grid_graph(C)
+        sp_pix = seed_pixels(M, W)
+        for lab in np.unique(Lg[diff]):
+            sel = Lg[ys, xs] == lab
+            dm = dijkstra(G, directed=False, indices=[sp_pix[lab]], limit=limit)[0]
+            pidx = ys[sel] * W + xs[sel]
+            ok = dm[pidx] - Dr[ys[sel], xs[sel]] <= TIE_RTOL * Dr[ys[sel], xs[sel]] + 1e-12
+            assert ok.all(), f"label {lab}: {(~ok).sum()} pixels are not near ties"
+            excused[ys[sel], xs[sel]] = True
+    report["label_mismatch"] = int(diff.sum())
+    report["d_max_rel"] = float(np.max(derr / np.maximum(Dr, 1e-12)))
+    report["d_max_abs"] = float(derr.max())
+    return excused
+
+
+def check_graph(C, M, g, ref, report):
+    N = M.shape[0]
+    em, en, ew = oracle.graph(C, ref["D"], g["L"], M)
+    kr = em.astype(np.int64) * N + en
+    kg = g["em"].astype(np.int64) * N + g["en"]
+    assert (g["em"] < g["en"]).all()
+    og = np.argsort(kg)
+    kg, wg = kg[og], g["ew"][og].astype(np.float64)
+    assert len(np.unique(kg)) == len(kg), "duplicate edges"
+    assert np.array_equal(kg, kr), (
+        f"edge sets differ: {len(np.setdiff1d(kg, kr))} extra, {len(np.setdiff1d(kr, kg))} missing")
+    werr = np.abs(wg - ew)
+    assert (werr <= W_RTOL * ew + W_ATOL).all(), f"edge weight error {werr.max():.3g}"
+    report["edges"] = int(len(kg))
+    report["w_max_abs"] = float(werr.max()) if len(werr) else 0.0
+
+
+def check_knn(M, g, report):
+    N = M.shape[0]
+    K = g["idx"].shape[1]
+    em, en, ew = g["em"], g["en"], g["ew"].astype(np.float64)
+    ridx, rdist, rcnt = oracle.knn(N, em, en, ew, min(K + 1, N))
+    assert np.array_equal(g["count"], np.minimum(rcnt, K))
+    n_tie = 0
+    for m in range(N):
+        c = g["count"][m]
+        dk = rdist[m, c - 1]
+        near = c < rcnt[m] and rdist[m, c] - dk <= KNN_TIE * max(dk, 1e-30)
+        same = np.array_equal(g["idx"][m, :c], ridx[m, :c])
+        if not same:
+            # accept reorderings among near-equal keys with the same set, or a
+            # swap at the K-th place when the K-th/(K+1)-th keys nearly tie
+            setg, setr = set(g["idx"][m, :c]), set(ridx[m, :c])
+            assert setg == setr or near, f"match {m}: K-NN lists differ"
+            n_tie += 1
+        derr = np.abs(np.sort(g["dist"][m, :c].astype(np.float64)) - rdist[m, :c])
+        assert (derr <= KNN_TIE * rdist[m, :c] + 1e-6).all(), f"match {m}: distances"
+    report["knn_tie_lists"] = n_tie
+
+
+def oracle_on_labels(C, M, K, a, D_ref, L, weight_squared=True):
+    """Stages (b)-(d) of the oracle on a given (valid) labelling."""
+    N = M.shape[0]
+    K = int(min(K, N))
+    em, en, ew = oracle.graph(C, D_ref, L, M)
+    idx, dist, count = oracle.knn(N, em, en, ew, K)
+    model, fb, dr = oracle.fit(M, idx, dist, count, a, weight_squared)
+    flow = oracle.writeout(L, M, model)
+    return dict(D=D_ref, L=L, em=em, en=en, ew=ew, idx=idx, dist=dist,
+                count=count, model=model, fallback=fb, detratio=dr, flow=flow,
+                K=K)
+
+
+def fit_sensitivity(M, ref, a, weight_squared=True, draws=4):
+    """Largest flow change over each match's cell when its neighbour
+    distances are perturbed by SENS_REL relative (random signs)."""
+    N = M.shape[0]
+    rng = np.random.default_rng(12345)
+    worst = np.zeros(N)
+    Lf = ref["L"].ravel()
+    for _ in range(draws):
+        d = ref["dist"] * (1 + SENS_REL * rng.uniform(-1, 1, ref["dist"].shape))
+        mod, _, _ = oracle.fit(M, ref["idx"], d, ref["count"], a, weight_squared)
+        f = oracle.writeout(ref["L"], M, mod)
+        e = np.abs(f - ref["flow"]).max(-1).ravel()
+        np.maximum.at(worst, Lf, e)
+    return worst
+
+
+def flow_exclusions(M, ref, excused_pix, a=1.0, weight_squared=True):
+    """Pixels excluded from the 1e-3 px flow check (see module docstring)."""
+    N = M.shape[0]
+    K = ref["K"]
+    ridx, rdist, rcnt = oracle.knn(N, ref["em"], ref["en"], ref["ew"], min(K + 1, N))
+    near = np.zeros(N, bool)
+    for m in range(N):
+        c = ref["count"][m]
+        if c < rcnt[m]:
+            dk = rdist[m, c - 1]
+            near[m] = rdist[m, c] - dk <= KNN_TIE * max(dk, 1e-30)
+    dr = ref["detratio"]
+    near_det = (dr >= DET_EPS / 10) & (dr <= 10 * DET_EPS)
+    ill = fit_sensitivity(M, ref, a, weight_squared) > SENS_PX
+    bad_match = near | near_det | ill
+    excl = excused_pix | bad_match[ref["L"]]
+    return excl, int(near.sum()), int(near_det.sum()), int(ill.sum())
+
+
+def check_input_error(g, ref, report):
+    """The GPU's neighbour distances differ from the FP64 ones by no more than
+    the perturbation the ill-conditioning exclusion assumes."""
+    if "idx" not in g:
+        return
+    same = (g["idx"] == ref["idx"]).all(1) & (g["count"] == ref["count"])
+    if not same.any():
+        return
+    dg = g["dist"][same].astype(np.float64)
+    dr = ref["dist"][same]
+    fin = np.isfinite(dr)
+    err = np.abs(dg[fin] - dr[fin])
+    report["knn_dist_max_rel"] = float(np.max(err / np.maximum(dr[fin], 1e-30)))
+    assert (err <= SENS_REL * dr[fin] + SENS_ABS).all(), (
+        f"neighbour distances off by more than {SENS_REL} relative: {err.max():.3g}")
+
+
+def check_flow(M, g, ref, excused_pix, report, tol=FLOW_TOL, a=1.0, weight_squared=True):
+    check_input_error(g, ref, report)
+    excl, n_knn, n_det, n_ill = flow_exclusions(M, ref, excused_pix, a, weight_squared)
+    err = np.abs(g["flow"].astype(np.float64) - ref["flow"]).max(-1)
+    e_in = err[~excl]
+    report["flow_excluded_px"] = int(excl.sum())
+    report["knn_near_tie_matches"] = n_knn
+    report["det_near_threshold_matches"] = n_det
+    report["ill_conditioned_matches"] = n_ill
+    report["flow_max_err"] = float(e_in.max()) if e_in.size else 0.0
+    report["flow_p99_err"] = float(np.percentile(e_in, 99)) if e_in.size else 0.0
+    bad = e_in > tol
+    assert not bad.any(), (
+        f"{bad.sum()} pixels exceed {tol} px; worst {e_in.max():.4g}; report {report}")
+
+
+def full_parity(pair_or_arrays, K=None, a=None, eng=None, check_knn_lists=True,
+                weight_squared=True, **cfg):
+    if hasattr(pair_or_arrays, "C"):
+        C, M = pair_or_arrays.C, pair_or_arrays.matches
+        K = pair_or_arrays.K if K is None else K
+        a = pair_or_arrays.a if a is None else a
+    else:
+        C, M = pair_or_arrays
+    cfg["weight_squared"] = int(bool(weight_squared))
+    g = run_gpu((C, M), K=K, a=a, eng=eng, **cfg)
+    ref = oracle.interp(C, M, K, a, weight_squared=weight_squared)
+    report = {}
+    check_labels_and_distances(C, M, g, ref, report)
+    refb = oracle_on_labels(C, M, K, a, ref["D"], g["L"], weight_squared)
+    check_graph(C, M, g, refb, report)
+    if check_knn_lists and "idx" in g:
+        check_knn(M, g, report)
+    check_flow(M, g, refb, np.zeros(g["L"].shape, bool), report, a=a,
+               weight_squared=weight_squared)
+    e2e = np.abs(g["flow"].astype(np.float64) - ref["flow"]).max(-1)
+    report["tie_sensitivity_px_p99"] = float(np.percentile(e2e, 99))
+    report["tie_sensitivity_px_max"] = float(e2e.max())
+    return g, refb, report

@@ -1,0 +1,107 @@
+"""CUDA path vs the FP64 oracle, element by element (tolerances in parity.py).
+
+All calls go through the C ABI (ctypes binding); the oracle runs on the host
+on the same seeded inputs."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_02565_gb300 import synth
+from helpers import random_small_case
+from parity import full_parity, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _print(name, rep):
+    print(f"\n[{name}] " + " ".join(f"{k}={v}" for k, v in rep.items()))
+
+
+def test_config1_polygon_pair_full_parity():
+    p = synth.config_pair(1, 0)
+    g, ref, rep = full_parity(p)
+    _print("config1", rep)
+    assert rep["flow_excluded_px"] < 0.02 * p.P
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_small_random_cases_several_tiles_ragged_tail(seed):
+    # 83 x 150: several 64x32 tiles with ragged right and bottom tails
+    C, M = random_small_case(600 + seed, H=83, W=150, N=120, c_lo=0.01, c_hi=1.0)
+    g, ref, rep = full_parity((C, M), K=16, a=1.0)
+    _print(f"random{seed}", rep)
+
+
+@pytest.mark.parametrize("tile", [(8, 8, 0), (16, 8, 3), (32, 32, 0), (64, 32, 4), (128, 64, 8)])
+def test_tile_shapes_give_identical_keys(tile):
+    # every tile shape reaches the same fixed point bit for bit
+    p = synth.config_pair(1, 1)
+    tw, th, ap = tile
+    g = run_gpu(p, tile_w=tw, tile_h=th, apron=ap)
+    base = run_gpu(p, tile_w=64, tile_h=32, apron=4)
+    assert np.array_equal(g["L"], base["L"])
+    assert np.array_equal(g["D"], base["D"])
+    assert np.array_equal(g["flow"], base["flow"])
+
+
+def test_image_smaller_than_one_tile_and_single_match():
+    C = np.full((5, 7), 0.3, np.float32)
+    M = np.array([[3, 2, 5.5, 1.25]], np.float32)
+    g, ref, rep = full_parity((C, M), K=4, a=1.0)
+    assert (g["L"] == 0).all()
+    np.testing.assert_allclose(g["flow"][..., 0], 2.5, atol=1e-6)
+    np.testing.assert_allclose(g["flow"][..., 1], -0.75, atol=1e-6)
+
+
+def test_single_pixel_image():
+    C = np.array([[1.0]], np.float32)
+    M = np.array([[0, 0, 2, 3]], np.float32)
+    g, ref, rep = full_parity((C, M), K=1, a=1.0)
+    np.testing.assert_allclose(g["flow"][0, 0], [2, 3], atol=1e-6)
+
+
+def test_duplicate_source_pixels_and_k_larger_than_n():
+    rng = np.random.default_rng(9)
+    C = rng.uniform(0.05, 1, (40, 50)).astype(np.float32)
+    M = np.zeros((12, 4), np.float32)
+    M[:, 0] = rng.integers(0, 50, 12)
+    M[:, 1] = rng.integers(0, 40, 12)
+    M[5, :2] = M[2, :2]          # duplicate pixel: match 5 has an empty cell
+    M[:, 2:] = M[:, :2] + rng.normal(0, 2, (12, 2))
+    g, ref, rep = full_parity((C, M), K=40, a=0.7)
+    assert not (g["L"] == 5).any()
+    assert g["count"][5] == 12
+
+
+def test_global_affine_recovered_by_gpu():
+    rng = np.random.default_rng(23)
+    H, W, N = 97, 131, 300
+    C = rng.uniform(0.01, 1.0, (H, W)).astype(np.float32)
+    flat = rng.choice(H * W, N, replace=False)
+    A = np.array([[0.98, 0.03], [-0.05, 1.02]])
+    t = np.array([4.0, -6.0])
+    M = np.zeros((N, 4), np.float32)
+    M[:, 0], M[:, 1] = flat % W, flat // W
+    M[:, 2:] = (M[:, :2].astype(np.float64) @ A.T + t).astype(np.float32)
+    g = run_gpu((C, M), K=20, a=1.0)
+    ys, xs = np.mgrid[0:H, 0:W]
+    P = np.stack([xs, ys], -1).astype(np.float64)
+    np.testing.assert_allclose(g["flow"], P @ A.T + t - P, atol=2e-3)
+
+
+def test_unsquared_weight_reading():
+    # weight_squared = 0 minimises sum k |r|^2 instead of sum k^2 |r|^2
+    p = synth.config_pair(1, 2)
+    g, ref, rep = full_parity(p, weight_squared=False)
+    _print("unsquared", rep)
+
+
+@pytest.mark.parametrize("config", [2, 3])
+def test_full_size_workloads_full_parity(config):
+    # every pixel and every match of the Sintel- and KITTI-shaped pairs,
+    # in the default launch configuration
+    p = synth.config_pair(config, 0)
+    g, ref, rep = full_parity(p)
+    _print(f"config{config}", rep)
+    assert rep["flow_excluded_px"] < 0.02 * p.P
