@@ -1,0 +1,401 @@
+"""Throughput benchmark of the GB300 sparse-to-dense interpolator.
+
+One step = the whole interpolator (relaxation, match graph, K-NN + LA fit,
+write-out) over a batch of Sintel-shaped synthetic pairs (1024x436, 5000
+matches on a jittered 8-px grid, K = 100, a = 1), launched as one batched run
+through the C ABI.  The batch's buffers (~300 MB) exceed the 129 MB L2, so
+consecutive steps do not run from cache.
+
+Prints one JSON line (rank 0).  Keys beyond the common ones:
+  roofline      the dominant kernel's achieved rate vs the measured HBM peak,
+                timed live with CUDA events recorded by the library between
+                its kernels; traffic from the committed ncu summary (null if
+                the kernel source changed since the capture)
+  stages        the same figures for every kernel
+  e2e           same metric through epic_interp_run_batch_host: pinned host
+                buffers, copies inside the timed region
+  plain         the one-pair-at-a-time GPU path on the same pairs
+  cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample
+  clocks        nvidia-smi samples taken during the timed region
+
+--impl reference runs the oracle itself as the reference arm.
+Multi-GPU (torchrun): independent replicas, one batch per rank, no collective
+on the data path ("scaling": "weak").
+"""
+
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W, N_MATCH, K_NN, A_KERNEL = 436, 1024, 5000, 100, 1.0
+PAPER_MPIX_S = 1024 * 436 / 0.25 / 1e6   # Sec. 5.4: 0.25 s per pair, 1 core
+STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout")
+KERNEL_SRC = {
+    "prepare": "k_prepare.cu", "relax": "k_dt.cu", "edges": "k_graph.cu",
+    "scatter": "k_graph.cu", "knn_fit": "k_knn_fit.cu", "writeout": "k_writeout.cu",
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=32, help="pairs per step")
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--cpu-threads", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_pairs(n, rank):
+    from paper_1501_02565_gb300 import synth
+    # distinct pairs per rank: pair index offset by rank * n
+    return [synth.config_pair(2, rank * n + i) for i in range(n)]
+
+
+# ---------------------------------------------------------------------------
+# workload accounting (algorithmic bytes per unit; see the design notes)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(stage, pairs, n_edges):
+    P = sum(p.P for p in pairs)
+    N = sum(p.N for p in pairs)
+    if stage == "relax":        # read C, write (D, L)
+        return 12.0 * P
+    if stage == "edges":        # read (D, L) and C
+        return 12.0 * P
+    if stage == "writeout":     # read L, write flow (u, v)
+        return 12.0 * P
+    if stage == "prepare":      # read matches, write seed bins
+        return 20.0 * N
+    if stage == "scatter":      # read edge table, write both adjacency entries
+        return 28.0 * n_edges
+    if stage == "knn_fit":      # per match: K neighbour records (16 B) and
+        # their adjacency rows (deg x 8 B), plus the 32 B model
+        deg = 2.0 * n_edges / max(N, 1)
+        return sum(p.N * (min(p.K, p.N) * (16.0 + deg * 8.0) + 32.0) for p in pairs)
+    raise KeyError(stage)
+
+
+def kernel_sha(stage):
+    path = os.path.join(ROOT, "paper_1501_02565_gb300", "csrc", KERNEL_SRC[stage])
+    h = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    return h[:16]
+
+
+def committed_traffic(stage, batch):
+    """dram bytes per launch from a committed ncu summary of this kernel at
+    this batch size, if its source hash still matches."""
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        txt = open(f).read()
+        m = re.search(r"traffic_bytes_per_launch\[%s,batch=%d\]:\s*([0-9.eE+]+)\s+src=([0-9a-f]+)"
+                      % (stage, batch), txt)
+        if m and m.group(2) == kernel_sha(stage):
+            return float(m.group(1)), os.path.relpath(f, ROOT)
+    return None, None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for nm, v in zip(names, r[2]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_pass(pairs, threads):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda p: oracle.interp(p.C, p.matches, p.K, p.a)["flow"].shape, pairs))
+    return time.perf_counter() - t0
+
+
+def cpu_threads(args):
+    if args.cpu_threads > 0:
+        return args.cpu_threads
+    return max(1, min(os.cpu_count() or 1, 16))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    threads = cpu_threads(args)
+    pairs = make_pairs(args.batch, 0)
+    sample = pairs[: max(threads, min(len(pairs), 2 * threads))]
+    for _ in range(args.warmup):
+        oracle_pass(sample[:threads], threads)
+    t = 0.0
+    for _ in range(args.steps):
+        t += oracle_pass(sample, threads)
+    px = sum(p.P for p in sample) * args.steps
+    value = px / t / 1e6
+    line = {
+        "impl": "reference", "metric": "interpolated Mpix/s", "value": value,
+        "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_MPIX_S,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Sintel-shaped pairs {W}x{H}, N={N_MATCH}, K={K_NN}, a={A_KERNEL}",
+                   "pairs_per_step": len(sample)},
+        "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "Mpix/s",
+                         "sample": f"{len(sample)} Sintel-shaped pairs per step, one pair per thread"},
+        "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1501_02565_gb300.native import EpicInterp
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pairs = make_pairs(args.batch, rank)
+    B = len(pairs)
+    eng = EpicInterp(local_rank, max_pairs=B)
+    items = []
+    for p in pairs:
+        items.append((torch.from_numpy(p.C).to(dev), torch.from_numpy(p.matches).to(dev),
+                      p.K, p.a, torch.empty((p.H, p.W, 2), dtype=torch.float32, device=dev)))
+    step_bytes = sum(it[0].numel() * 4 + it[4].numel() * 4 + it[1].numel() * 4 for it in items)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (also checks the device status once)
+    for _ in range(max(args.warmup, 3)):
+        eng.run_batch(items)
+    eng.sync()
+    n_edges = sum(eng.get_edge_count(i) for i in range(B))
+    passes = eng.get_passes()
+
+    # ---- device-resident timed region --------------------------------------
+    clocks = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    eng.enable_stage_timing(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        eng.run_batch(items)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    stage_ms, n_runs = eng.stage_times()
+    eng.enable_stage_timing(False)
+    eng.sync()
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    px_rank = sum(p.P for p in pairs) * args.steps
+    value = px_rank * world / (ms_total / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with pinned host buffers ------------
+    host = []
+    for p in pairs:
+        host.append((torch.from_numpy(p.C).pin_memory(), torch.from_numpy(p.matches).pin_memory(),
+                     p.K, p.a, torch.empty((p.H, p.W, 2), dtype=torch.float32).pin_memory()))
+    h2d = sum(h[0].numel() * 4 + h[1].numel() * 4 for h in host)
+    d2h = sum(h[4].numel() * 4 for h in host)
+    eng.run_batch_host(host)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        eng.run_batch_host(host)
+    t_e2e = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = px_rank * world / t_e2e / 1e6
+    # sanity: the host result equals the device-resident one
+    assert torch.equal(host[0][4], items[0][4].cpu()), "host and device paths differ"
+
+    # ---- plain one-pair-at-a-time path ------------------------------------
+    lat = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in items]
+    for it in items:
+        eng.run_batch([it])
+    torch.cuda.synchronize()
+    tp0 = torch.cuda.Event(enable_timing=True)
+    tp1 = torch.cuda.Event(enable_timing=True)
+    tp0.record(stream)
+    for it, (a0, a1) in zip(items, ev):
+        a0.record(stream)
+        eng.run_batch([it])
+        a1.record(stream)
+    tp1.record(stream)
+    torch.cuda.synchronize()
+    eng.sync()
+    lat = [a0.elapsed_time(a1) for a0, a1 in ev]
+    plain_value = sum(p.P for p in pairs) / (tp0.elapsed_time(tp1) / 1e3) / 1e6
+
+    # ---- roofline ----------------------------------------------------------
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    stages = {}
+    for s in STAGES:
+        ms = stage_ms[s] / max(n_runs, 1)
+        by = algorithmic_bytes(s, pairs, n_edges)
+        gbs = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        stages[s] = {"ms_per_launch": ms, "algorithmic_bytes": by, "achieved_gbs": gbs,
+                     "frac_hbm": gbs / hbm}
+    dom = max(STAGES, key=lambda s: stages[s]["ms_per_launch"])
+    traffic, traffic_src = committed_traffic(dom, B)
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": stages[dom]["achieved_gbs"],
+                "peak": hbm, "unit": "GB/s", "frac": stages[dom]["frac_hbm"],
+                "traffic": traffic, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                "traffic_source": traffic_src}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ---------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = cpu_threads(args)
+        sample = pairs[: max(threads, min(B, 2 * threads))]
+        t = oracle_pass(sample, threads)
+        cpu = {"value": sum(p.P for p in sample) / t / 1e6, "unit": "Mpix/s",
+               "cores": threads, "kind": "oracle",
+               "sample": f"{len(sample)} of the step's Sintel-shaped pairs, one pair per thread"}
+
+    if rank == 0:
+        line = {
+            "metric": "interpolated Mpix/s", "value": value, "unit": "Mpix/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / PAPER_MPIX_S,
+            "vs_baseline_ref": "paper Sec. 5.4: 0.25 s per 1024x436 pair on one 3.6 GHz CPU core",
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Sintel-shaped pairs {W}x{H}, N={N_MATCH}, K={K_NN}, a={A_KERNEL}",
+                       "pairs_per_step": B, "parallelism": f"replicas{world}",
+                       "l2": f"inputs larger than L2 ({step_bytes / 1e6:.0f} MB of inputs and outputs per step)"},
+            "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": eng.launches_per_run(B) * args.steps,
+            "roofline": roofline,
+            "stages": stages,
+            "plain": {"value": plain_value, "unit": "Mpix/s",
+                      "latency_ms_p50": float(np.percentile(lat, 50)),
+                      "latency_ms_p99": float(np.percentile(lat, 99))},
+            "batched_latency_ms": ms_total / args.steps,
+            "relax_passes": passes,
+            "edges_per_step": n_edges,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    eng.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

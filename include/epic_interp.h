@@ -117,6 +117,13 @@ int epic_interp_run_host(epic_interp_t *h, const float *cost_map,
                          const float *matches, int H, int W, int N, int K,
                          float a, float *flow_out, void *stream);
 
+/* Batched form of epic_interp_run_host: every descriptor holds HOST
+ * pointers.  Copies all inputs to the device (one cudaMemcpyAsync per
+ * buffer; pinned host memory makes them asynchronous DMA), runs the batch,
+ * copies every flow back and waits.  Returns the device status. */
+int epic_interp_run_batch_host(epic_interp_t *h, const epic_pair_desc_t *pairs,
+                               int n, void *stream);
+
 /* Wait for the last run's stream and return its device status (then clear
  * it).  EPIC_OK when every stage completed within its limits. */
 int epic_interp_sync(epic_interp_t *h);

@@ -67,6 +67,7 @@ struct PairDev {
     pkey_t *hkeys;           // [hash_cap] (m << 32 | n), m < n
     unsigned *hw;           // [hash_cap] float bits of the edge weight
     int *deg;               // [N] node degree in G
+    unsigned *wmin;         // [N] float bits of the lightest edge at each node
     pkey_t *adj;             // [N * max_degree] (w bits << 32 | neighbour)
     float4 *models;         // [N * 2] (c_u, c_v, b11, b12), (b21, b22, x_m, y_m)
     int *fallback;          // [N]

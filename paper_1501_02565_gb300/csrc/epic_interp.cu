@@ -99,7 +99,7 @@ void choose_tiles(const epic_config_t &c, int H, int W, int *tw, int *th, int *a
 }
 
 struct Layout {
-    size_t keys, tile_start, tile_fill, tile_seeds, hkeys, hw, deg, adj, models,
+    size_t keys, tile_start, tile_fill, tile_seeds, hkeys, hw, deg, wmin, adj, models,
         fallback, knn_idx, knn_dist, knn_count, info, end;
 };
 
@@ -120,6 +120,7 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep) {
     L.hkeys = take((size_t)P.hash_cap * sizeof(pkey_t));
     L.hw = take((size_t)P.hash_cap * sizeof(unsigned));
     L.deg = take((size_t)P.N * sizeof(int));
+    L.wmin = take((size_t)P.N * sizeof(unsigned));
     L.adj = take((size_t)P.N * max_degree * sizeof(pkey_t));
     L.models = take((size_t)P.N * 2 * sizeof(float4));
     L.fallback = take((size_t)P.N * sizeof(int));
@@ -343,6 +344,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         P[i].hkeys = reinterpret_cast<pkey_t *>(b + L[i].hkeys);
         P[i].hw = reinterpret_cast<unsigned *>(b + L[i].hw);
         P[i].deg = reinterpret_cast<int *>(b + L[i].deg);
+        P[i].wmin = reinterpret_cast<unsigned *>(b + L[i].wmin);
         P[i].adj = reinterpret_cast<pkey_t *>(b + L[i].adj);
         P[i].models = reinterpret_cast<float4 *>(b + L[i].models);
         P[i].fallback = reinterpret_cast<int *>(b + L[i].fallback);
@@ -500,6 +502,61 @@ int epic_interp_run_host(epic_interp_t *h, const float *cost_map, const float *m
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(flow_out, h->io_F, nF * 4, cudaMemcpyDeviceToHost, stream)))
         return cuda_fail(h, e, "run_host download");
+    return epic_interp_sync(h);
+}
+
+int epic_interp_run_batch_host(epic_interp_t *h, const epic_pair_desc_t *descs, int n,
+                               void *stream_) {
+    if (!h) return EPIC_ERR_INVALID;
+    if (!descs || n < 1) return fail(h, EPIC_ERR_INVALID, "empty batch");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(h, descs[i], i);
+        if (rc) return rc;
+    }
+    // one staging buffer: per pair C, matches, flow (256-byte aligned)
+    std::vector<size_t> oc(n), om(n), of(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)descs[i].H * descs[i].W;
+        oc[i] = off; off = align_up(off + px * 4, 256);
+        om[i] = off; off = align_up(off + (size_t)descs[i].N * 16, 256);
+        of[i] = off; off = align_up(off + px * 8, 256);
+    }
+    if (off > h->io_C_n * 4) {
+        int rc = wait_last(h);
+        if (rc) return rc;
+        if (h->io_C) cudaFree(h->io_C);
+        h->io_C = nullptr;
+        h->io_C_n = 0;
+        e = cudaMalloc(&h->io_C, off);
+        if (e != cudaSuccess) return cuda_fail(h, e, "run_batch_host cudaMalloc");
+        h->io_C_n = off / 4;
+    }
+    char *base = reinterpret_cast<char *>(h->io_C);
+    std::vector<epic_pair_desc_t> dev(n);
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)descs[i].H * descs[i].W;
+        if ((e = cudaMemcpyAsync(base + oc[i], descs[i].cost_map, px * 4,
+                                 cudaMemcpyHostToDevice, stream)) ||
+            (e = cudaMemcpyAsync(base + om[i], descs[i].matches, (size_t)descs[i].N * 16,
+                                 cudaMemcpyHostToDevice, stream)))
+            return cuda_fail(h, e, "run_batch_host upload");
+        dev[i] = descs[i];
+        dev[i].cost_map = reinterpret_cast<const float *>(base + oc[i]);
+        dev[i].matches = reinterpret_cast<const float *>(base + om[i]);
+        dev[i].flow_out = reinterpret_cast<float *>(base + of[i]);
+    }
+    int rc = epic_interp_run_batch(h, dev.data(), n, stream_);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)descs[i].H * descs[i].W;
+        if ((e = cudaMemcpyAsync(descs[i].flow_out, base + of[i], px * 8,
+                                 cudaMemcpyDeviceToHost, stream)))
+            return cuda_fail(h, e, "run_batch_host download");
+    }
     return epic_interp_sync(h);
 }
 

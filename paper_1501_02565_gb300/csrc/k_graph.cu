@@ -18,7 +18,8 @@
 //                match whose source pixel is owned by a smaller index (a
 //                duplicate) is joined to the owner at distance D = 0.
 // scatter_kernel every occupied slot appends (w, n) to row m and (w, m) to
-//                row n of a fixed-capacity adjacency array.
+//                row n of a fixed-capacity adjacency array, and lowers the
+//                lightest-edge weight of both nodes.
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -161,6 +162,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(BatchArgs a) {
         if (pm < md) P.adj[(size_t)m * md + pm] = wb | n;
         if (pn < md) P.adj[(size_t)n * md + pn] = wb | m;
         if (pm >= md || pn >= md) set_status(st, EPIC_ERR_CAPACITY);
+        atomicMin(P.wmin + m, P.hw[s]);
+        atomicMin(P.wmin + n, P.hw[s]);
         atomicAdd(P.info + 0, 1);
         atomicMax(P.info + 1, max(pm, pn) + 1);
     }

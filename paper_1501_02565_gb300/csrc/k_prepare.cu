@@ -77,7 +77,10 @@ __global__ void __launch_bounds__(1024) prepare_kernel(BatchArgs a) {
         const PairDev P = a.pairs[p];
         const int T = P.tiles_x * P.tiles_y;
         for (int t = threadIdx.x; t < T; t += blockDim.x) P.tile_start[t] = 0;
-        for (int m = threadIdx.x; m < P.N; m += blockDim.x) P.deg[m] = 0;
+        for (int m = threadIdx.x; m < P.N; m += blockDim.x) {
+            P.deg[m] = 0;
+            P.wmin[m] = 0x7F800000u;  // +inf
+        }
         if (threadIdx.x < 4) P.info[threadIdx.x] = 0;
         __syncthreads();
         for (int m = threadIdx.x; m < P.N; m += blockDim.x) {

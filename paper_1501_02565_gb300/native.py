@@ -30,7 +30,8 @@ STATUS_NAMES = {
 # Every symbol include/epic_interp.h declares.
 EXPORTED = (
     "epic_config_default", "epic_interp_create", "epic_interp_run",
-    "epic_interp_run_batch", "epic_interp_run_host", "epic_interp_sync",
+    "epic_interp_run_batch", "epic_interp_run_host",
+    "epic_interp_run_batch_host", "epic_interp_sync",
     "epic_interp_get_labels", "epic_interp_get_edge_count",
     "epic_interp_get_graph", "epic_interp_get_knn", "epic_interp_get_models",
     "epic_interp_get_passes", "epic_interp_enable_stage_timing",
@@ -96,6 +97,8 @@ def load(path: str | None = None):
     lib.epic_interp_run_batch.restype = I
     lib.epic_interp_run_host.argtypes = [P, P, P, I, I, I, I, F, P, P]
     lib.epic_interp_run_host.restype = I
+    lib.epic_interp_run_batch_host.argtypes = [P, ctypes.POINTER(epic_pair_desc_t), I, P]
+    lib.epic_interp_run_batch_host.restype = I
     lib.epic_interp_sync.argtypes = [P]
     lib.epic_interp_sync.restype = I
     lib.epic_interp_get_labels.argtypes = [P, I, P, P, P]
@@ -209,6 +212,18 @@ class EpicInterp:
                                            matches.shape[0], int(K), float(a),
                                            addr(flow), _stream_handle(stream))
         self._check(rc, "epic_interp_run_host")
+
+    def run_batch_host(self, items, stream=None):
+        """items: list of (C, matches, K, a, flow) with contiguous float32 CPU
+        tensors (pinned for asynchronous copies); waits for completion."""
+        n = len(items)
+        arr = (epic_pair_desc_t * n)()
+        for i, (C, M, K, a, F) in enumerate(items):
+            arr[i] = epic_pair_desc_t(C.data_ptr(), M.data_ptr(), C.shape[0],
+                                      C.shape[1], M.shape[0], int(K), float(a),
+                                      F.data_ptr())
+        rc = self.lib.epic_interp_run_batch_host(self.h, arr, n, _stream_handle(stream))
+        self._check(rc, "epic_interp_run_batch_host")
 
     def sync(self):
         self._check(self.lib.epic_interp_sync(self.h), "device status")
