@@ -172,6 +172,31 @@ int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages,
 /* Number of kernel launches one run of `n` pairs enqueues. */
 int epic_interp_launches_per_run(epic_interp_t *h, int n);
 
+/* Stage (a) alone -- the assignment map L and distance D -- computed without
+ * allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library allocate, such as a
+ * host framework that owns every device allocation and only lends buffers,
+ * or a latency-critical loop where cudaMalloc's implicit synchronisation is
+ * not acceptable.  Inputs as for epic_interp_run (device pointers, matches
+ * 16-byte aligned); outputs labels_out [H*W] int32 and dist_out [H*W]
+ * float32 (device pointers, either may be NULL but not both), identical to
+ * epic_interp_get_labels after epic_interp_run.
+ *   - Scratch is a file-scope device array of the library (about 5 MB, held
+ *     by every GPU that loads the library until the process exits); frames
+ *     are limited to 524288 pixels, 32768 matches and 16384 relaxation tiles
+ *     of 64 x 32 pixels.  Larger inputs return EPIC_ERR_CAPACITY without
+ *     doing any work.
+ *   - Runs on the current device.  The first call on each device looks up
+ *     the array's device address (cudaGetSymbolAddress); make that first
+ *     call before any stream capture.
+ *   - Every call shares the array: calls that overlap on the GPU race.  Each
+ *     call clears its run state, waits for its own work on `stream` and
+ *     returns the device status (EPIC_OK, or e.g. EPIC_ERR_INVALID for a
+ *     match outside the image). */
+int epic_geodesic_labels_noalloc(const float *cost_map, const float *matches,
+                                 int H, int W, int N, int *labels_out,
+                                 float *dist_out, void *stream);
+
 /* Message describing the last error on this handle (never NULL). */
 const char *epic_interp_last_error(epic_interp_t *h);
 

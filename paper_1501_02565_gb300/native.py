@@ -37,6 +37,7 @@ EXPORTED = (
     "epic_interp_get_passes", "epic_interp_enable_stage_timing",
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
+    "epic_geodesic_labels_noalloc",
 )
 
 
@@ -123,6 +124,8 @@ def load(path: str | None = None):
     lib.epic_interp_last_error.restype = ctypes.c_char_p
     lib.epic_interp_destroy.argtypes = [P]
     lib.epic_interp_destroy.restype = None
+    lib.epic_geodesic_labels_noalloc.argtypes = [P, P, I, I, I, P, P, P]
+    lib.epic_geodesic_labels_noalloc.restype = I
     _lib = lib
     return lib
 

@@ -1,0 +1,74 @@
+"""epic_geodesic_labels_noalloc: the assignment map (stage a) for callers that
+cannot let a library allocate device memory, e.g. a host framework that owns
+every device allocation and only lends buffers, or a latency-critical loop
+where cudaMalloc's implicit synchronisation is not acceptable.  Its scratch is
+a fixed device array inside the library.
+
+Checked through the C ABI against the regular entry point
+(epic_interp_run + epic_interp_get_labels) on two calls in a row, with the
+parity tolerances of tests/parity.py (labels equal, distances within
+1e-4 * D + 1e-6)."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1501_02565_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(lib, C, M, H, W, N):
+    import torch
+    L = torch.full((H, W), -7, dtype=torch.int32, device=C.device)
+    D = torch.full((H, W), -7.0, dtype=torch.float32, device=C.device)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.epic_geodesic_labels_noalloc(ctypes.c_void_p(C.data_ptr()),
+                                          ctypes.c_void_p(M.data_ptr()), H, W, N,
+                                          ctypes.c_void_p(L.data_ptr()),
+                                          ctypes.c_void_p(D.data_ptr()), stream)
+    return rc, L.cpu().numpy(), D.cpu().numpy()
+
+
+def _regular(p, C, M):
+    eng = native.EpicInterp(0)
+    eng.run(C, M, p.K, p.a)
+    eng.sync()
+    L, D = eng.get_labels(0, p.H, p.W)
+    out = L.cpu().numpy(), D.cpu().numpy()
+    eng.close()
+    return out
+
+
+def _check(Ln, Dn, Lr, Dr):
+    assert np.array_equal(Ln, Lr)
+    Dr64 = Dr.astype(np.float64)
+    assert (np.abs(Dn.astype(np.float64) - Dr64) <= 1e-4 * Dr64 + 1e-6).all()
+
+
+def test_noalloc_matches_regular_entry_point_on_two_calls():
+    import torch
+    lib = native.load()
+    # two calls in a row on different frames (the second larger), then the
+    # first frame again: the shared scratch keeps the previous call's
+    # contents, which must not leak into the next result
+    frames = [synth.config_pair(1, 0), synth.config_pair(2, 0), synth.config_pair(1, 0)]
+    for p in frames:
+        C = torch.from_numpy(p.C).cuda()
+        M = torch.from_numpy(p.matches).cuda()
+        rc, Ln, Dn = _noalloc(lib, C, M, p.H, p.W, p.N)
+        assert rc == native.EPIC_OK, native.STATUS_NAMES.get(rc, rc)
+        Lr, Dr = _regular(p, C, M)
+        _check(Ln, Dn, Lr, Dr)
+
+
+def test_noalloc_rejects_frames_beyond_its_scratch():
+    import torch
+    lib = native.load()
+    H, W, N = 1024, 1024, 10       # 1 Mpixel > the 524288-pixel limit
+    C = torch.ones((H, W), dtype=torch.float32, device="cuda")
+    M = torch.zeros((N, 4), dtype=torch.float32, device="cuda")
+    rc, Ln, Dn = _noalloc(lib, C, M, H, W, N)
+    assert rc == native.EPIC_ERR_CAPACITY
+    assert (Ln == -7).all() and (Dn == -7.0).all()   # nothing was written
