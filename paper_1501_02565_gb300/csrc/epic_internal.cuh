@@ -64,6 +64,7 @@ struct PairDev {
     int *tile_start;        // [tiles+1] seed bins (prefix offsets)
     int *tile_fill;         // [tiles] scatter cursors
     int *tile_seeds;        // [N] match indices grouped by tile
+    int *tile_stamp;        // [tiles] last relaxation pass that wrote the tile
     pkey_t *hkeys;           // [hash_cap] (m << 32 | n), m < n
     unsigned *hw;           // [hash_cap] float bits of the edge weight
     int *deg;               // [N] node degree in G

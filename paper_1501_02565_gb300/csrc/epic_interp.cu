@@ -99,7 +99,7 @@ void choose_tiles(const epic_config_t &c, int H, int W, int *tw, int *th, int *a
 }
 
 struct Layout {
-    size_t keys, tile_start, tile_fill, tile_seeds, hkeys, hw, deg, wmin, adj, models,
+    size_t keys, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, adj, models,
         fallback, knn_idx, knn_dist, knn_count, info, end;
 };
 
@@ -117,6 +117,7 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep) {
     L.tile_start = take((T + 1) * sizeof(int));
     L.tile_fill = take(T * sizeof(int));
     L.tile_seeds = take((size_t)P.N * sizeof(int));
+    L.tile_stamp = take(T * sizeof(int));
     L.hkeys = take((size_t)P.hash_cap * sizeof(pkey_t));
     L.hw = take((size_t)P.hash_cap * sizeof(unsigned));
     L.deg = take((size_t)P.N * sizeof(int));
@@ -324,8 +325,9 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     int max_tw = 8, max_th = 8, max_ap = 0, max_K = 1;
     for (int i = 0; i < n; ++i) {
         P[i] = make_pair_desc(c, descs[i]);
-        if (P[i].apron + 1 > std::min(P[i].tile_w, P[i].tile_h))
-            return fail(h, EPIC_ERR_INVALID, "apron must be smaller than the tile sides");
+        if (P[i].apron + 1 > std::min(P[i].tile_w, P[i].tile_h) || P[i].apron > 64)
+            return fail(h, EPIC_ERR_INVALID,
+                        "apron must be smaller than the tile sides and at most 64");
         L[i] = layout_pair(off, P[i], c.max_degree, c.keep_intermediates != 0);
         off = L[i].end;
         max_tw = std::max(max_tw, P[i].tile_w);
@@ -341,6 +343,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         P[i].tile_start = reinterpret_cast<int *>(b + L[i].tile_start);
         P[i].tile_fill = reinterpret_cast<int *>(b + L[i].tile_fill);
         P[i].tile_seeds = reinterpret_cast<int *>(b + L[i].tile_seeds);
+        P[i].tile_stamp = reinterpret_cast<int *>(b + L[i].tile_stamp);
         P[i].hkeys = reinterpret_cast<pkey_t *>(b + L[i].hkeys);
         P[i].hw = reinterpret_cast<unsigned *>(b + L[i].hw);
         P[i].deg = reinterpret_cast<int *>(b + L[i].deg);

@@ -37,7 +37,8 @@ constexpr size_t OFF_KEYS = 0;
 constexpr size_t OFF_TSTART = align256(OFF_KEYS + sizeof(pkey_t) * NA_MAX_PIXELS);
 constexpr size_t OFF_TFILL = align256(OFF_TSTART + sizeof(int) * (NA_MAX_TILES + 1));
 constexpr size_t OFF_TSEEDS = align256(OFF_TFILL + sizeof(int) * NA_MAX_TILES);
-constexpr size_t OFF_DEG = align256(OFF_TSEEDS + sizeof(int) * NA_MAX_MATCHES);
+constexpr size_t OFF_TSTAMP = align256(OFF_TSEEDS + sizeof(int) * NA_MAX_MATCHES);
+constexpr size_t OFF_DEG = align256(OFF_TSTAMP + sizeof(int) * NA_MAX_TILES);
 constexpr size_t OFF_WMIN = align256(OFF_DEG + sizeof(int) * NA_MAX_MATCHES);
 constexpr size_t OFF_INFO = align256(OFF_WMIN + sizeof(unsigned) * NA_MAX_MATCHES);
 constexpr size_t OFF_STATE = align256(OFF_INFO + 4 * sizeof(int));
@@ -110,6 +111,7 @@ extern "C" int epic_geodesic_labels_noalloc(const float *cost_map, const float *
     Pd.tile_start = reinterpret_cast<int *>(base + OFF_TSTART);
     Pd.tile_fill = reinterpret_cast<int *>(base + OFF_TFILL);
     Pd.tile_seeds = reinterpret_cast<int *>(base + OFF_TSEEDS);
+    Pd.tile_stamp = reinterpret_cast<int *>(base + OFF_TSTAMP);
     Pd.deg = reinterpret_cast<int *>(base + OFF_DEG);
     Pd.wmin = reinterpret_cast<unsigned *>(base + OFF_WMIN);
     Pd.info = reinterpret_cast<int *>(base + OFF_INFO);

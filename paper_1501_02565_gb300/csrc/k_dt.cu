@@ -16,7 +16,11 @@
 //   phase 2  repeated passes: a tile whose border can be improved from the
 //            current keys of the pixels just outside it reloads
 //            (tile + ring) and re-solves; the passes end when no tile is
-//            dirty, i.e. no step improves any key anywhere.
+//            dirty, i.e. no step improves any key anywhere.  Every tile
+//            records the last pass that wrote it; a tile is checked in pass k
+//            only if one of its eight neighbours was written in pass k-1 or
+//            later (phase 1 counts as pass 0), because a tile checked clean
+//            stays clean until a neighbour changes.
 //
 // The in-tile solver runs directional sweeps (down, up, right, left), each
 // relaxing a pixel from its three neighbours on the side the sweep comes
@@ -227,7 +231,8 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
     }
     __syncthreads();
     local_solve(K, h, g, st);
-    // write the tile's own pixels
+    // write the tile's own pixels and mark it written in pass 0
+    if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = 0;
     const int off = P.apron + 1;
     for (int i = threadIdx.x; i < P.tile_w * P.tile_h; i += blockDim.x) {
         int ly = i / P.tile_w, lx = i - ly * P.tile_w;
@@ -282,7 +287,7 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
 
 // Phase 2 re-solve of tile (tx, ty) from the current keys (tile + ring).
 __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
-                            float *h, RunState *st) {
+                            float *h, RunState *st, int pass) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, 0);
     load_costs(P, g, h);
@@ -301,7 +306,25 @@ __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
                 P.keys[(size_t)gy * P.W + gx] = K[(ly + 1) * g.P + lx + 1];
         }
     }
+    if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = pass;
     __syncthreads();
+}
+
+// Was any of the eight neighbours of tile (tx, ty) written in pass
+// `since` or later?  (Stamps of other tiles change during the launch, so
+// they are read through L2.)
+__device__ __forceinline__ bool neighbour_changed(const PairDev &P, int tx, int ty,
+                                                  int since) {
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int y = ty + dy;
+        if (y < 0 || y >= P.tiles_y) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int x = tx + dx;
+            if ((dx == 0 && dy == 0) || x < 0 || x >= P.tiles_x) continue;
+            if (__ldcg(P.tile_stamp + y * P.tiles_x + x) >= since) return true;
+        }
+    }
+    return false;
 }
 
 __global__ void __launch_bounds__(DT_THREADS) dt_kernel(BatchArgs a) {
@@ -343,13 +366,17 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(BatchArgs a) {
             __syncthreads();
             const PairDev &P = a.pairs[s_pair];
             const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
-            if (border_dirty(P, tx, ty)) {
+            __shared__ int s_check;
+            if (threadIdx.x == 0) s_check = neighbour_changed(P, tx, ty, pass);
+            __syncthreads();
+            if (s_check && border_dirty(P, tx, ty)) {
                 const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                 pkey_t *K = reinterpret_cast<pkey_t *>(smem);
                 float *h = reinterpret_cast<float *>(smem + sizeof(pkey_t) * g.RH * g.P);
-                solve_again(P, tx, ty, K, h, st);
+                solve_again(P, tx, ty, K, h, st, pass + 1);
                 if (threadIdx.x == 0) atomicAdd(cnt, 1u);
             }
+            __syncthreads();
         }
         if (!grid_sync(st)) return;
         const unsigned dirty = ld_acquire(cnt);

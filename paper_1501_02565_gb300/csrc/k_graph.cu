@@ -12,11 +12,14 @@
 //
 // edges_kernel   every pixel looks at its four forward neighbours (right,
 //                down-left, down, down-right: each unordered pixel pair once)
-//                and inserts (min label, max label, weight) into an
-//                open-addressing table with atomicMin on the weight; lanes of
-//                a warp holding the same label pair are merged first.  A
-//                match whose source pixel is owned by a smaller index (a
-//                duplicate) is joined to the owner at distance D = 0.
+//                and forms (min label, max label, weight).  Candidates are
+//                merged per tile (64 x 32 pixels hold only tens of distinct
+//                label pairs): first across the lanes of a warp, then in a
+//                shared-memory table with atomicMin on the weight; the tile's
+//                unique entries are then inserted into the pair's global
+//                open-addressing table.  A match whose source pixel is owned
+//                by a smaller index (a duplicate) is joined to the owner at
+//                distance D = 0.
 // scatter_kernel every occupied slot appends (w, n) to row m and (w, m) to
 //                row n of a fixed-capacity adjacency array, and lowers the
 //                lightest-edge weight of both nodes.
@@ -45,9 +48,28 @@ __device__ __forceinline__ void table_insert(const PairDev &P, pkey_t k,
     set_status(st, EPIC_ERR_CAPACITY);
 }
 
-// Insert one candidate per active lane, merging equal label pairs in the warp.
-__device__ __forceinline__ void warp_insert(const PairDev &P, bool have,
-                                            pkey_t k, unsigned wbits,
+constexpr int TILE_TABLE = 1024;  // shared-memory slots per CTA (power of two)
+
+// Insert into the CTA's shared table; false if the probe sequence is full.
+__device__ __forceinline__ bool smem_insert(pkey_t *sk, unsigned *sw, pkey_t k,
+                                            unsigned wbits) {
+    unsigned s = hash_slot(k, TILE_TABLE);
+    for (int probe = 0; probe < 64; ++probe) {
+        const pkey_t prev = atomicCAS(sk + s, EMPTY64, k);
+        if (prev == EMPTY64 || prev == k) {
+            atomicMin(sw + s, wbits);
+            return true;
+        }
+        s = (s + 1) & (TILE_TABLE - 1);
+    }
+    return false;
+}
+
+// Insert one candidate per active lane, merging equal label pairs in the
+// warp first; the leader of each group inserts into the shared table (or,
+// if that is full, straight into the global table).
+__device__ __forceinline__ void warp_insert(const PairDev &P, bool have, pkey_t k,
+                                            unsigned wbits, pkey_t *sk, unsigned *sw,
                                             RunState *st) {
     const unsigned lane = threadIdx.x & 31;
     unsigned pend = __ballot_sync(0xffffffffu, have);
@@ -57,7 +79,8 @@ __device__ __forceinline__ void warp_insert(const PairDev &P, bool have,
         const bool mine = have && k == lk;
         const unsigned grp = __ballot_sync(0xffffffffu, mine);
         const unsigned wmin = __reduce_min_sync(0xffffffffu, mine ? wbits : 0xFFFFFFFFu);
-        if (lane == (unsigned)leader) table_insert(P, lk, wmin, st);
+        if (lane == (unsigned)leader && !smem_insert(sk, sw, lk, wmin))
+            table_insert(P, lk, wmin, st);
         pend &= ~grp;
         if (mine) have = false;
     }
@@ -67,10 +90,16 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(BatchArgs a) {
     RunState *st = a.state;
     if (get_status(st) != 0) return;
     __shared__ int s_pair, s_local;
+    __shared__ pkey_t sk[TILE_TABLE];
+    __shared__ unsigned sw[TILE_TABLE];
     for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
         if (threadIdx.x == 0) {
             s_pair = find_pair(a.tile_base, a.npairs, t);
             s_local = t - a.tile_base[s_pair];
+        }
+        for (int i = threadIdx.x; i < TILE_TABLE; i += blockDim.x) {
+            sk[i] = EMPTY64;
+            sw[i] = 0xFFFFFFFFu;
         }
         __syncthreads();
         const PairDev &P = a.pairs[s_pair];
@@ -118,9 +147,13 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(BatchArgs a) {
                         wb = __float_as_uint(w);
                     }
                 }
-                warp_insert(P, have, k, wb, st);
+                warp_insert(P, have, k, wb, sk, sw, st);
             }
         }
+        __syncthreads();
+        // flush the tile's unique edges to the pair's table
+        for (int i = threadIdx.x; i < TILE_TABLE; i += blockDim.x)
+            if (sk[i] != EMPTY64) table_insert(P, sk[i], sw[i], st);
         __syncthreads();
     }
     // duplicate source pixels: join an ownerless match to its pixel's owner
