@@ -192,6 +192,45 @@ def cpu_threads(args):
     return max(1, min(os.cpu_count() or 1, 16))
 
 
+def run_served(pairs, e2e_mpix_s, device, n_requests=256):
+    """Poisson stream of requests (the step's pairs, reused cyclically) at
+    60% of the end-to-end batched capacity, served with continuous batching
+    and, for comparison, one request at a time."""
+    import torch
+    from paper_1501_02565_gb300.serve import Request, Server, replay
+    rate = 0.6 * e2e_mpix_s * 1e6 / pairs[0].P              # requests / s
+    rng = np.random.default_rng(5)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    arrivals -= arrivals[0]
+    hostC = [torch.from_numpy(p.C).pin_memory() for p in pairs]
+    hostM = [torch.from_numpy(p.matches).pin_memory() for p in pairs]
+    # caller-owned pinned outputs, reused round-robin (more buffers than
+    # requests can be in flight: admitted + computing <= 3 batches)
+    nbuf = min(n_requests, 4 * len(pairs))
+    outs = [torch.empty((pairs[i % len(pairs)].H, pairs[i % len(pairs)].W, 2),
+                        dtype=torch.float32, pin_memory=True) for i in range(nbuf)]
+    out = []
+    for max_batch in (len(pairs), 1):
+        reqs = [Request(hostC[i % len(pairs)], hostM[i % len(pairs)], pairs[i % len(pairs)].K,
+                        pairs[i % len(pairs)].a, rid=i, out=outs[i % nbuf])
+                for i in range(n_requests)]
+        srv = Server(device, max_batch=max_batch).start()
+        # warm the loop and the pinned-memory cache
+        warm = [Request(hostC[i], hostM[i], pairs[i].K, pairs[i].a, rid=-1) for i in range(min(4, len(pairs)))]
+        for r in warm:
+            srv.submit(r)
+        for r in warm:
+            r.wait(timeout=120)
+        srv.completed.clear()
+        srv.batch_sizes.clear()
+        st = replay(srv, reqs, arrivals)
+        status = srv.stop()
+        st.update({"rate_req_s": rate, "max_batch": max_batch, "status": status,
+                   "unit": "Mpix/s"})
+        out.append(st)
+    return out[0], out[1]
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -322,6 +361,11 @@ def run_ours(args, rank, world, local_rank):
     lat = [a0.elapsed_time(a1) for a0, a1 in ev]
     plain_value = sum(p.P for p in pairs) / (tp0.elapsed_time(tp1) / 1e3) / 1e6
 
+    # ---- served: continuous batching vs one request at a time ------------
+    served = served_plain = None
+    if rank == 0 and world == 1:
+        served, served_plain = run_served(pairs, e2e_value, local_rank)
+
     # ---- roofline ----------------------------------------------------------
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -369,6 +413,8 @@ def run_ours(args, rank, world, local_rank):
                       "latency_ms_p50": float(np.percentile(lat, 50)),
                       "latency_ms_p99": float(np.percentile(lat, 99))},
             "batched_latency_ms": ms_total / args.steps,
+            "served": served,
+            "served_plain": served_plain,
             "relax_passes": passes,
             "edges_per_step": n_edges,
             "cpu_baseline": cpu,

@@ -1,0 +1,86 @@
+"""Continuous-batching server: every request's flow is bit-identical alone
+and in the mix, admission respects the HBM budget, requests that arrive while
+a batch runs join later batches."""
+
+import time
+
+import numpy as np
+import pytest
+
+from paper_1501_02565_gb300 import synth
+from paper_1501_02565_gb300.native import EpicInterp
+from paper_1501_02565_gb300.serve import Request, Server
+from helpers import random_small_case
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    reqs = []
+    for i in range(6):
+        p = synth.config_pair(1, i)
+        reqs.append(Request(p.C, p.matches, p.K, p.a, rid=len(reqs)))
+    for i in range(6):
+        C, M = random_small_case(700 + i, H=60 + 7 * i, W=90 + 11 * i, N=40 + 5 * i,
+                                 c_lo=0.01, c_hi=1.0)
+        reqs.append(Request(C, M, 8 + i, 1.0, rid=len(reqs)))
+    p = synth.config_pair(2, 0)
+    reqs.append(Request(p.C, p.matches, p.K, p.a, rid=len(reqs)))
+    return reqs
+
+
+def _alone(reqs):
+    import torch
+    eng = EpicInterp(0)
+    out = []
+    for r in reqs:
+        f = eng.run(torch.from_numpy(r.C).cuda(), torch.from_numpy(r.matches).cuda(), r.K, r.a)
+        eng.sync()
+        out.append(f.cpu().numpy())
+    eng.close()
+    return out
+
+
+def test_each_result_is_identical_alone_and_in_the_mix():
+    reqs = _requests()
+    ref = _alone(reqs)
+    srv = Server(0, max_batch=8).start()
+    # staggered arrivals: later requests arrive while earlier batches run
+    for i, r in enumerate(reqs):
+        srv.submit(r)
+        if i % 4 == 3:
+            time.sleep(0.002)
+    for r in reqs:
+        r.wait(timeout=60)
+    assert srv.stop() == 0
+    st = srv.stats()
+    print("\n[serving]", st)
+    assert st["requests"] == len(reqs)
+    assert max(srv.batch_sizes) > 1      # requests were batched together
+    for r, f in zip(reqs, ref):
+        assert np.array_equal(r.flow.numpy(), f), r.rid
+
+
+def test_admission_stays_within_the_hbm_budget():
+    reqs = _requests()[:8]
+    budget = 2 * max(r.device_bytes() for r in reqs)
+    srv = Server(0, max_batch=8, hbm_budget=budget).start()
+    for r in reqs:
+        srv.submit(r)
+    for r in reqs:
+        r.wait(timeout=60)
+    assert srv.stop() == 0
+    assert srv.max_in_use <= budget
+    assert len(srv.completed) == len(reqs)
+    assert srv.steps >= 3                 # only a few requests fit at a time
+
+
+def test_bad_request_is_refused_at_submission():
+    srv = Server(0, max_batch=2)
+    C = np.ones((10, 10), np.float32)
+    with pytest.raises(ValueError):
+        srv.submit(Request(C, np.array([[12, 1, 0, 0]], np.float32), 4, 1.0))
+    C[3, 3] = np.nan
+    with pytest.raises(ValueError):
+        srv.submit(Request(C, np.array([[1, 1, 0, 0]], np.float32), 4, 1.0))
+    srv.stop()
