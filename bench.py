@@ -62,10 +62,11 @@ def parse_args():
     return ap.parse_args()
 
 
-def make_pairs(n, rank):
+def make_pairs(n, rank, world=1):
     from paper_1501_02565_gb300 import synth
-    # distinct pairs per rank: pair index offset by rank * n
-    return [synth.config_pair(2, rank * n + i) for i in range(n)]
+    from paper_1501_02565_gb300.replicas import rank_pair_indices
+    # distinct pairs per rank
+    return [synth.config_pair(2, i) for i in rank_pair_indices(rank, max(world, rank + 1), n)]
 
 
 # ---------------------------------------------------------------------------
@@ -268,10 +269,11 @@ def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     from paper_1501_02565_gb300.native import EpicInterp
+    from paper_1501_02565_gb300.replicas import max_over_ranks, whole_job_rate
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    pairs = make_pairs(args.batch, rank)
+    pairs = make_pairs(args.batch, rank, world)
     B = len(pairs)
     eng = EpicInterp(local_rank, max_pairs=B)
     items = []
@@ -311,12 +313,9 @@ def run_ours(args, rank, world, local_rank):
     stage_ms, n_runs = eng.stage_times()
     eng.enable_stage_timing(False)
     eng.sync()
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev)
     px_rank = sum(p.P for p in pairs) * args.steps
-    value = px_rank * world / (ms_total / 1e3) / 1e6
+    value = whole_job_rate(px_rank, world, ms_total / 1e3) / 1e6
 
     # ---- end to end through the C ABI with pinned host buffers ------------
     host = []
@@ -333,11 +332,8 @@ def run_ours(args, rank, world, local_rank):
         eng.run_batch_host(host)
     t_e2e = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = px_rank * world / t_e2e / 1e6
+    t_e2e = max_over_ranks(t_e2e, dev)
+    e2e_value = whole_job_rate(px_rank, world, t_e2e) / 1e6
     # sanity: the host result equals the device-resident one
     assert torch.equal(host[0][4], items[0][4].cpu()), "host and device paths differ"
 
