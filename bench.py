@@ -356,6 +356,28 @@ def run_ours(args, rank, world, local_rank):
     eng.sync()
     lat = [a0.elapsed_time(a1) for a0, a1 in ev]
     plain_value = sum(p.P for p in pairs) / (tp0.elapsed_time(tp1) / 1e3) / 1e6
+    # the same one-pair path replayed from captured CUDA graphs
+    geng = EpicInterp(local_rank, use_graphs=1)
+    gs = torch.cuda.Stream(dev)
+    with torch.cuda.stream(gs):
+        for it in items[:4]:
+            geng.run_batch([it], stream=gs)
+        gs.synchronize()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in items]
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(gs)
+        for it, (a0, a1) in zip(items, gev):
+            a0.record(gs)
+            geng.run_batch([it], stream=gs)
+            a1.record(gs)
+        g1.record(gs)
+        gs.synchronize()
+    geng.sync()
+    glat = [a0.elapsed_time(a1) for a0, a1 in gev]
+    plain_graph_value = sum(p.P for p in pairs) / (g0.elapsed_time(g1) / 1e3) / 1e6
+    geng.close()
 
     # ---- served: continuous batching vs one request at a time ------------
     served = served_plain = None
@@ -408,6 +430,9 @@ def run_ours(args, rank, world, local_rank):
             "plain": {"value": plain_value, "unit": "Mpix/s",
                       "latency_ms_p50": float(np.percentile(lat, 50)),
                       "latency_ms_p99": float(np.percentile(lat, 99))},
+            "plain_graph": {"value": plain_graph_value, "unit": "Mpix/s",
+                            "latency_ms_p50": float(np.percentile(glat, 50)),
+                            "latency_ms_p99": float(np.percentile(glat, 99))},
             "batched_latency_ms": ms_total / args.steps,
             "served": served,
             "served_plain": served_plain,

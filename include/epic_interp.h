@@ -78,6 +78,11 @@ typedef struct {
                              relaxation pass (-1 = chosen per frame size) */
     int keep_intermediates; /* 1: keep K-NN lists for epic_interp_get_knn */
     int max_degree;       /* match-graph adjacency row capacity (default 32) */
+    int use_graphs;       /* 1: capture the launch sequence once per table
+                             slot and replay it as a CUDA graph (needs a
+                             non-default stream, K <= max_K and tiles no
+                             larger than the configured ones; otherwise the
+                             run uses plain launches) */
 } epic_config_t;
 
 /* One frame pair of a batch; pointers are device pointers. */

@@ -139,13 +139,19 @@ struct LaunchCfg {
     int smem_optin;  // max dynamic shared memory per CTA (opt-in)
     cudaStream_t stream;
 };
-cudaError_t launch_prepare(const BatchArgs &a, const LaunchCfg &lc);
-cudaError_t launch_dt(const BatchArgs &a, const LaunchCfg &lc, int max_tile_w,
-                      int max_tile_h, int max_apron, int *grid_used);
-cudaError_t launch_edges(const BatchArgs &a, const LaunchCfg &lc);
-cudaError_t launch_scatter(const BatchArgs &a, const LaunchCfg &lc);
-cudaError_t launch_knn_fit(const BatchArgs &a, const LaunchCfg &lc, int max_K);
-cudaError_t launch_writeout(const BatchArgs &a, const LaunchCfg &lc);
+// Launchers: `a` is the host copy of the launch arguments (used only for
+// launch-shape decisions), `dev` the same struct in device memory (the
+// kernels' only parameter, so a captured launch sequence can be replayed for
+// any batch whose table has been uploaded to the same address).
+cudaError_t launch_prepare(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
+cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                      int max_tile_w, int max_tile_h, int max_apron, bool fixed_grid,
+                      int *grid_used);
+cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
+cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
+cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                           int max_K);
+cudaError_t launch_writeout(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
 cudaError_t launch_split_keys(const PairDev *pair_host_copy, int *labels,
                               float *dist, cudaStream_t stream);
 cudaError_t launch_collect_edges(const PairDev *pair_host_copy, int *em,

@@ -23,6 +23,9 @@ using epic::PairDev;
 using epic::RunState;
 using epic::pkey_t;
 
+struct epic_interp;
+using Handle = epic_interp;
+
 struct epic_interp {
     int device = 0;
     int num_sms = 0;
@@ -33,11 +36,18 @@ struct epic_interp {
     RunState *state = nullptr;      // device
     RunState *state_host = nullptr; // pinned mirror for reads
     int *scratch_count = nullptr;   // device int for getters
-    char *table_dev = nullptr;
-    char *table_host = nullptr;     // pinned staging
+    // two batch-table slots used alternately: pinned staging, device copy,
+    // the event that marks the slot's last run finished, and (graph mode)
+    // the captured launch sequence that reads this slot
+    struct Slot {
+        char *dev = nullptr;
+        char *host = nullptr;
+        cudaEvent_t done = nullptr;
+        bool pending = false;
+        cudaGraphExec_t graph = nullptr;
+    } slot[2];
+    int next_slot = 0;
     size_t table_cap = 0;
-    cudaEvent_t table_ev = nullptr;
-    bool table_ev_pending = false;
     std::vector<PairDev> pairs;     // last run's descriptors
     cudaStream_t last_stream = nullptr;
     // device staging for epic_interp_run_host
@@ -197,21 +207,31 @@ int ensure_arena(epic_interp_t *h, size_t need) {
     return EPIC_OK;
 }
 
+void drop_graphs(epic_interp_t *h) {
+    for (auto &sl : h->slot) {
+        if (sl.graph) cudaGraphExecDestroy(sl.graph);
+        sl.graph = nullptr;
+    }
+}
+
 int ensure_table(epic_interp_t *h, size_t need) {
     if (need <= h->table_cap) return EPIC_OK;
     int rc = wait_last(h);
     if (rc) return rc;
-    if (h->table_dev) cudaFree(h->table_dev);
-    if (h->table_host) cudaFreeHost(h->table_host);
-    h->table_dev = nullptr;
-    h->table_host = nullptr;
-    h->table_cap = 0;
-    h->table_ev_pending = false;
+    drop_graphs(h);
     size_t sz = align_up(need * 2, 4096);
-    cudaError_t e = cudaMalloc(&h->table_dev, sz);
-    if (e != cudaSuccess) return cuda_fail(h, e, "table cudaMalloc");
-    e = cudaMallocHost(&h->table_host, sz);
-    if (e != cudaSuccess) return cuda_fail(h, e, "table cudaMallocHost");
+    for (auto &sl : h->slot) {
+        if (sl.done && sl.pending) cudaEventSynchronize(sl.done);
+        sl.pending = false;
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.host) cudaFreeHost(sl.host);
+        sl.dev = nullptr;
+        sl.host = nullptr;
+        cudaError_t e = cudaMalloc(&sl.dev, sz);
+        if (e != cudaSuccess) { h->table_cap = 0; return cuda_fail(h, e, "table cudaMalloc"); }
+        e = cudaMallocHost(&sl.host, sz);
+        if (e != cudaSuccess) { h->table_cap = 0; return cuda_fail(h, e, "table cudaMallocHost"); }
+    }
     h->table_cap = sz;
     return EPIC_OK;
 }
@@ -252,6 +272,7 @@ void epic_config_default(epic_config_t *c) {
     c->apron = -1;
     c->keep_intermediates = 0;
     c->max_degree = 32;
+    c->use_graphs = 0;
 }
 
 int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg) {
@@ -284,8 +305,10 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     cudaMemset(h->state, 0, sizeof(RunState) + 64);
     e = cudaMallocHost(&h->state_host, sizeof(RunState));
     if (e != cudaSuccess) { epic_interp_destroy(h); return EPIC_ERR_OOM; }
-    e = cudaEventCreateWithFlags(&h->table_ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) { epic_interp_destroy(h); return EPIC_ERR_CUDA; }
+    for (auto &sl : h->slot) {
+        e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) { epic_interp_destroy(h); return EPIC_ERR_CUDA; }
+    }
     // size the arena for the configured maxima
     epic_pair_desc_t d{};
     d.cost_map = reinterpret_cast<const float *>(16);
@@ -358,7 +381,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         }
         P[i].info = reinterpret_cast<int *>(b + L[i].info);
     }
-    // batch table: PairDev[n] then 5 prefix arrays of n+1 ints
+    // batch table: BatchArgs, PairDev[n], then 5 prefix arrays of n+1 ints
     std::vector<int> tile_base(n + 1), match_base(n + 1), chunk_base(n + 1),
         hash_base(n + 1), clear_base(n + 1);
     long long tt = 0, tm = 0, tc = 0, th = 0, tcl = 0;
@@ -382,31 +405,35 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     chunk_base[n] = (int)tc;
     hash_base[n] = (int)th;
     clear_base[n] = (int)tcl;
+    const size_t args_bytes = align_up(sizeof(BatchArgs), 256);
     const size_t pd_bytes = align_up(sizeof(PairDev) * n, 256);
     const size_t pre_bytes = sizeof(int) * (n + 1);
-    const size_t table_bytes = pd_bytes + 5 * align_up(pre_bytes, 256);
+    const size_t pre_stride = align_up(pre_bytes, 256);
+    const size_t table_bytes = args_bytes + pd_bytes + 5 * pre_stride;
     rc = ensure_table(h, table_bytes);
     if (rc) return rc;
-    if (h->table_ev_pending) {
-        e = cudaEventSynchronize(h->table_ev);  // staging reuse
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
-    }
-    char *hs = h->table_host;
-    memcpy(hs, P.data(), sizeof(PairDev) * n);
-    const int *pres[5] = {tile_base.data(), match_base.data(), chunk_base.data(),
-                          hash_base.data(), clear_base.data()};
-    for (int k = 0; k < 5; ++k)
-        memcpy(hs + pd_bytes + k * align_up(pre_bytes, 256), pres[k], pre_bytes);
-    e = cudaMemcpyAsync(h->table_dev, hs, table_bytes, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "table upload");
-    e = cudaEventRecord(h->table_ev, stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-    h->table_ev_pending = true;
 
+    // graph replay applies when the launch shapes chosen below do not depend
+    // on this batch: kernel sizes from the configured maxima
+    const int cfg_tw = c.tile_w > 0 ? c.tile_w : 64, cfg_th = c.tile_h > 0 ? c.tile_h : 32;
+    const int cfg_ap = c.apron >= 0 ? c.apron : 4;
+    const bool graph = c.use_graphs && stream != nullptr && !h->timing && max_K <= c.max_K &&
+                       max_tw <= cfg_tw && max_th <= cfg_th && max_ap <= cfg_ap;
+    const int knn_K = graph ? c.max_K : max_K;
+    const int dt_tw = graph ? cfg_tw : max_tw, dt_th = graph ? cfg_th : max_th;
+    const int dt_ap = graph ? cfg_ap : max_ap;
+
+    Handle::Slot &sl = h->slot[h->next_slot];
+    h->next_slot ^= 1;
+    if (sl.pending) {
+        e = cudaEventSynchronize(sl.done);  // the slot's previous run has finished
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+        sl.pending = false;
+    }
     BatchArgs a{};
-    a.pairs = reinterpret_cast<const PairDev *>(h->table_dev);
+    a.pairs = reinterpret_cast<const PairDev *>(sl.dev + args_bytes);
     auto pre_dev = [&](int k) {
-        return reinterpret_cast<const int *>(h->table_dev + pd_bytes + k * align_up(pre_bytes, 256));
+        return reinterpret_cast<const int *>(sl.dev + args_bytes + pd_bytes + k * pre_stride);
     };
     a.npairs = n;
     a.tile_base = pre_dev(0);
@@ -420,47 +447,86 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     a.total_hash = (int)th;
     a.total_clear = (int)tcl;
     a.max_degree = c.max_degree;
-    epic::knn_table_sizes(max_K, &a.knn_hs, &a.knn_fs);
-    a.knn_kmax = max_K;
+    epic::knn_table_sizes(knn_K, &a.knn_hs, &a.knn_fs);
+    a.knn_kmax = knn_K;
     a.max_passes = c.max_passes;
     a.weight_squared = c.weight_squared ? 1 : 0;
     a.fallback_eps = c.fallback_eps;
     a.state = h->state;
-    if (epic::knn_warps_per_cta(max_K, h->smem_optin) < 1)
+    if (epic::knn_warps_per_cta(knn_K, h->smem_optin) < 1)
         return fail(h, EPIC_ERR_INVALID, "K too large for the per-warp search tables");
-    if (epic::dt_smem_bytes(max_tw, max_th, max_ap) > (size_t)h->smem_optin)
+    if (epic::dt_smem_bytes(dt_tw, dt_th, dt_ap) > (size_t)h->smem_optin)
         return fail(h, EPIC_ERR_INVALID, "relaxation tile does not fit in shared memory");
 
+    char *hs = sl.host;
+    memcpy(hs, &a, sizeof(BatchArgs));
+    memcpy(hs + args_bytes, P.data(), sizeof(PairDev) * n);
+    const int *pres[5] = {tile_base.data(), match_base.data(), chunk_base.data(),
+                          hash_base.data(), clear_base.data()};
+    for (int k = 0; k < 5; ++k) memcpy(hs + args_bytes + pd_bytes + k * pre_stride, pres[k], pre_bytes);
+    const BatchArgs *dev_a = reinterpret_cast<const BatchArgs *>(sl.dev);
+
     epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
-    cudaEvent_t *ev = nullptr;
-    if (h->timing) {
-        size_t need = (size_t)(h->timed_runs + 1) * (NSTAGE + 1);
-        while (h->tev.size() < need) {
-            cudaEvent_t x;
-            if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
-            h->tev.push_back(x);
-        }
-        ev = &h->tev[(size_t)h->timed_runs * (NSTAGE + 1)];
-        h->timed_runs++;
-    }
-    auto mark = [&](int i) {
-        if (ev) cudaEventRecord(ev[i], stream);
+    auto enqueue = [&](cudaEvent_t *ev, size_t copy_bytes) -> cudaError_t {
+        auto mark = [&](int i) {
+            if (ev) cudaEventRecord(ev[i], stream);
+        };
+        cudaError_t r = cudaMemcpyAsync(sl.dev, sl.host, copy_bytes, cudaMemcpyHostToDevice, stream);
+        if (r) return r;
+        mark(0);
+        if ((r = epic::launch_prepare(a, dev_a, lc))) return r;
+        mark(1);
+        if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
+        mark(2);
+        if ((r = epic::launch_edges(a, dev_a, lc))) return r;
+        mark(3);
+        if ((r = epic::launch_scatter(a, dev_a, lc))) return r;
+        mark(4);
+        if ((r = epic::launch_knn_fit(a, dev_a, lc, knn_K))) return r;
+        mark(5);
+        if ((r = epic::launch_writeout(a, dev_a, lc))) return r;
+        mark(6);
+        return cudaSuccess;
     };
-    mark(0);
-    if ((e = epic::launch_prepare(a, lc)) != cudaSuccess) return cuda_fail(h, e, "prepare launch");
-    mark(1);
-    int grid = 0;
-    if ((e = epic::launch_dt(a, lc, max_tw, max_th, max_ap, &grid)) != cudaSuccess)
-        return cuda_fail(h, e, "relaxation launch");
-    mark(2);
-    if ((e = epic::launch_edges(a, lc)) != cudaSuccess) return cuda_fail(h, e, "edge launch");
-    mark(3);
-    if ((e = epic::launch_scatter(a, lc)) != cudaSuccess) return cuda_fail(h, e, "scatter launch");
-    mark(4);
-    if ((e = epic::launch_knn_fit(a, lc, max_K)) != cudaSuccess) return cuda_fail(h, e, "knn launch");
-    mark(5);
-    if ((e = epic::launch_writeout(a, lc)) != cudaSuccess) return cuda_fail(h, e, "write-out launch");
-    mark(6);
+    if (graph) {
+        if (!sl.graph) {
+            // capture the whole sequence once; the copy node uploads the
+            // slot's entire staging buffer, so any later batch that fits
+            // replays the same graph
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t le = enqueue(nullptr, h->table_cap);
+                e = cudaStreamEndCapture(stream, &g);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                sl.graph = nullptr;
+                return cuda_fail(h, e, "graph capture");
+            }
+        }
+        e = cudaGraphLaunch(sl.graph, stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    } else {
+        cudaEvent_t *ev = nullptr;
+        if (h->timing) {
+            size_t need = (size_t)(h->timed_runs + 1) * (NSTAGE + 1);
+            while (h->tev.size() < need) {
+                cudaEvent_t x;
+                if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+                h->tev.push_back(x);
+            }
+            ev = &h->tev[(size_t)h->timed_runs * (NSTAGE + 1)];
+            h->timed_runs++;
+        }
+        e = enqueue(ev, table_bytes);
+        if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+    }
+    e = cudaEventRecord(sl.done, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    sl.pending = true;
     h->pairs = P;
     h->last_stream = stream;
     return EPIC_OK;
@@ -696,9 +762,12 @@ void epic_interp_destroy(epic_interp_t *h) {
     if (h->arena) cudaFree(h->arena);
     if (h->state) cudaFree(h->state);
     if (h->state_host) cudaFreeHost(h->state_host);
-    if (h->table_dev) cudaFree(h->table_dev);
-    if (h->table_host) cudaFreeHost(h->table_host);
-    if (h->table_ev) cudaEventDestroy(h->table_ev);
+    drop_graphs(h);
+    for (auto &sl : h->slot) {
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
     if (h->io_C) cudaFree(h->io_C);
     if (h->io_M) cudaFree(h->io_M);
     if (h->io_F) cudaFree(h->io_F);

@@ -44,7 +44,8 @@ constexpr size_t OFF_INFO = align256(OFF_WMIN + sizeof(unsigned) * NA_MAX_MATCHE
 constexpr size_t OFF_STATE = align256(OFF_INFO + 4 * sizeof(int));
 constexpr size_t OFF_PAIR = align256(OFF_STATE + sizeof(epic::RunState));
 constexpr size_t OFF_PREFIX = align256(OFF_PAIR + sizeof(epic::PairDev));
-constexpr size_t NA_SCRATCH_BYTES = align256(OFF_PREFIX + 5 * 2 * sizeof(int));
+constexpr size_t OFF_ARGS = align256(OFF_PREFIX + 5 * 2 * sizeof(int));
+constexpr size_t NA_SCRATCH_BYTES = align256(OFF_ARGS + sizeof(epic::BatchArgs));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
 
@@ -146,9 +147,13 @@ extern "C" int epic_geodesic_labels_noalloc(const float *cost_map, const float *
     a.weight_squared = 1;
     a.fallback_eps = 1e-10f;
     a.state = state;
+    const epic::BatchArgs *dev_a = reinterpret_cast<const epic::BatchArgs *>(base + OFF_ARGS);
+    if (cudaMemcpyAsync(base + OFF_ARGS, &a, sizeof(a), cudaMemcpyHostToDevice, stream))
+        return EPIC_ERR_CUDA;
     epic::LaunchCfg lc{num_sms, smem_optin, stream};
-    if (epic::launch_prepare(a, lc) != cudaSuccess ||
-        epic::launch_dt(a, lc, NA_TILE_W, NA_TILE_H, NA_APRON, nullptr) != cudaSuccess ||
+    if (epic::launch_prepare(a, dev_a, lc) != cudaSuccess ||
+        epic::launch_dt(a, dev_a, lc, NA_TILE_W, NA_TILE_H, NA_APRON, false, nullptr) !=
+            cudaSuccess ||
         epic::launch_split_keys(&Pd, labels_out, dist_out, stream) != cudaSuccess)
         return EPIC_ERR_CUDA;
     int status = 0;

@@ -52,7 +52,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Sense-free generation barrier over all CTAs of a cooperative launch.  The
 // wait gives up after BARRIER_LIMIT_NS (or as soon as another CTA has given
 // up) and reports EPIC_ERR_TIMEOUT instead of spinning forever.
-__device__ bool grid_sync(RunState *st) {
+__device__ bool grid_sync(RunState *st, unsigned nblocks) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -61,7 +61,7 @@ __device__ bool grid_sync(RunState *st) {
         unsigned g = ld_acquire(&b->gen);
         __threadfence();
         unsigned arrived = atomicAdd(&b->count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == nblocks - 1) {
             b->count = 0;
             __threadfence();
             st_release(&b->gen, g + 1);
@@ -327,14 +327,19 @@ __device__ __forceinline__ bool neighbour_changed(const PairDev &P, int tx, int 
     return false;
 }
 
-__global__ void __launch_bounds__(DT_THREADS) dt_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
     extern __shared__ __align__(16) unsigned char smem[];
     RunState *st = a.state;
     if (get_status(st) != 0) return;  // same decision in every CTA
+    // a launch replayed for a smaller batch may have more CTAs than tiles:
+    // the extra CTAs leave at once and the barrier counts only the others
+    const unsigned nblocks = min(gridDim.x, (unsigned)a.total_tiles);
+    if (blockIdx.x >= nblocks) return;
     __shared__ int s_pair, s_local;
 
     // phase 1
-    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+    for (int t = blockIdx.x; t < a.total_tiles; t += nblocks) {
         if (threadIdx.x == 0) {
             s_pair = find_pair(a.tile_base, a.npairs, t);
             s_local = t - a.tile_base[s_pair];
@@ -346,7 +351,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(BatchArgs a) {
         float *h = reinterpret_cast<float *>(smem + sizeof(pkey_t) * g.RH * g.P);
         solve_fresh(P, s_local % P.tiles_x, s_local / P.tiles_x, K, h, st);
     }
-    if (!grid_sync(st)) return;
+    if (!grid_sync(st, nblocks)) return;
 
     // phase 2
     for (int pass = 0;; ++pass) {
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(BatchArgs a) {
             return;
         }
         unsigned *cnt = &st->changed[pass % 3];
-        for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+        for (int t = blockIdx.x; t < a.total_tiles; t += nblocks) {
             if (threadIdx.x == 0) {
                 s_pair = find_pair(a.tile_base, a.npairs, t);
                 s_local = t - a.tile_base[s_pair];
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(BatchArgs a) {
             }
             __syncthreads();
         }
-        if (!grid_sync(st)) return;
+        if (!grid_sync(st, nblocks)) return;
         const unsigned dirty = ld_acquire(cnt);
         // the counter of pass-1 (== pass+2 mod 3) was read by every CTA
         // before this barrier; clear it for pass+2
@@ -398,8 +403,9 @@ size_t dt_smem_bytes(int tile_w, int tile_h, int apron) {
     return (size_t)RH * P * (sizeof(pkey_t) + sizeof(float));
 }
 
-cudaError_t launch_dt(const BatchArgs &a, const LaunchCfg &lc, int max_tile_w,
-                      int max_tile_h, int max_apron, int *grid_used) {
+cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                      int max_tile_w, int max_tile_h, int max_apron, bool fixed_grid,
+                      int *grid_used) {
     size_t smem = dt_smem_bytes(max_tile_w, max_tile_h, max_apron);
     cudaError_t e = cudaFuncSetAttribute(
         dt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -410,7 +416,7 @@ cudaError_t launch_dt(const BatchArgs &a, const LaunchCfg &lc, int max_tile_w,
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int grid = per_sm * lc.num_sms;
-    if (grid > a.total_tiles) grid = a.total_tiles;
+    if (!fixed_grid && grid > a.total_tiles) grid = a.total_tiles;
     if (grid < 1) grid = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -423,7 +429,7 @@ cudaError_t launch_dt(const BatchArgs &a, const LaunchCfg &lc, int max_tile_w,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (grid_used) *grid_used = grid;
-    return cudaLaunchKernelEx(&cfg, dt_kernel, a);
+    return cudaLaunchKernelEx(&cfg, dt_kernel, dev);
 }
 
 }  // namespace epic

@@ -86,7 +86,8 @@ __device__ __forceinline__ void warp_insert(const PairDev &P, bool have, pkey_t 
     }
 }
 
-__global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
     RunState *st = a.state;
     if (get_status(st) != 0) return;
     __shared__ int s_pair, s_local;
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(BatchArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) scatter_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256) scatter_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
     RunState *st = a.state;
     if (get_status(st) != 0) return;
     const int md = a.max_degree;
@@ -227,13 +229,15 @@ __global__ void collect_kernel(const pkey_t *hkeys, const unsigned *hw, int cap_
 
 }  // namespace
 
-cudaError_t launch_edges(const BatchArgs &a, const LaunchCfg &lc) {
-    edges_kernel<<<lc.num_sms * 8, EDGE_THREADS, 0, lc.stream>>>(a);
+cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
+    (void)a;
+    edges_kernel<<<lc.num_sms * 8, EDGE_THREADS, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const BatchArgs &a, const LaunchCfg &lc) {
-    scatter_kernel<<<lc.num_sms * 4, 256, 0, lc.stream>>>(a);
+cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
+    (void)a;
+    scatter_kernel<<<lc.num_sms * 4, 256, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

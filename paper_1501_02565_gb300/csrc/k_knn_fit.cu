@@ -134,7 +134,8 @@ __device__ void sort_settled(unsigned *rn, float *rd, int n, pkey_t *scratch, in
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
     const int warps = blockDim.x >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     RunState *st = a.state;
@@ -518,7 +519,9 @@ int knn_warps_per_cta(int max_K, int smem_limit) {
     return w > KNN_WARPS ? KNN_WARPS : w;
 }
 
-cudaError_t launch_knn_fit(const BatchArgs &a, const LaunchCfg &lc, int max_K) {
+cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                           int max_K) {
+    (void)a;
     int warps = knn_warps_per_cta(max_K, lc.smem_optin);
     if (warps < 1) return cudaErrorInvalidValue;
     size_t smem = knn_smem_per_warp(max_K) * warps;
@@ -530,7 +533,7 @@ cudaError_t launch_knn_fit(const BatchArgs &a, const LaunchCfg &lc, int max_K) {
                                                       warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    knn_fit_kernel<<<per_sm * lc.num_sms, warps * 32, smem, lc.stream>>>(a);
+    knn_fit_kernel<<<per_sm * lc.num_sms, warps * 32, smem, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

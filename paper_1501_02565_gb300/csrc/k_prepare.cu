@@ -63,7 +63,8 @@ __device__ __forceinline__ bool seed_pixel(float4 mt, int H, int W, int *px,
     return true;
 }
 
-__global__ void __launch_bounds__(1024) prepare_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
     RunState *st = a.state;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // Nothing else touches these until the relaxation kernel starts,
@@ -124,9 +125,10 @@ __global__ void __launch_bounds__(1024) prepare_kernel(BatchArgs a) {
 
 }  // namespace
 
-cudaError_t launch_prepare(const BatchArgs &a, const LaunchCfg &lc) {
+cudaError_t launch_prepare(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
+    (void)a;
     int grid = lc.num_sms * 2;
-    prepare_kernel<<<grid, 1024, 0, lc.stream>>>(a);
+    prepare_kernel<<<grid, 1024, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,8 @@ __device__ __forceinline__ float2 apply(const float4 *models, unsigned m, int n,
 
 __device__ __forceinline__ void st_stream(float4 *p, float4 v) { __stcs(p, v); }
 
-__global__ void __launch_bounds__(256) writeout_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256) writeout_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
     RunState *st = a.state;
     if (get_status(st) != 0) return;
     constexpr int PER_THREAD = WRITEOUT_CHUNK / 256;
@@ -65,8 +66,9 @@ __global__ void __launch_bounds__(256) writeout_kernel(BatchArgs a) {
 
 }  // namespace
 
-cudaError_t launch_writeout(const BatchArgs &a, const LaunchCfg &lc) {
-    writeout_kernel<<<lc.num_sms * 8, 256, 0, lc.stream>>>(a);
+cudaError_t launch_writeout(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
+    (void)a;
+    writeout_kernel<<<lc.num_sms * 8, 256, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

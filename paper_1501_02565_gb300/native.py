@@ -49,7 +49,7 @@ class epic_config_t(ctypes.Structure):
         ("weight_squared", ctypes.c_int), ("fallback_eps", ctypes.c_float),
         ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
         ("apron", ctypes.c_int), ("keep_intermediates", ctypes.c_int),
-        ("max_degree", ctypes.c_int),
+        ("max_degree", ctypes.c_int), ("use_graphs", ctypes.c_int),
     ]
 
 

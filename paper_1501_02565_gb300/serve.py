@@ -98,6 +98,7 @@ class Server:
             hbm_budget = max(free - reserve_bytes, 256 << 20)
         self.budget = int(hbm_budget)
         self.in_use = 0
+        engine_cfg.setdefault("use_graphs", 1)
         self.engine = EpicInterp(device, max_pairs=max_batch, **engine_cfg)
         self.compute = torch.cuda.Stream(device)
         self.copy = torch.cuda.Stream(device)

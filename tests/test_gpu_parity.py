@@ -105,3 +105,33 @@ def test_full_size_workloads_full_parity(config):
     g, ref, rep = full_parity(p)
     _print(f"config{config}", rep)
     assert rep["flow_excluded_px"] < 0.02 * p.P
+
+
+def test_graph_replay_matches_plain_launches():
+    # one captured sequence per table slot replays any batch composition
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    pairs = [synth.config_pair(1, i) for i in range(3)]
+    C, M = random_small_case(900, H=70, W=120, N=90, c_lo=0.01, c_hi=1.0)
+    extra = (C, M, 12, 1.0)
+    items = [(p.C, p.matches, p.K, p.a) for p in pairs] + [extra]
+    dev = [(torch.from_numpy(c).cuda(), torch.from_numpy(m).cuda(), k, a) for c, m, k, a in items]
+    s = torch.cuda.Stream()
+    eng_g = EpicInterp(0, use_graphs=1, max_pairs=4)
+    eng_p = EpicInterp(0, max_pairs=4)
+    compositions = [[0, 1], [1, 2, 3], [3], [0, 1], [2, 0, 3, 1], [1, 2, 3]]
+    for comp in compositions:
+        outs = []
+        for eng in (eng_g, eng_p):
+            batch = [(dev[i][0], dev[i][1], dev[i][2], dev[i][3],
+                      torch.empty((items[i][0].shape[0], items[i][0].shape[1], 2),
+                                  device="cuda")) for i in comp]
+            with torch.cuda.stream(s):
+                eng.run_batch(batch, stream=s)
+            s.synchronize()
+            eng.sync()
+            outs.append([b[4].cpu().numpy() for b in batch])
+        for fg, fp in zip(*outs):
+            assert np.array_equal(fg, fp)
+    eng_g.close()
+    eng_p.close()
