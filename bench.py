@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--cpu-threads", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
     return ap.parse_args()
 
 
@@ -281,6 +282,12 @@ def run_ours(args, rank, world, local_rank):
         items.append((torch.from_numpy(p.C).to(dev), torch.from_numpy(p.matches).to(dev),
                       p.K, p.a, torch.empty((p.H, p.W, 2), dtype=torch.float32, device=dev)))
     step_bytes = sum(it[0].numel() * 4 + it[4].numel() * 4 + it[1].numel() * 4 for it in items)
+    # relaxation tile picked by the autotuner on this step's own batch
+    tile_rules, tune_report = [], None
+    if not args.no_tune:
+        from paper_1501_02565_gb300 import tune
+        tile_rules, tune_report = tune.autotune(pairs, device=local_rank, reps=2)
+        eng.set_tile_rules(tile_rules)
 
     def barrier():
         if world > 1:
@@ -358,6 +365,8 @@ def run_ours(args, rank, world, local_rank):
     plain_value = sum(p.P for p in pairs) / (tp0.elapsed_time(tp1) / 1e3) / 1e6
     # the same one-pair path replayed from captured CUDA graphs
     geng = EpicInterp(local_rank, use_graphs=1)
+    if tile_rules:
+        geng.set_tile_rules(tile_rules)
     gs = torch.cuda.Stream(dev)
     with torch.cuda.stream(gs):
         for it in items[:4]:
@@ -421,6 +430,7 @@ def run_ours(args, rank, world, local_rank):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"Sintel-shaped pairs {W}x{H}, N={N_MATCH}, K={K_NN}, a={A_KERNEL}",
                        "pairs_per_step": B, "parallelism": f"replicas{world}",
+                       "tile_rules": [list(r) for r in tile_rules],
                        "l2": f"inputs larger than L2 ({step_bytes / 1e6:.0f} MB of inputs and outputs per step)"},
             "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -437,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
             "served": served,
             "served_plain": served_plain,
             "relax_passes": passes,
+            "tune": tune_report,
             "edges_per_step": n_edges,
             "cpu_baseline": cpu,
             "clocks": clk,

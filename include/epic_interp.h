@@ -94,6 +94,13 @@ typedef struct {
     float *flow_out;        /* [H*W*2] */
 } epic_pair_desc_t;
 
+/* A relaxation tile rule: frames of at most max_pixels pixels use tiles of
+ * tile_w x tile_h with the given first-pass apron. */
+typedef struct {
+    long long max_pixels;
+    int tile_w, tile_h, apron;
+} epic_tile_rule_t;
+
 /* Fill *cfg with defaults (sizes for a 1024x436 frame, 5000 matches,
  * K = 100, squared weights, eps = 1e-10, max_passes = 4096). */
 void epic_config_default(epic_config_t *cfg);
@@ -162,6 +169,14 @@ int epic_interp_get_models(epic_interp_t *h, int pair, float *models,
 /* Number of relaxation verification passes the last run needed for its
  * whole batch (waits for the stream). */
 int epic_interp_get_passes(epic_interp_t *h, int *passes);
+
+/* Install relaxation tile rules (replacing any earlier ones; n = 0 clears
+ * them).  A pair uses the first rule whose max_pixels >= H*W, else the
+ * configured tile.  Tile sides must be in [8, 256], apron < min(side) and
+ * <= 64.  Rules only change speed, never results (every tiling reaches the
+ * same fixed point).  The rules are copied. */
+int epic_interp_set_tile_rules(epic_interp_t *h, const epic_tile_rule_t *rules,
+                               int n);
 
 /* Stage timing.  While enabled, every run records CUDA events on its
  * stream between its six kernels (prepare, relaxation, edges, scatter,

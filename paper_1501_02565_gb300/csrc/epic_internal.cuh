@@ -16,37 +16,65 @@
 
 namespace epic {
 
-// Packed (distance, label) key of the geodesic relaxation.  The high word is
-// the IEEE-754 bit pattern of a non-negative float32 distance, whose unsigned
-// order equals numeric order; the low word is the match index.  Comparing
-// keys as uint64 therefore compares (D, L) lexicographically, which realises
+// Packed (distance, label) key of the geodesic relaxation.
+//   bit 63       : unreached flag
+//   bits 62..22  : D in fixed point, units of 2^-32 (D < 2^41 units = 512)
+//   bits 21..0   : match index (label), 0x3FFFFF = none
+// Comparing keys as uint64 compares (D, L) lexicographically, which realises
 // "nearest match, ties to the smallest index" (Sec. 3.4), and a 64-bit access
-// moves both halves at once so no reader ever sees a torn pair.
+// moves both halves at once so no reader ever sees a torn pair.  Path sums
+// are integers, hence exact and associative: the minimum key over all paths
+// is then the unique fixed point of the relaxation whatever order the steps
+// run in (with rounded float sums, a step absorbed by rounding can leave a
+// label that depends on the order).  A step adds (w << 22) to the
+// neighbour's key, carrying its label along.
 typedef unsigned long long pkey_t;
-constexpr pkey_t KEY_INF = 0x7F800000FFFFFFFFull;  // (+inf, no label)
+constexpr int LABEL_BITS = 22;
+constexpr unsigned LABEL_NONE = (1u << LABEL_BITS) - 1u;
+constexpr pkey_t KEY_INF = 0x8000000000000000ull | LABEL_NONE;
 constexpr unsigned EMPTY32 = 0xFFFFFFFFu;
 constexpr pkey_t EMPTY64 = 0xFFFFFFFFFFFFFFFFull;
+constexpr int MAX_LABELS = (1 << LABEL_BITS) - 2;    // largest N
+constexpr float UNITS_PER_ONE = 4294967296.0f;        // 2^32
+constexpr float ONE_PER_UNIT = 2.3283064365386963e-10f;  // 2^-32
 
-__device__ __forceinline__ pkey_t make_key(float d, unsigned label) {
-    return ((pkey_t)__float_as_uint(d) << 32) | label;
+__device__ __forceinline__ pkey_t make_key(unsigned long long d_units, unsigned label) {
+    return (d_units << LABEL_BITS) | label;
 }
+__device__ __forceinline__ unsigned long long key_dunits(pkey_t k) { return k >> LABEL_BITS; }
+__device__ __forceinline__ bool key_reached(pkey_t k) { return !(k >> 63); }
 __device__ __forceinline__ float key_dist(pkey_t k) {
-    return __uint_as_float((unsigned)(k >> 32));
+    return key_reached(k) ? __fmul_rn(__ull2float_rn(key_dunits(k)), ONE_PER_UNIT)
+                          : __int_as_float(0x7f800000);
 }
-__device__ __forceinline__ unsigned key_label(pkey_t k) { return (unsigned)k; }
+__device__ __forceinline__ unsigned key_label(pkey_t k) { return (unsigned)k & LABEL_NONE; }
 
-// Step cost of Eq. 3 between 8-neighbours p, q, from half-costs
-// h = C/2: |p-q| (C(p)+C(q))/2 = |p-q| (h(p)+h(q)).  Multiplying by 1/2 is
-// exact in float32, so h(p)+h(q) == (C(p)+C(q))/2 bit for bit.  Explicit
-// round-to-nearest intrinsics keep the compiler from contracting the
-// product into a later addition, so every kernel evaluates the identical
-// float32 value for the same step.
-constexpr float SQRT2_F = 1.41421356237309515f;
-__device__ __forceinline__ float step_axis(float hp, float hq) {
-    return __fadd_rn(hp, hq);
+// Step cost of Eq. 3 between 8-neighbours p, q in fixed-point units:
+// |p-q| (C(p)+C(q))/2 = |p-q| (h(p)+h(q)) with half-costs h = C/2 held as
+// integers h = rint(C 2^31) (units of 2^-32; 0 <= C < 2).  An axis step is
+// the exact sum of the two halves; a diagonal step multiplies that sum by
+// sqrt 2 in 2.30 fixed point, rounded to the nearest unit.  Both are
+// symmetric in p, q and every kernel forms the identical integer.
+constexpr float C_MAX = 2.0f;  // costs are edge strengths in [0, 2)
+constexpr unsigned long long SQRT2_Q30 = 1518500250ull;  // rint(sqrt(2) 2^30)
+__device__ __forceinline__ unsigned long long step_axis(unsigned hp, unsigned hq) {
+    return (unsigned long long)hp + hq;
 }
-__device__ __forceinline__ float step_diag(float hp, float hq) {
-    return __fmul_rn(SQRT2_F, __fadd_rn(hp, hq));
+__device__ __forceinline__ unsigned long long step_diag(unsigned hp, unsigned hq) {
+    return (((unsigned long long)hp + hq) * SQRT2_Q30 + (1ull << 29)) >> 30;
+}
+// h = rint(C 2^31) for 0 <= C < C_MAX, else 0 and *bad set.
+__device__ __forceinline__ unsigned half_cost(float c, bool *bad) {
+    if (!(c >= 0.f && c < C_MAX)) {
+        *bad = true;
+        return 0u;
+    }
+    return __float2uint_rn(__fmul_rn(c, 2147483648.0f));
+}
+// Candidate key at p from neighbour key kq over a step of w units; an
+// unreached neighbour offers nothing (its flag bit makes the sum >= KEY_INF).
+__device__ __forceinline__ pkey_t step_key(pkey_t kq, unsigned long long w) {
+    return kq + (w << LABEL_BITS);
 }
 
 // Per-pair state; every pointer is a device address.

@@ -54,6 +54,7 @@ struct epic_interp {
     float *io_C = nullptr, *io_M = nullptr, *io_F = nullptr;
     size_t io_C_n = 0, io_M_n = 0, io_F_n = 0;
     // stage timing: NSTAGE+1 events per timed run, reused across enablements
+    std::vector<epic_tile_rule_t> rules;  // relaxation tile by frame size
     bool timing = false;
     std::vector<cudaEvent_t> tev;
     int timed_runs = 0;
@@ -96,16 +97,22 @@ int next_pow2(long long x) {
     return (int)p;
 }
 
-// Tile shape for the relaxation of an H x W frame.
-void choose_tiles(const epic_config_t &c, int H, int W, int *tw, int *th, int *ap) {
-    int w = c.tile_w > 0 ? c.tile_w : 64;
-    int t = c.tile_h > 0 ? c.tile_h : 32;
-    int a = c.apron >= 0 ? c.apron : 4;
-    (void)H;
-    (void)W;
-    *tw = w;
-    *th = t;
-    *ap = a;
+// Tile shape for the relaxation of an H x W frame: the first installed rule
+// covering the frame, else the configured tile (64 x 32, apron 4 by default).
+void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &rules, int H,
+                  int W, int *tw, int *th, int *ap) {
+    const long long P = (long long)H * W;
+    for (const auto &r : rules) {
+        if (P <= r.max_pixels) {
+            *tw = r.tile_w;
+            *th = r.tile_h;
+            *ap = r.apron;
+            return;
+        }
+    }
+    *tw = c.tile_w > 0 ? c.tile_w : 64;
+    *th = c.tile_h > 0 ? c.tile_h : 32;
+    *ap = c.apron >= 0 ? c.apron : 4;
 }
 
 struct Layout {
@@ -143,7 +150,8 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep) {
     return L;
 }
 
-PairDev make_pair_desc(const epic_config_t &c, const epic_pair_desc_t &d) {
+PairDev make_pair_desc(const epic_config_t &c, const std::vector<epic_tile_rule_t> &rules,
+                       const epic_pair_desc_t &d) {
     PairDev P{};
     P.C = d.cost_map;
     P.matches = reinterpret_cast<const float4 *>(d.matches);
@@ -153,7 +161,7 @@ PairDev make_pair_desc(const epic_config_t &c, const epic_pair_desc_t &d) {
     P.N = d.N;
     P.K = std::min(d.K, d.N);
     P.a = d.a;
-    choose_tiles(c, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron);
+    choose_tiles(c, rules, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron);
     P.tiles_x = (d.W + P.tile_w - 1) / P.tile_w;
     P.tiles_y = (d.H + P.tile_h - 1) / P.tile_h;
     P.hash_cap = std::max(1024, next_pow2(8LL * d.N));
@@ -173,7 +181,7 @@ int validate(epic_interp_t *h, const epic_pair_desc_t &d, int i) {
                  i, d.H, d.W, d.N, d.K, (double)d.a);
         return fail(h, EPIC_ERR_INVALID, buf);
     }
-    if ((long long)d.H * d.W > (1LL << 30) || d.N > (1 << 26)) {
+    if ((long long)d.H * d.W > (1LL << 30) || d.N > epic::MAX_LABELS) {
         snprintf(buf, sizeof buf, "pair %d: frame or match count too large", i);
         return fail(h, EPIC_ERR_INVALID, buf);
     }
@@ -319,7 +327,7 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     d.N = std::max(1, c.max_N);
     d.K = std::max(1, c.max_K);
     d.a = 1.f;
-    PairDev P = make_pair_desc(c, d);
+    PairDev P = make_pair_desc(c, h->rules, d);
     size_t per = layout_pair(0, P, c.max_degree, c.keep_intermediates != 0).end;
     int rc = ensure_arena(h, per * (size_t)c.max_pairs);
     if (rc) { epic_interp_destroy(h); return rc; }
@@ -347,7 +355,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     size_t off = 0;
     int max_tw = 8, max_th = 8, max_ap = 0, max_K = 1;
     for (int i = 0; i < n; ++i) {
-        P[i] = make_pair_desc(c, descs[i]);
+        P[i] = make_pair_desc(c, h->rules, descs[i]);
         if (P[i].apron + 1 > std::min(P[i].tile_w, P[i].tile_h) || P[i].apron > 64)
             return fail(h, EPIC_ERR_INVALID,
                         "apron must be smaller than the tile sides and at most 64");
@@ -415,8 +423,15 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
 
     // graph replay applies when the launch shapes chosen below do not depend
     // on this batch: kernel sizes from the configured maxima
-    const int cfg_tw = c.tile_w > 0 ? c.tile_w : 64, cfg_th = c.tile_h > 0 ? c.tile_h : 32;
-    const int cfg_ap = c.apron >= 0 ? c.apron : 4;
+    // graph launches size the relaxation's shared memory for the largest
+    // tile the handle can pick (configured tile or any rule)
+    int cfg_tw = c.tile_w > 0 ? c.tile_w : 64, cfg_th = c.tile_h > 0 ? c.tile_h : 32;
+    int cfg_ap = c.apron >= 0 ? c.apron : 4;
+    for (const auto &r : h->rules) {
+        cfg_tw = std::max(cfg_tw, r.tile_w);
+        cfg_th = std::max(cfg_th, r.tile_h);
+        cfg_ap = std::max(cfg_ap, r.apron);
+    }
     const bool graph = c.use_graphs && stream != nullptr && !h->timing && max_K <= c.max_K &&
                        max_tw <= cfg_tw && max_th <= cfg_th && max_ap <= cfg_ap;
     const int knn_K = graph ? c.max_K : max_K;
@@ -711,6 +726,25 @@ int epic_interp_get_passes(epic_interp_t *h, int *passes) {
     int rc = read_state(h);
     if (rc) return rc;
     *passes = h->state_host->passes;
+    return EPIC_OK;
+}
+
+int epic_interp_set_tile_rules(epic_interp_t *h, const epic_tile_rule_t *rules, int n) {
+    if (!h) return EPIC_ERR_INVALID;
+    if (n < 0 || (n > 0 && !rules)) return fail(h, EPIC_ERR_INVALID, "bad rule list");
+    std::vector<epic_tile_rule_t> v(rules, rules + n);
+    for (const auto &r : v) {
+        if (r.tile_w < 8 || r.tile_h < 8 || r.tile_w > 256 || r.tile_h > 256 || r.apron < 0 ||
+            r.apron > 64 || r.apron + 1 > std::min(r.tile_w, r.tile_h) || r.max_pixels < 1)
+            return fail(h, EPIC_ERR_INVALID, "tile rule out of range");
+        if (epic::dt_smem_bytes(r.tile_w, r.tile_h, r.apron) > (size_t)h->smem_optin)
+            return fail(h, EPIC_ERR_INVALID, "tile rule does not fit in shared memory");
+    }
+    // graphs were captured for the old maximum tile
+    int rc = wait_last(h);
+    if (rc) return rc;
+    drop_graphs(h);
+    h->rules = v;
     return EPIC_OK;
 }
 

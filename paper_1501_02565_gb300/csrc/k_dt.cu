@@ -2,13 +2,12 @@
 // Voronoi diagram"; D_G of Eq. 3 on the 8-connected grid).
 //
 // Each pixel's packed key (D, L) is the minimum over all matches m and all
-// grid paths from p_m of (path cost, m), where the path cost is accumulated
-// in float32 from the seed outwards, one step at a time:
-//     D <- D + |p-q| (C(p)+C(q))/2.
-// Any order of such relaxation steps that ends when no step improves any key
-// reaches the same keys bit for bit, because every step is monotone in its
-// input and each key is the exact float32 fold along some path.  The kernel
-// exploits that freedom:
+// grid paths from p_m of (path cost, m), with path costs summed exactly in
+// fixed point (units of 2^-32) from the steps |p-q| (C(p)+C(q))/2.  Any
+// order of relaxation steps that ends when no step improves any key reaches
+// these keys bit for bit: with exact sums every prefix of an optimal path is
+// optimal, so a state that no single step improves is the minimum.  The
+// kernel exploits that freedom:
 //
 //   phase 1  every tile is solved alone in shared memory on its region
 //            (tile + apron + 1-px ring), with the seeds of that region, and
@@ -112,20 +111,16 @@ __device__ __forceinline__ Region make_region(const PairDev &P, int gx0,
 
 // Best of the current key and the three candidates reached from the
 // neighbours at offsets ax (axis step) and d1, d2 (diagonal steps).
-__device__ __forceinline__ int relax3(pkey_t *K, const float *h, int idx,
+__device__ __forceinline__ int relax3(pkey_t *K, const unsigned *h, int idx,
                                       int ax, int d1, int d2) {
     const pkey_t kp = K[idx];
-    const float hp = h[idx];
+    const unsigned hp = h[idx];
     pkey_t best = kp;
-    pkey_t kq = K[idx + ax];
-    pkey_t c = make_key(__fadd_rn(key_dist(kq), step_axis(hp, h[idx + ax])),
-                       key_label(kq));
+    pkey_t c = step_key(K[idx + ax], step_axis(hp, h[idx + ax]));
     best = c < best ? c : best;
-    kq = K[idx + d1];
-    c = make_key(__fadd_rn(key_dist(kq), step_diag(hp, h[idx + d1])), key_label(kq));
+    c = step_key(K[idx + d1], step_diag(hp, h[idx + d1]));
     best = c < best ? c : best;
-    kq = K[idx + d2];
-    c = make_key(__fadd_rn(key_dist(kq), step_diag(hp, h[idx + d2])), key_label(kq));
+    c = step_key(K[idx + d2], step_diag(hp, h[idx + d2]));
     best = c < best ? c : best;
     if (best < kp) {
         K[idx] = best;
@@ -135,7 +130,7 @@ __device__ __forceinline__ int relax3(pkey_t *K, const float *h, int idx,
 }
 
 // Sweep the region to its fixed point.  Returns 1 if any key changed.
-__device__ int local_solve(pkey_t *K, const float *h, const Region &g,
+__device__ int local_solve(pkey_t *K, const unsigned *h, const Region &g,
                            RunState *st) {
     const int ncols = g.bx1 - g.bx0 + 1, nrows = g.by1 - g.by0 + 1;
     if (ncols <= 0 || nrows <= 0) return 0;
@@ -189,22 +184,26 @@ __device__ int local_solve(pkey_t *K, const float *h, const Region &g,
     return any;
 }
 
+// Half-costs of the region in fixed-point units; a cost outside [0, C_MAX)
+// (or not finite) is an invalid input.
 __device__ __forceinline__ void load_costs(const PairDev &P, const Region &g,
-                                           float *h) {
+                                           unsigned *h, RunState *st) {
+    bool bad = false;
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         int gx = g.x0 + c, gy = g.y0 + r;
         bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
-        h[r * g.P + c] = in ? __fmul_rn(0.5f, __ldg(P.C + (size_t)gy * P.W + gx)) : 0.f;
+        h[r * g.P + c] = in ? half_cost(__ldg(P.C + (size_t)gy * P.W + gx), &bad) : 0u;
     }
+    if (bad) set_status(st, EPIC_ERR_INVALID);
 }
 
 // Phase 1: solve tile (tx, ty) on its region from its seeds alone.
 __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
-                            float *h, RunState *st) {
+                            unsigned *h, RunState *st) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, P.apron);
-    load_costs(P, g, h);
+    load_costs(P, g, h, st);
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         K[r * g.P + c] = KEY_INF;
@@ -225,7 +224,7 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
                 int px = (int)floorf(mt.x + 0.5f) - g.x0;
                 int py = (int)floorf(mt.y + 0.5f) - g.y0;
                 if (px >= 0 && px < g.RW && py >= 0 && py < g.RH)
-                    atomicMin(&K[py * g.P + px], make_key(0.f, (unsigned)m));
+                    atomicMin(&K[py * g.P + px], make_key(0ull, (unsigned)m));
             }
         }
     }
@@ -266,7 +265,8 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
         else { x = gx1; y = gy0 + 1 + (i - n_top - n_bot - n_left); }
         const size_t p = (size_t)y * P.W + x;
         const pkey_t kp = ld_key(P.keys + p);
-        const float hp = __fmul_rn(0.5f, __ldg(P.C + p));
+        bool bad = false;
+        const unsigned hp = half_cost(__ldg(P.C + p), &bad);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int dx = (k == 0 || k == 4 || k == 6) ? 1 : (k == 1 || k == 5 || k == 7) ? -1 : 0;
@@ -276,10 +276,9 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
             if (qx >= gx0 && qx <= gx1 && qy >= gy0 && qy <= gy1) continue;
             const size_t q = (size_t)qy * P.W + qx;
             const pkey_t kq = ld_key(P.keys + q);
-            const float hq = __fmul_rn(0.5f, __ldg(P.C + q));
-            const float st = (dx != 0 && dy != 0) ? step_diag(hp, hq) : step_axis(hp, hq);
-            const pkey_t c = make_key(__fadd_rn(key_dist(kq), st), key_label(kq));
-            dirty |= c < kp;
+            const unsigned hq = half_cost(__ldg(P.C + q), &bad);
+            const unsigned long long w = (dx != 0 && dy != 0) ? step_diag(hp, hq) : step_axis(hp, hq);
+            dirty |= step_key(kq, w) < kp;
         }
     }
     return __syncthreads_or(dirty) != 0;
@@ -287,10 +286,10 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
 
 // Phase 2 re-solve of tile (tx, ty) from the current keys (tile + ring).
 __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
-                            float *h, RunState *st, int pass) {
+                            unsigned *h, RunState *st, int pass) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, 0);
-    load_costs(P, g, h);
+    load_costs(P, g, h, st);
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         int gx = g.x0 + c, gy = g.y0 + r;
@@ -348,7 +347,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
         const PairDev &P = a.pairs[s_pair];
         const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, P.apron);
         pkey_t *K = reinterpret_cast<pkey_t *>(smem);
-        float *h = reinterpret_cast<float *>(smem + sizeof(pkey_t) * g.RH * g.P);
+        unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
         solve_fresh(P, s_local % P.tiles_x, s_local / P.tiles_x, K, h, st);
     }
     if (!grid_sync(st, nblocks)) return;
@@ -377,7 +376,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
             if (s_check && border_dirty(P, tx, ty)) {
                 const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                 pkey_t *K = reinterpret_cast<pkey_t *>(smem);
-                float *h = reinterpret_cast<float *>(smem + sizeof(pkey_t) * g.RH * g.P);
+                unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
                 solve_again(P, tx, ty, K, h, st, pass + 1);
                 if (threadIdx.x == 0) atomicAdd(cnt, 1u);
             }
@@ -400,7 +399,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
 size_t dt_smem_bytes(int tile_w, int tile_h, int apron) {
     int RW = tile_w + 2 * apron + 2, RH = tile_h + 2 * apron + 2;
     int P = RW | 1;
-    return (size_t)RH * P * (sizeof(pkey_t) + sizeof(float));
+    return (size_t)RH * P * (sizeof(pkey_t) + sizeof(unsigned));
 }
 
 cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,

@@ -6,9 +6,8 @@
 // is the minimum over touching pairs (p, q) of D(p) + step(p, q) + D(q): the
 // shortest path from a seed to a pixel of its own cell stays in that cell,
 // and a path inside the union crosses from one cell to the other at some
-// touching pair.  Each candidate is evaluated in float32 as
-// (D(p_small) + step) + D(p_large), p_small being the pixel whose label is
-// the smaller index, so every kernel forms the same value for the same pair.
+// touching pair.  Each candidate D(p) + step(p, q) + D(q) is summed exactly
+// in the relaxation's fixed point and rounded once to float32.
 //
 // edges_kernel   every pixel looks at its four forward neighbours (right,
 //                down-left, down, down-right: each unordered pixel pair once)
@@ -113,10 +112,11 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
             const int x = tx * P.tile_w + lx, y = ty * P.tile_h + ly;
             const bool act = i < npx && x < W && y < H;
             pkey_t kp = 0;
-            float hp = 0.f;
+            unsigned hp = 0;
+            bool bad = false;
             if (act) {
                 kp = __ldg(P.keys + (size_t)y * W + x);
-                hp = __fmul_rn(0.5f, __ldg(P.C + (size_t)y * W + x));
+                hp = half_cost(__ldg(P.C + (size_t)y * W + x), &bad);
             }
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
@@ -131,20 +131,22 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                     const pkey_t kq = __ldg(P.keys + q);
                     const unsigned lp = key_label(kp), lq = key_label(kq);
                     have = lp != lq;
-                    if (have && (lp >= (unsigned)P.N || lq >= (unsigned)P.N)) {
-                        // an unreached pixel: the cost map was not finite and >= 0
+                    if (have && (lp >= (unsigned)P.N || lq >= (unsigned)P.N ||
+                                 !key_reached(kp) || !key_reached(kq))) {
+                        // an unreached pixel (or a distance beyond the fixed-
+                        // point range): the cost map was not in [0, C_MAX)
                         set_status(st, EPIC_ERR_INVALID);
                         have = false;
                     }
                     if (have) {
-                        const float hq = __fmul_rn(0.5f, __ldg(P.C + q));
-                        const float stp = (dx != 0 && dy != 0) ? step_diag(hp, hq)
-                                                               : step_axis(hp, hq);
-                        const bool ps = lp < lq;
-                        const float dsm = ps ? key_dist(kp) : key_dist(kq);
-                        const float dlg = ps ? key_dist(kq) : key_dist(kp);
-                        const float w = __fadd_rn(__fadd_rn(dsm, stp), dlg);
-                        k = ps ? (((pkey_t)lp << 32) | lq) : (((pkey_t)lq << 32) | lp);
+                        const unsigned hq = half_cost(__ldg(P.C + q), &bad);
+                        const unsigned long long stp = (dx != 0 && dy != 0)
+                                                           ? step_diag(hp, hq)
+                                                           : step_axis(hp, hq);
+                        // exact sum in fixed point, rounded once to float32
+                        const unsigned long long units = key_dunits(kp) + stp + key_dunits(kq);
+                        const float w = __fmul_rn(__ull2float_rn(units), ONE_PER_UNIT);
+                        k = lp < lq ? (((pkey_t)lp << 32) | lq) : (((pkey_t)lq << 32) | lp);
                         wb = __float_as_uint(w);
                     }
                 }

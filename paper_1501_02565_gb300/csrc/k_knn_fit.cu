@@ -20,9 +20,9 @@
 //   * an open-addressing table node -> tentative distance (bit 31 = settled),
 //     updated with compare-and-swap so several lanes may relax into one node,
 //   * the settled list (node, distance).
-// Batches are appended in frontier order (deterministic); only the batch
-// that crosses K is sorted (warp bitonic network) so that exactly the K
-// smallest keys are kept.  All edges of all batch nodes are relaxed in one
+// Batches are appended in frontier order; only the batch that crosses K is
+// sorted (warp bitonic network) so that exactly the K smallest keys are
+// kept, and the finished list is sorted once more (all keys) before the fit.  All edges of all batch nodes are relaxed in one
 // pass: lanes take (node, edge) pairs found from a warp prefix sum of the
 // batch nodes' degrees.  A newly pushed node's adjacency row, degree and
 // lightest edge are prefetched into L1 for when it is settled.
@@ -45,6 +45,16 @@ namespace epic {
 namespace {
 
 constexpr unsigned SETTLED = 0x80000000u;
+
+// Search key on G: float32 bits of the graph distance (non-negative, so the
+// bit pattern orders like the value) above the 32-bit node index.
+__device__ __forceinline__ pkey_t make_key(float d, unsigned node) {
+    return ((pkey_t)__float_as_uint(d) << 32) | node;
+}
+__device__ __forceinline__ float key_dist(pkey_t k) {
+    return __uint_as_float((unsigned)(k >> 32));
+}
+__device__ __forceinline__ unsigned key_label(pkey_t k) { return (unsigned)k; }
 
 __device__ __forceinline__ unsigned node_slot(unsigned u, int hs) {
     return (u * 0x9E3779B1u) >> 7 & (unsigned)(hs - 1);
@@ -396,9 +406,11 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
         }
         if (cnt > K) cnt = K;
         __syncwarp();
-        // diagnostic output is in settle order, i.e. sorted by key; batches
-        // are appended in frontier order, so sort the list first
-        if (P.knn_idx) sort_settled(rn, rd, cnt, fk, lane);
+        // batches are appended in frontier order, which follows the order
+        // of the adjacency rows (filled with atomics); sorting the list by
+        // key restores Dijkstra's settle order, so the fit below sums in a
+        // canonical order and the result is bit-for-bit reproducible
+        sort_settled(rn, rd, cnt, fk, lane);
 
         // locally-weighted affine fit over the cnt settled neighbours
         const float4 pm = __ldg(P.matches + m);

@@ -34,7 +34,8 @@ EXPORTED = (
     "epic_interp_run_batch_host", "epic_interp_sync",
     "epic_interp_get_labels", "epic_interp_get_edge_count",
     "epic_interp_get_graph", "epic_interp_get_knn", "epic_interp_get_models",
-    "epic_interp_get_passes", "epic_interp_enable_stage_timing",
+    "epic_interp_get_passes", "epic_interp_set_tile_rules",
+    "epic_interp_enable_stage_timing",
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
     "epic_geodesic_labels_noalloc",
@@ -59,6 +60,13 @@ class epic_pair_desc_t(ctypes.Structure):
         ("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int),
         ("K", ctypes.c_int), ("a", ctypes.c_float),
         ("flow_out", ctypes.c_void_p),
+    ]
+
+
+class epic_tile_rule_t(ctypes.Structure):
+    _fields_ = [
+        ("max_pixels", ctypes.c_longlong), ("tile_w", ctypes.c_int),
+        ("tile_h", ctypes.c_int), ("apron", ctypes.c_int),
     ]
 
 
@@ -114,6 +122,8 @@ def load(path: str | None = None):
     lib.epic_interp_get_models.restype = I
     lib.epic_interp_get_passes.argtypes = [P, pi]
     lib.epic_interp_get_passes.restype = I
+    lib.epic_interp_set_tile_rules.argtypes = [P, ctypes.POINTER(epic_tile_rule_t), I]
+    lib.epic_interp_set_tile_rules.restype = I
     lib.epic_interp_enable_stage_timing.argtypes = [P, I]
     lib.epic_interp_enable_stage_timing.restype = I
     lib.epic_interp_get_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), I, pi]
@@ -297,6 +307,15 @@ class EpicInterp:
         return n.value
 
     STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout")
+
+    def set_tile_rules(self, rules):
+        """rules: iterable of (max_pixels, tile_w, tile_h, apron)."""
+        rules = list(rules)
+        arr = (epic_tile_rule_t * max(len(rules), 1))()
+        for i, (mp, tw, th, ap) in enumerate(rules):
+            arr[i] = epic_tile_rule_t(int(mp), int(tw), int(th), int(ap))
+        self._check(self.lib.epic_interp_set_tile_rules(self.h, arr, len(rules)),
+                    "set_tile_rules")
 
     def enable_stage_timing(self, enable=True):
         self._check(self.lib.epic_interp_enable_stage_timing(self.h, int(enable)),
