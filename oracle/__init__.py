@@ -13,8 +13,11 @@ numpy arrays.  Functions follow the paper's Algorithm 1 (LA form, Sec. 3.4):
   knn(N, em, en, ew, K)           -> idx, dist, count   N_K by Dijkstra on G
   fit(matches, idx, dist, count, a)  -> model, fallback, detratio  (Eq. 2)
   writeout(L, matches, model)     -> flow      (Algorithm 1, steps 7-8)
-  nw(matches, idx, dist, count, a)   -> Nadaraya-Watson estimate (Eq. 1)
+  nw(matches, idx, dist, count, a)   -> Nadaraya-Watson flow estimate (Eq. 1)
   interp(C, matches, K, a)        -> dict with every intermediate
+  consistency(C, matches, a, ...) -> keep flags of the NW consistency check
+                                     (Sec. 4.1, "Pruning of matches")
+  interp_pruned(C, matches, K, a) -> the check, then interp on the kept matches
 
 Parity status of each function and the pins that check it are listed in the
 test files ``tests/test_oracle_*.py``; every function here is pinned.
@@ -177,7 +180,8 @@ def writeout(L, matches, model):
 
 
 def nw(matches, idx, dist, count, a):
-    """Nadaraya-Watson target estimate at every match, float64 [N, 2]."""
+    """Nadaraya-Watson estimate at every match, float64 [N, 2]: the
+    kernel-weighted mean of the neighbours' flows p'_n - p_n (Eq. 1)."""
     lib = _load()
     matches = _f32(matches).reshape(-1, 4)
     N = matches.shape[0]
@@ -191,16 +195,56 @@ def nw(matches, idx, dist, count, a):
     return out
 
 
-def interp(C, matches, K, a, weight_squared=True):
-    """The whole interpolator (Algorithm 1, LA form) with every intermediate."""
+def interp(C, matches, K, a, weight_squared=True, estimator="la"):
+    """The whole interpolator (Algorithm 1) with every intermediate.
+
+    estimator "la": locally-weighted affine fit per match (Eq. 2, with the
+    NW fallback of a degenerate fit); "nw": the Nadaraya-Watson flow of
+    Eq. 1 per match, constant over the match's cell (Algorithm 1)."""
     matches = _f32(matches).reshape(-1, 4)
     N = matches.shape[0]
     K = int(min(K, N))
     D, L = geodesic(C, matches)
     em, en, ew = graph(C, D, L, matches)
     idx, dist, count = knn(N, em, en, ew, K)
-    model, fb, dr = fit(matches, idx, dist, count, a, weight_squared)
+    if estimator == "la":
+        model, fb, dr = fit(matches, idx, dist, count, a, weight_squared)
+    elif estimator == "nw":
+        model = np.zeros((N, 6), np.float64)
+        model[:, :2] = nw(matches, idx, dist, count, a)
+        fb = np.ones(N, np.int32)
+        dr = np.zeros(N, np.float64)
+    else:
+        raise ValueError(f"unknown estimator {estimator!r}")
     flow = writeout(L, matches, model)
     return dict(D=D, L=L, em=em, en=en, ew=ew, idx=idx, dist=dist,
                 count=count, model=model, fallback=fb, detratio=dr,
                 flow=flow, K=K)
+
+
+def consistency(C, matches, a, threshold=5.0, K_nw=25):
+    """Consistency check of Sec. 4.1 ("Pruning of matches"): the NW
+    interpolation is run once on all matches (K_nw neighbours, Eq. 1) and a
+    match is kept when the Euclidean distance between its own flow
+    p'_m - p_m and the estimate at p_m is at most `threshold` px.
+
+    Returns (keep bool [N], deviation float64 [N], the NW run's dict)."""
+    matches = _f32(matches).reshape(-1, 4)
+    r = interp(C, matches, K_nw, a, estimator="nw")
+    own = matches[:, 2:].astype(np.float64) - matches[:, :2].astype(np.float64)
+    dev = np.hypot(*(r["model"][:, :2] - own).T)
+    return dev <= threshold, dev, r
+
+
+def interp_pruned(C, matches, K, a, threshold=5.0, K_nw=25, weight_squared=True,
+                  estimator="la"):
+    """Consistency check, then the interpolator on the kept matches.  When
+    no match passes, all are kept.  The result dict adds keep (flags over
+    the submitted matches), kept_index (original index of every match used)
+    and deviation."""
+    matches = _f32(matches).reshape(-1, 4)
+    keep, dev, _ = consistency(C, matches, a, threshold, K_nw)
+    kept_index = np.flatnonzero(keep) if keep.any() else np.arange(matches.shape[0])
+    r = interp(C, matches[kept_index], K, a, weight_squared, estimator)
+    r.update(keep=keep, kept_index=kept_index.astype(np.int32), deviation=dev)
+    return r

@@ -30,9 +30,15 @@
  *   - Eq. 2 is solved as a weighted least-squares problem whose rows are
  *     scaled by k, i.e. it minimises sum k^2 |A p + t - p'|^2
  *     (weight_squared = 1); weight_squared = 0 minimises sum k |.|^2.
+ *   - Eq. 1 averages the matches' correspondences expressed as flows,
+ *     u_n = p'_n - p_n, so the estimate at p_m is a flow; the per-cell
+ *     property of Sec. 3.4 then makes the NW flow constant over a cell.
+ *     (Averaging the positions p'_n literally would shift every estimate
+ *     by the kernel-weighted centroid offset of the neighbours, a bias of
+ *     several pixels that the NW accuracy the paper reports rules out.)
  *   - a fit with fewer than 3 neighbours or det(M) <= 1e-10 (tr M / 3)^3
- *     falls back to the Nadaraya-Watson estimate (Eq. 1) at p_m, held as a
- *     constant flow over the cell.
+ *     falls back to that Nadaraya-Watson flow at p_m, held constant over
+ *     the cell.
  *   - a match whose source pixel is owned by a smaller-index duplicate has an
  *     empty cell; it is joined to the owner by an edge of weight D = 0.
  *
@@ -408,8 +414,8 @@ static void solve3x2(const double Min[3][3], const double r1[3],
  *   minimise sum_n w_n | B (p_n - p_m) + c - (p'_n - p_n) |^2   (Eq. 2)
  * through the 3x3 normal equations in (x~, y~, 1), x~ = x_n - x_m.
  * fallback[m] = 1 when the fit is degenerate and the Nadaraya-Watson
- * estimate (Eq. 1) at p_m is used instead: c = sum k p'_n / sum k - p_m
- * (Eq. 1's kernel k, not squared), B = 0.  detratio[m] = det M / (tr M / 3)^3 (0 when fewer
+ * estimate (Eq. 1) at p_m is used instead: c = sum k u_n / sum k with
+ * u_n = p'_n - p_n (Eq. 1's kernel k, not squared), B = 0.  detratio[m] = det M / (tr M / 3)^3 (0 when fewer
  * than 3 neighbours).
  */
 int epic_oracle_fit(int N, const float *matches, int K, const int *idx,
@@ -436,8 +442,8 @@ int epic_oracle_fit(int N, const float *matches, int K, const int *idx,
                 rv[r] += w * phi[r] * v;
             }
             sw += k;
-            swu += k * (double)matches[4 * n + 2];
-            swv += k * (double)matches[4 * n + 3];
+            swu += k * u;
+            swv += k * v;
         }
         double tr = M[0][0] + M[1][1] + M[2][2];
         double det = det3(M);
@@ -446,8 +452,8 @@ int epic_oracle_fit(int N, const float *matches, int K, const int *idx,
         double *out = model + 6L * m;
         if (c < 3 || !(det > 1e-10 * scale)) {
             fallback[m] = 1;
-            out[0] = swu / sw - xm;
-            out[1] = swv / sw - ym;
+            out[0] = swu / sw;
+            out[1] = swv / sw;
             out[2] = out[3] = out[4] = out[5] = 0.0;
         } else {
             double bu[3], bv[3];
@@ -491,7 +497,8 @@ int epic_oracle_writeout(int H, int W, const int *L, int N,
 /* Nadaraya-Watson estimate at every match (Eq. 1 restricted to N_K)         */
 /* ------------------------------------------------------------------------ */
 
-/* nw[2m], nw[2m+1] = sum_n k_n p'_n / sum_n k_n with k_n = exp(-a d_n). */
+/* nw[2m], nw[2m+1] = sum_n k_n u_n / sum_n k_n with k_n = exp(-a d_n) and
+ * u_n = p'_n - p_n the flow of neighbour n. */
 int epic_oracle_nw(int N, const float *matches, int K, const int *idx,
                    const double *dist, const int *count, double a,
                    double *nw) {
@@ -502,8 +509,8 @@ int epic_oracle_nw(int N, const float *matches, int K, const int *idx,
             int n = idx[(long)m * K + j];
             double k = exp(-a * dist[(long)m * K + j]);
             s += k;
-            sx += k * (double)matches[4 * n + 2];
-            sy += k * (double)matches[4 * n + 3];
+            sx += k * ((double)matches[4 * n + 2] - (double)matches[4 * n + 0]);
+            sy += k * ((double)matches[4 * n + 3] - (double)matches[4 * n + 1]);
         }
         nw[2 * m + 0] = sx / s;
         nw[2 * m + 1] = sy / s;

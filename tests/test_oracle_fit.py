@@ -86,28 +86,56 @@ def test_degenerate_neighbourhood_falls_back_to_nadaraya_watson():
     assert fb.all()
     k = np.exp(-dist[0])
     for i in range(N):
-        tgt = m[idx[i], 2:].astype(np.float64)
-        ref = (k[:, None] * tgt).sum(0) / k.sum() - m[i, :2]
+        # neighbour n has flow (n, -2n): the fallback is the k-weighted mean
+        # flow, held constant over the cell (B = 0)
+        n = idx[i].astype(np.float64)
+        ref = [(k * n).sum() / k.sum(), (k * -2 * n).sum() / k.sum()]
         np.testing.assert_allclose(model[i, :2], ref, rtol=1e-12, atol=1e-12)
         assert (model[i, 2:] == 0).all()
 
 
 def test_fewer_than_three_neighbours_falls_back():
+    # flows (1, 1) and (4, 4); match 0 sees itself (k = 1) and match 1
+    # (k = e^-1): estimate (1 + 4/e) / (1 + 1/e) by hand
     m = np.array([[0, 0, 1, 1], [5, 5, 9, 9]], np.float32)
     idx = np.array([[0, 1], [1, 0]], np.int32)
     dist = np.array([[0, 1.0], [0, 1.0]])
     model, fb, _ = oracle.fit(m, idx, dist, np.array([2, 2], np.int32), 1.0)
     assert fb.all()
-    k = np.exp(-1.0)
-    np.testing.assert_allclose(model[0, :2], [(1 + 9 * k) / (1 + k)] * 2)
+    e = np.e
+    np.testing.assert_allclose(model[0, :2], [(1 + 4 / e) / (1 + 1 / e)] * 2, rtol=1e-14)
+    np.testing.assert_allclose(model[1, :2], [(4 + 1 / e) / (1 + 1 / e)] * 2, rtol=1e-14)
 
 
-def test_nadaraya_watson_is_kernel_weighted_mean():
-    m, idx, dist, count = _random_neighbourhoods(14)
-    for a in (0.3, 1.0):
+def test_nadaraya_watson_reproduces_a_translation():
+    # Eq. 1 is a weighted mean: every neighbour moving by the same (u, v)
+    # gives exactly (u, v), whatever the weights and wherever the
+    # neighbours sit (a position average would be pulled towards the
+    # neighbours' centroid instead)
+    m, idx, dist, count = _random_neighbourhoods(15)
+    m[:, 2] = m[:, 0] + 3.25
+    m[:, 3] = m[:, 1] - 7.5
+    for a in (0.3, 1.0, 4.0):
         out = oracle.nw(m, idx, dist, count, a)
-        for i in range(m.shape[0]):
-            k = np.exp(-a * dist[i])
-            tgt = m[idx[i], 2:].astype(np.float64)
-            np.testing.assert_allclose(out[i], (k[:, None] * tgt).sum(0) / k.sum(),
-                                       rtol=1e-12)
+        np.testing.assert_allclose(out, np.tile([3.25, -7.5], (m.shape[0], 1)), atol=1e-12)
+
+
+def test_nadaraya_watson_single_neighbour_is_own_flow():
+    m, idx, dist, count = _random_neighbourhoods(16)
+    out = oracle.nw(m, idx, dist, np.ones_like(count), 1.0)
+    own = m[:, 2:].astype(np.float64) - m[:, :2]
+    np.testing.assert_allclose(out, own, atol=1e-12)
+
+
+def test_nadaraya_watson_kernel_limits():
+    # a -> 0: plain mean of the K neighbours' flows; large a with distinct
+    # distances: the nearest neighbour (the match itself, distance 0) wins
+    m, idx, dist, count = _random_neighbourhoods(14)
+    flows = m[:, 2:].astype(np.float64) - m[:, :2]
+    out0 = oracle.nw(m, idx, dist, count, 1e-12)
+    np.testing.assert_allclose(out0, flows[idx].mean(axis=1), rtol=1e-9, atol=1e-9)
+    far = dist.copy()
+    far[:, 1:] += 0.5          # every other neighbour at least 0.5 away
+    out_inf = oracle.nw(m, idx, far, count, 200.0)
+    # the others' total weight is below (K-1) e^-100 relative to the match's
+    np.testing.assert_allclose(out_inf, flows, atol=1e-30)
