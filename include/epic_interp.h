@@ -83,6 +83,19 @@ typedef struct {
                              non-default stream, K <= max_K and tiles no
                              larger than the configured ones; otherwise the
                              run uses plain launches) */
+    int estimator;        /* 0: locally-weighted affine fit (Eq. 2, default);
+                             1: Nadaraya-Watson (Eq. 1), a constant flow per
+                             cell (Algorithm 1) */
+    int prune;            /* 1: consistency pruning before the interpolation
+                             (Sec. 4.1, "Pruning of matches"): a first pass
+                             computes the NW estimate at every match with
+                             prune_K neighbours, matches whose flow is farther
+                             than prune_threshold px from it are removed, and
+                             the configured estimator then runs on the kept
+                             matches with K neighbours.  If no match of a pair
+                             passes, the pair keeps all its matches. */
+    float prune_threshold; /* px (default 5) */
+    int prune_K;          /* neighbours of the NW pass (default 25) */
 } epic_config_t;
 
 /* One frame pair of a batch; pointers are device pointers. */
@@ -166,6 +179,18 @@ int epic_interp_get_knn(epic_interp_t *h, int pair, int *idx, float *dist,
 int epic_interp_get_models(epic_interp_t *h, int pair, float *models,
                            int *fallback, void *stream);
 
+/* Consistency pruning of pair `pair` of the last run (needs prune = 1;
+ * waits for the stream).  keep [N] int32: 1 where match m passed the check
+ * of Sec. 4.1 (N = the pair's match count as submitted); kept_index
+ * [capacity N] int32: the original index of each match the interpolation
+ * used, in order (every match when none passed); *n_kept: their number.
+ * keep and kept_index are device pointers and may be NULL.  After a pruned
+ * run, the labels, graph, K-NN lists and models of the other getters are
+ * those of the second pass: match indices there refer to positions in
+ * kept_index. */
+int epic_interp_get_pruning(epic_interp_t *h, int pair, int *keep,
+                            int *kept_index, int *n_kept);
+
 /* Number of relaxation verification passes the last run needed for its
  * whole batch (waits for the stream). */
 int epic_interp_get_passes(epic_interp_t *h, int *passes);
@@ -179,12 +204,14 @@ int epic_interp_set_tile_rules(epic_interp_t *h, const epic_tile_rule_t *rules,
                                int n);
 
 /* Stage timing.  While enabled, every run records CUDA events on its
- * stream between its six kernels (prepare, relaxation, edges, scatter,
- * K-NN + fit, write-out).  Enabling (again) clears the accumulated times. */
+ * stream around its stages: 0 prepare, 1 relaxation, 2 edges, 3 scatter,
+ * 4 K-NN + fit, 5 write-out, 6 pruning (the whole first pass and the
+ * compaction; zero when prune = 0).  Enabling (again) clears the
+ * accumulated times. */
 int epic_interp_enable_stage_timing(epic_interp_t *h, int enable);
 
 /* Sum over the runs since timing was enabled of each stage's elapsed time in
- * milliseconds, into ms_out[0..n_stages) (n_stages <= 6); *n_runs receives
+ * milliseconds, into ms_out[0..n_stages) (n_stages <= 7); *n_runs receives
  * the number of runs summed.  Waits for the last timed run. */
 int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages,
                                 int *n_runs);

@@ -104,6 +104,13 @@ struct PairDev {
     float *knn_dist;        // [N*K] or null
     int *knn_count;         // [N] or null
     int *info;              // [4] edges, max degree, spare
+    // consistency pruning (Sec. 4.1 "Pruning of matches"): the first pass
+    // writes keep[N]; the compaction rewrites matches/N/K of this entry in
+    // device memory for the second pass
+    int *keep;              // [N] 1 = kept, or null when not pruning
+    float4 *pruned;         // [N] kept matches, in their original order
+    int *kept_index;        // [N] original index of each kept match
+    int K2;                 // K of the second (LA) pass
 };
 
 struct GridBarrier {
@@ -116,6 +123,7 @@ struct RunState {
     int status;            // first device error (epic_status_t), 0 = OK
     int passes;            // relaxation verification passes of the last run
     unsigned changed[3];   // per-pass dirty-tile counters (rotating)
+    unsigned compact_done; // CTAs finished in the pruning compaction
     GridBarrier barrier;
 };
 
@@ -134,6 +142,10 @@ struct BatchArgs {
     int max_passes;
     int weight_squared;
     float fallback_eps;
+    int estimator;          // 0 = LA (Eq. 2), 1 = Nadaraya-Watson (Eq. 1)
+    int final_estimator;    // estimator of the second pass when pruning
+    int write_keep;         // first pass of a pruned run: write PairDev::keep
+    float prune_threshold;  // px; a match farther than this from the NW estimate is dropped
     RunState *state;
 };
 
@@ -180,6 +192,7 @@ cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const Launc
 cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                            int max_K);
 cudaError_t launch_writeout(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
+cudaError_t launch_compact(const BatchArgs &a, BatchArgs *dev, const LaunchCfg &lc);
 cudaError_t launch_split_keys(const PairDev *pair_host_copy, int *labels,
                               float *dist, cudaStream_t stream);
 cudaError_t launch_collect_edges(const PairDev *pair_host_copy, int *em,

@@ -49,6 +49,9 @@ struct epic_interp {
     int next_slot = 0;
     size_t table_cap = 0;
     std::vector<PairDev> pairs;     // last run's descriptors
+    const PairDev *pairs_dev = nullptr;  // last run's device descriptors
+    bool pruned = false;            // last run pruned (device N, K changed)
+    std::vector<int> n_submitted;   // last run's match counts as submitted
     cudaStream_t last_stream = nullptr;
     // device staging for epic_interp_run_host
     float *io_C = nullptr, *io_M = nullptr, *io_F = nullptr;
@@ -61,7 +64,7 @@ struct epic_interp {
     std::string err;
 };
 
-static constexpr int NSTAGE = 6;
+static constexpr int NSTAGE = 7;  // prepare .. write-out, pruning
 
 namespace {
 
@@ -117,10 +120,13 @@ void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &r
 
 struct Layout {
     size_t keys, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, adj, models,
-        fallback, knn_idx, knn_dist, knn_count, info, end;
+        fallback, knn_idx, knn_dist, knn_count, info, keep, pruned, kept_index, end;
 };
 
-Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep) {
+// K-NN lists hold max(K of the first pass, K of the second) entries per match
+int knn_cap(const PairDev &P) { return std::max(P.K, P.K2); }
+
+Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep, bool prune) {
     Layout L;
     size_t o = align_up(base, 256);
     const size_t npx = (size_t)P.H * P.W;
@@ -142,10 +148,13 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep) {
     L.adj = take((size_t)P.N * max_degree * sizeof(pkey_t));
     L.models = take((size_t)P.N * 2 * sizeof(float4));
     L.fallback = take((size_t)P.N * sizeof(int));
-    L.knn_idx = keep ? take((size_t)P.N * P.K * sizeof(int)) : 0;
-    L.knn_dist = keep ? take((size_t)P.N * P.K * sizeof(float)) : 0;
+    L.knn_idx = keep ? take((size_t)P.N * knn_cap(P) * sizeof(int)) : 0;
+    L.knn_dist = keep ? take((size_t)P.N * knn_cap(P) * sizeof(float)) : 0;
     L.knn_count = keep ? take((size_t)P.N * sizeof(int)) : 0;
     L.info = take(4 * sizeof(int));
+    L.keep = prune ? take((size_t)P.N * sizeof(int)) : 0;
+    L.pruned = prune ? take((size_t)P.N * sizeof(float4)) : 0;
+    L.kept_index = prune ? take((size_t)P.N * sizeof(int)) : 0;
     L.end = o;
     return L;
 }
@@ -160,6 +169,11 @@ PairDev make_pair_desc(const epic_config_t &c, const std::vector<epic_tile_rule_
     P.W = d.W;
     P.N = d.N;
     P.K = std::min(d.K, d.N);
+    P.K2 = P.K;
+    if (c.prune) {
+        // first pass: the NW estimate with prune_K neighbours
+        P.K = std::min(c.prune_K, d.N);
+    }
     P.a = d.a;
     choose_tiles(c, rules, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron);
     P.tiles_x = (d.W + P.tile_w - 1) / P.tile_w;
@@ -257,6 +271,16 @@ int check_pair(epic_interp_t *h, int pair) {
     if (!h) return EPIC_ERR_INVALID;
     if (pair < 0 || pair >= (int)h->pairs.size())
         return fail(h, EPIC_ERR_INVALID, "pair index out of range of the last run");
+    if (!h->pruned) return EPIC_OK;
+    // a pruned run rewrote the pair's matches, N and K on the device
+    int rc = wait_last(h);
+    if (rc) return rc;
+    PairDev d;
+    cudaError_t e = cudaMemcpy(&d, h->pairs_dev + pair, sizeof d, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pair descriptor read");
+    h->pairs[pair].matches = d.matches;
+    h->pairs[pair].N = d.N;
+    h->pairs[pair].K = d.K;
     return EPIC_OK;
 }
 
@@ -281,6 +305,10 @@ void epic_config_default(epic_config_t *c) {
     c->keep_intermediates = 0;
     c->max_degree = 32;
     c->use_graphs = 0;
+    c->estimator = 0;
+    c->prune = 0;
+    c->prune_threshold = 5.f;
+    c->prune_K = 25;
 }
 
 int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg) {
@@ -293,6 +321,13 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     if (c.max_degree <= 0) c.max_degree = 32;
     if (!(c.fallback_eps > 0.f)) c.fallback_eps = 1e-10f;
     if (c.max_pairs <= 0) c.max_pairs = 1;
+    if (c.prune_K <= 0) c.prune_K = 25;
+    if ((c.estimator != 0 && c.estimator != 1) || !(c.prune_threshold >= 0.f) ||
+        !std::isfinite(c.prune_threshold)) {
+        int r = fail(h, EPIC_ERR_INVALID, "estimator must be 0 or 1, prune_threshold finite >= 0");
+        delete h;
+        return r;
+    }
     if ((c.tile_w > 0 && c.tile_w < 8) || (c.tile_h > 0 && c.tile_h < 8) ||
         c.tile_w > 256 || c.tile_h > 256) {
         int r = fail(h, EPIC_ERR_INVALID, "tile sides must be in [8, 256]");
@@ -328,7 +363,7 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     d.K = std::max(1, c.max_K);
     d.a = 1.f;
     PairDev P = make_pair_desc(c, h->rules, d);
-    size_t per = layout_pair(0, P, c.max_degree, c.keep_intermediates != 0).end;
+    size_t per = layout_pair(0, P, c.max_degree, c.keep_intermediates != 0, c.prune != 0).end;
     int rc = ensure_arena(h, per * (size_t)c.max_pairs);
     if (rc) { epic_interp_destroy(h); return rc; }
     rc = ensure_table(h, 4096);
@@ -359,12 +394,12 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         if (P[i].apron + 1 > std::min(P[i].tile_w, P[i].tile_h) || P[i].apron > 64)
             return fail(h, EPIC_ERR_INVALID,
                         "apron must be smaller than the tile sides and at most 64");
-        L[i] = layout_pair(off, P[i], c.max_degree, c.keep_intermediates != 0);
+        L[i] = layout_pair(off, P[i], c.max_degree, c.keep_intermediates != 0, c.prune != 0);
         off = L[i].end;
         max_tw = std::max(max_tw, P[i].tile_w);
         max_th = std::max(max_th, P[i].tile_h);
         max_ap = std::max(max_ap, P[i].apron);
-        max_K = std::max(max_K, P[i].K);
+        max_K = std::max(max_K, knn_cap(P[i]));
     }
     int rc = ensure_arena(h, off);
     if (rc) return rc;
@@ -388,6 +423,11 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
             P[i].knn_count = reinterpret_cast<int *>(b + L[i].knn_count);
         }
         P[i].info = reinterpret_cast<int *>(b + L[i].info);
+        if (c.prune) {
+            P[i].keep = reinterpret_cast<int *>(b + L[i].keep);
+            P[i].pruned = reinterpret_cast<float4 *>(b + L[i].pruned);
+            P[i].kept_index = reinterpret_cast<int *>(b + L[i].kept_index);
+        }
     }
     // batch table: BatchArgs, PairDev[n], then 5 prefix arrays of n+1 ints
     std::vector<int> tile_base(n + 1), match_base(n + 1), chunk_base(n + 1),
@@ -432,9 +472,10 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         cfg_th = std::max(cfg_th, r.tile_h);
         cfg_ap = std::max(cfg_ap, r.apron);
     }
-    const bool graph = c.use_graphs && stream != nullptr && !h->timing && max_K <= c.max_K &&
+    const int cfg_K = std::max(c.max_K, c.prune ? c.prune_K : 1);
+    const bool graph = c.use_graphs && stream != nullptr && !h->timing && max_K <= cfg_K &&
                        max_tw <= cfg_tw && max_th <= cfg_th && max_ap <= cfg_ap;
-    const int knn_K = graph ? c.max_K : max_K;
+    const int knn_K = graph ? cfg_K : max_K;
     const int dt_tw = graph ? cfg_tw : max_tw, dt_th = graph ? cfg_th : max_th;
     const int dt_ap = graph ? cfg_ap : max_ap;
 
@@ -467,6 +508,10 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     a.max_passes = c.max_passes;
     a.weight_squared = c.weight_squared ? 1 : 0;
     a.fallback_eps = c.fallback_eps;
+    a.estimator = c.prune ? 1 : c.estimator;
+    a.final_estimator = c.estimator;
+    a.write_keep = c.prune ? 1 : 0;
+    a.prune_threshold = c.prune_threshold;
     a.state = h->state;
     if (epic::knn_warps_per_cta(knn_K, h->smem_optin) < 1)
         return fail(h, EPIC_ERR_INVALID, "K too large for the per-warp search tables");
@@ -482,25 +527,45 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     const BatchArgs *dev_a = reinterpret_cast<const BatchArgs *>(sl.dev);
 
     epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
+    BatchArgs *dev_rw = reinterpret_cast<BatchArgs *>(sl.dev);
+    const bool prune = c.prune != 0;
+    // ev (timing only): a start and an end event per stage
     auto enqueue = [&](cudaEvent_t *ev, size_t copy_bytes) -> cudaError_t {
         auto mark = [&](int i) {
             if (ev) cudaEventRecord(ev[i], stream);
         };
         cudaError_t r = cudaMemcpyAsync(sl.dev, sl.host, copy_bytes, cudaMemcpyHostToDevice, stream);
         if (r) return r;
+        mark(12);
+        if (prune) {
+            // first pass: NW estimate at every match and its keep flag, then
+            // the compaction that rewrites the device tables for the second
+            if ((r = epic::launch_prepare(a, dev_a, lc))) return r;
+            if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
+            if ((r = epic::launch_edges(a, dev_a, lc))) return r;
+            if ((r = epic::launch_scatter(a, dev_a, lc))) return r;
+            if ((r = epic::launch_knn_fit(a, dev_a, lc, knn_K))) return r;
+            if ((r = epic::launch_compact(a, dev_rw, lc))) return r;
+        }
+        mark(13);
         mark(0);
         if ((r = epic::launch_prepare(a, dev_a, lc))) return r;
         mark(1);
-        if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
         mark(2);
-        if ((r = epic::launch_edges(a, dev_a, lc))) return r;
+        if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
         mark(3);
-        if ((r = epic::launch_scatter(a, dev_a, lc))) return r;
         mark(4);
-        if ((r = epic::launch_knn_fit(a, dev_a, lc, knn_K))) return r;
+        if ((r = epic::launch_edges(a, dev_a, lc))) return r;
         mark(5);
-        if ((r = epic::launch_writeout(a, dev_a, lc))) return r;
         mark(6);
+        if ((r = epic::launch_scatter(a, dev_a, lc))) return r;
+        mark(7);
+        mark(8);
+        if ((r = epic::launch_knn_fit(a, dev_a, lc, knn_K))) return r;
+        mark(9);
+        mark(10);
+        if ((r = epic::launch_writeout(a, dev_a, lc))) return r;
+        mark(11);
         return cudaSuccess;
     };
     if (graph) {
@@ -527,13 +592,13 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     } else {
         cudaEvent_t *ev = nullptr;
         if (h->timing) {
-            size_t need = (size_t)(h->timed_runs + 1) * (NSTAGE + 1);
+            size_t need = (size_t)(h->timed_runs + 1) * (2 * NSTAGE);
             while (h->tev.size() < need) {
                 cudaEvent_t x;
                 if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
                 h->tev.push_back(x);
             }
-            ev = &h->tev[(size_t)h->timed_runs * (NSTAGE + 1)];
+            ev = &h->tev[(size_t)h->timed_runs * (2 * NSTAGE)];
             h->timed_runs++;
         }
         e = enqueue(ev, table_bytes);
@@ -543,6 +608,10 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
     sl.pending = true;
     h->pairs = P;
+    h->pairs_dev = a.pairs;
+    h->pruned = prune;
+    h->n_submitted.resize(n);
+    for (int i = 0; i < n; ++i) h->n_submitted[i] = descs[i].N;
     h->last_stream = stream;
     return EPIC_OK;
 }
@@ -721,6 +790,24 @@ int epic_interp_get_models(epic_interp_t *h, int pair, float *models, int *fallb
     return e == cudaSuccess ? EPIC_OK : cuda_fail(h, e, "get_models");
 }
 
+int epic_interp_get_pruning(epic_interp_t *h, int pair, int *keep, int *kept_index,
+                            int *n_kept) {
+    int rc = check_pair(h, pair);
+    if (rc) return rc;
+    if (!h->pruned) return fail(h, EPIC_ERR_INVALID, "the last run did not prune (prune = 0)");
+    const PairDev &P = h->pairs[pair];
+    cudaError_t e = cudaSuccess;
+    if (keep)
+        e = cudaMemcpy(keep, P.keep, (size_t)h->n_submitted[pair] * sizeof(int),
+                       cudaMemcpyDeviceToDevice);
+    if (!e && kept_index)
+        e = cudaMemcpy(kept_index, P.kept_index, (size_t)P.N * sizeof(int),
+                       cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_pruning");
+    if (n_kept) *n_kept = P.N;
+    return EPIC_OK;
+}
+
 int epic_interp_get_passes(epic_interp_t *h, int *passes) {
     if (!h || !passes) return EPIC_ERR_INVALID;
     int rc = read_state(h);
@@ -764,13 +851,14 @@ int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages, i
     for (int s = 0; s < n_stages; ++s) ms_out[s] = 0.f;
     if (n_runs) *n_runs = h->timed_runs;
     if (h->timed_runs == 0) return EPIC_OK;
-    cudaError_t e = cudaEventSynchronize(h->tev[(size_t)h->timed_runs * (NSTAGE + 1) - 1]);
+    // the write-out's end event (index 11) is the last one a run records
+    cudaError_t e = cudaEventSynchronize(h->tev[(size_t)(h->timed_runs - 1) * (2 * NSTAGE) + 11]);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
     for (int r = 0; r < h->timed_runs; ++r) {
-        const cudaEvent_t *ev = &h->tev[(size_t)r * (NSTAGE + 1)];
+        const cudaEvent_t *ev = &h->tev[(size_t)r * (2 * NSTAGE)];
         for (int s = 0; s < n_stages; ++s) {
             float ms = 0.f;
-            e = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+            e = cudaEventElapsedTime(&ms, ev[2 * s], ev[2 * s + 1]);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventElapsedTime");
             ms_out[s] += ms;
         }
@@ -779,9 +867,10 @@ int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages, i
 }
 
 int epic_interp_launches_per_run(epic_interp_t *h, int n) {
-    (void)h;
     (void)n;
-    return 6;  // prepare, relaxation, edges, scatter, K-NN + fit, write-out
+    // prepare, relaxation, edges, scatter, K-NN + fit, write-out; pruning
+    // adds the first pass's five and the compaction
+    return h && h->cfg.prune ? 12 : 6;
 }
 
 const char *epic_interp_last_error(epic_interp_t *h) {

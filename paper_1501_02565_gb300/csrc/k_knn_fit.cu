@@ -444,15 +444,10 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
             acc_prod(s[9], wx, vh);  s[9].lo = __fmaf_rn(wx, vl, s[9].lo);
             acc_prod(s[10], wy, vh); s[10].lo = __fmaf_rn(wy, vl, s[10].lo);
             acc_prod(s[11], w, vh);  s[11].lo = __fmaf_rn(w, vl, s[11].lo);
-            // Nadaraya-Watson sums (kernel k): k and k (p'_n - p_m)
+            // Nadaraya-Watson sums (kernel k, not squared): k and k u_n
             acc_add(s[12], k);
-            float th, tl;
-            two_sum(xt, uh, th, tl);
-            acc_prod(s[13], k, th);
-            s[13].lo = __fmaf_rn(k, __fadd_rn(tl, ul), s[13].lo);
-            two_sum(yt, vh, th, tl);
-            acc_prod(s[14], k, th);
-            s[14].lo = __fmaf_rn(k, __fadd_rn(tl, vl), s[14].lo);
+            acc_prod(s[13], k, uh); s[13].lo = __fmaf_rn(k, ul, s[13].lo);
+            acc_prod(s[14], k, vh); s[14].lo = __fmaf_rn(k, vl, s[14].lo);
         }
         double S[15];
 #pragma unroll
@@ -470,7 +465,19 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
             const double tr3 = (M00 + M11 + M22) / 3.0;
             float4 r0, r1;
             int fb;
-            if (cnt >= 3 && det > (double)a.fallback_eps * tr3 * tr3 * tr3) {
+            // Nadaraya-Watson estimate at p_m (Eq. 1), as a flow: the
+            // kernel-weighted mean of the neighbours' flows p'_n - p_n
+            const double sk = S[12];
+            const double nwu = S[13] / sk, nwv = S[14] / sk;
+            if (a.write_keep) {
+                // consistency check (Sec. 4.1): keep the match when its own
+                // flow is within the threshold of the estimate
+                const double du = nwu - ((double)pm.z - (double)pm.x);
+                const double dv = nwv - ((double)pm.w - (double)pm.y);
+                const double thr = (double)a.prune_threshold;
+                P.keep[m] = du * du + dv * dv <= thr * thr ? 1 : 0;
+            }
+            if (a.estimator == 0 && cnt >= 3 && det > (double)a.fallback_eps * tr3 * tr3 * tr3) {
                 const double ru0 = S[6], ru1 = S[7], ru2 = S[8];
                 const double rv0 = S[9], rv1 = S[10], rv2 = S[11];
                 const double id = 1.0 / det;
@@ -484,8 +491,9 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                 r1 = make_float4((float)bv0, (float)bv1, pm.x, pm.y);
                 fb = 0;
             } else {
-                const double sk = S[12];
-                r0 = make_float4((float)(S[13] / sk), (float)(S[14] / sk), 0.f, 0.f);
+                // the NW estimator, or the LA fit's fallback: the flow is
+                // constant over the cell (Algorithm 1, step 8)
+                r0 = make_float4((float)nwu, (float)nwv, 0.f, 0.f);
                 r1 = make_float4(0.f, 0.f, pm.x, pm.y);
                 fb = 1;
             }

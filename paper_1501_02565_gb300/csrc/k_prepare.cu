@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
         st->passes = 0;
         st->changed[0] = st->changed[1] = st->changed[2] = 0;
         st->barrier.count = 0;
+        st->compact_done = 0;
     }
     // seed binning: one CTA per pair at a time
     for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {

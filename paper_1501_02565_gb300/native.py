@@ -34,7 +34,8 @@ EXPORTED = (
     "epic_interp_run_batch_host", "epic_interp_sync",
     "epic_interp_get_labels", "epic_interp_get_edge_count",
     "epic_interp_get_graph", "epic_interp_get_knn", "epic_interp_get_models",
-    "epic_interp_get_passes", "epic_interp_set_tile_rules",
+    "epic_interp_get_pruning", "epic_interp_get_passes",
+    "epic_interp_set_tile_rules",
     "epic_interp_enable_stage_timing",
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
@@ -51,6 +52,8 @@ class epic_config_t(ctypes.Structure):
         ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
         ("apron", ctypes.c_int), ("keep_intermediates", ctypes.c_int),
         ("max_degree", ctypes.c_int), ("use_graphs", ctypes.c_int),
+        ("estimator", ctypes.c_int), ("prune", ctypes.c_int),
+        ("prune_threshold", ctypes.c_float), ("prune_K", ctypes.c_int),
     ]
 
 
@@ -120,6 +123,8 @@ def load(path: str | None = None):
     lib.epic_interp_get_knn.restype = I
     lib.epic_interp_get_models.argtypes = [P, I, P, P, P]
     lib.epic_interp_get_models.restype = I
+    lib.epic_interp_get_pruning.argtypes = [P, I, P, P, pi]
+    lib.epic_interp_get_pruning.restype = I
     lib.epic_interp_get_passes.argtypes = [P, pi]
     lib.epic_interp_get_passes.restype = I
     lib.epic_interp_set_tile_rules.argtypes = [P, ctypes.POINTER(epic_tile_rule_t), I]
@@ -301,12 +306,25 @@ class EpicInterp:
                     "get_models")
         return models, fb
 
+    def get_pruning(self, pair, N):
+        """Consistency pruning of the last run's pair (prune = 1): keep
+        flags [N] of the submitted matches and the original index of every
+        match the interpolation used."""
+        import torch
+        dev = f"cuda:{self.device}"
+        keep = torch.empty(N, dtype=torch.int32, device=dev)
+        kept = torch.empty(N, dtype=torch.int32, device=dev)
+        n = ctypes.c_int()
+        self._check(self.lib.epic_interp_get_pruning(self.h, pair, _ptr(keep), _ptr(kept),
+                                                     ctypes.byref(n)), "get_pruning")
+        return keep, kept[:n.value]
+
     def get_passes(self):
         n = ctypes.c_int()
         self._check(self.lib.epic_interp_get_passes(self.h, ctypes.byref(n)), "get_passes")
         return n.value
 
-    STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout")
+    STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout", "prune")
 
     def set_tile_rules(self, rules):
         """rules: iterable of (max_pixels, tile_w, tile_h, apron)."""
@@ -323,9 +341,10 @@ class EpicInterp:
 
     def stage_times(self):
         """{stage: summed ms} over the timed runs, and the run count."""
-        arr = (ctypes.c_float * 6)()
+        ns = len(self.STAGES)
+        arr = (ctypes.c_float * ns)()
         n = ctypes.c_int()
-        self._check(self.lib.epic_interp_get_stage_times(self.h, arr, 6, ctypes.byref(n)),
+        self._check(self.lib.epic_interp_get_stage_times(self.h, arr, ns, ctypes.byref(n)),
                     "get_stage_times")
         return dict(zip(self.STAGES, list(arr))), n.value
 

@@ -152,20 +152,28 @@ def check_knn(M, g, report):
     report["knn_tie_lists"] = n_tie
 
 
-def oracle_on_labels(C, M, K, a, D_ref, L, weight_squared=True):
+def _models(M, idx, dist, count, a, weight_squared, estimator):
+    if estimator == "nw":
+        model = np.zeros((M.shape[0], 6))
+        model[:, :2] = oracle.nw(M, idx, dist, count, a)
+        return model, np.ones(M.shape[0], np.int32), np.zeros(M.shape[0])
+    return oracle.fit(M, idx, dist, count, a, weight_squared)
+
+
+def oracle_on_labels(C, M, K, a, D_ref, L, weight_squared=True, estimator="la"):
     """Stages (b)-(d) of the oracle on a given (valid) labelling."""
     N = M.shape[0]
     K = int(min(K, N))
     em, en, ew = oracle.graph(C, D_ref, L, M)
     idx, dist, count = oracle.knn(N, em, en, ew, K)
-    model, fb, dr = oracle.fit(M, idx, dist, count, a, weight_squared)
+    model, fb, dr = _models(M, idx, dist, count, a, weight_squared, estimator)
     flow = oracle.writeout(L, M, model)
     return dict(D=D_ref, L=L, em=em, en=en, ew=ew, idx=idx, dist=dist,
                 count=count, model=model, fallback=fb, detratio=dr, flow=flow,
                 K=K)
 
 
-def fit_sensitivity(M, ref, a, weight_squared=True, draws=4):
+def fit_sensitivity(M, ref, a, weight_squared=True, draws=4, estimator="la"):
     """Largest flow change over each match's cell when its neighbour
     distances are perturbed by SENS_REL relative (random signs)."""
     N = M.shape[0]
@@ -174,15 +182,16 @@ def fit_sensitivity(M, ref, a, weight_squared=True, draws=4):
     Lf = ref["L"].ravel()
     for _ in range(draws):
         d = ref["dist"] * (1 + SENS_REL * rng.uniform(-1, 1, ref["dist"].shape))
-        mod, _, _ = oracle.fit(M, ref["idx"], d, ref["count"], a, weight_squared)
+        mod, _, _ = _models(M, ref["idx"], d, ref["count"], a, weight_squared, estimator)
         f = oracle.writeout(ref["L"], M, mod)
         e = np.abs(f - ref["flow"]).max(-1).ravel()
         np.maximum.at(worst, Lf, e)
     return worst
 
 
-def flow_exclusions(M, ref, excused_pix, a=1.0, weight_squared=True):
-    """Pixels excluded from the 1e-3 px flow check (see module docstring)."""
+def knn_near_ties(M, ref):
+    """Matches whose K-th and (K+1)-th oracle keys nearly tie: their
+    neighbour set is not unique under float32 distances."""
     N = M.shape[0]
     K = ref["K"]
     ridx, rdist, rcnt = oracle.knn(N, ref["em"], ref["en"], ref["ew"], min(K + 1, N))
@@ -192,9 +201,15 @@ def flow_exclusions(M, ref, excused_pix, a=1.0, weight_squared=True):
         if c < rcnt[m]:
             dk = rdist[m, c - 1]
             near[m] = rdist[m, c] - dk <= KNN_TIE * max(dk, 1e-30)
+    return near
+
+
+def flow_exclusions(M, ref, excused_pix, a=1.0, weight_squared=True, estimator="la"):
+    """Pixels excluded from the 1e-3 px flow check (see module docstring)."""
+    near = knn_near_ties(M, ref)
     dr = ref["detratio"]
     near_det = (dr >= DET_EPS / 10) & (dr <= 10 * DET_EPS)
-    ill = fit_sensitivity(M, ref, a, weight_squared) > SENS_PX
+    ill = fit_sensitivity(M, ref, a, weight_squared, estimator=estimator) > SENS_PX
     bad_match = near | near_det | ill
     excl = excused_pix | bad_match[ref["L"]]
     return excl, int(near.sum()), int(near_det.sum()), int(ill.sum())
@@ -217,9 +232,11 @@ def check_input_error(g, ref, report):
         f"neighbour distances off by more than {SENS_REL} relative: {err.max():.3g}")
 
 
-def check_flow(M, g, ref, excused_pix, report, tol=FLOW_TOL, a=1.0, weight_squared=True):
+def check_flow(M, g, ref, excused_pix, report, tol=FLOW_TOL, a=1.0, weight_squared=True,
+               estimator="la"):
     check_input_error(g, ref, report)
-    excl, n_knn, n_det, n_ill = flow_exclusions(M, ref, excused_pix, a, weight_squared)
+    excl, n_knn, n_det, n_ill = flow_exclusions(M, ref, excused_pix, a, weight_squared,
+                                                estimator)
     err = np.abs(g["flow"].astype(np.float64) - ref["flow"]).max(-1)
     e_in = err[~excl]
     report["flow_excluded_px"] = int(excl.sum())
@@ -234,7 +251,7 @@ def check_flow(M, g, ref, excused_pix, report, tol=FLOW_TOL, a=1.0, weight_squar
 
 
 def full_parity(pair_or_arrays, K=None, a=None, eng=None, check_knn_lists=True,
-                weight_squared=True, **cfg):
+                weight_squared=True, estimator="la", **cfg):
     if hasattr(pair_or_arrays, "C"):
         C, M = pair_or_arrays.C, pair_or_arrays.matches
         K = pair_or_arrays.K if K is None else K
@@ -242,16 +259,18 @@ def full_parity(pair_or_arrays, K=None, a=None, eng=None, check_knn_lists=True,
     else:
         C, M = pair_or_arrays
     cfg["weight_squared"] = int(bool(weight_squared))
+    if eng is None:
+        cfg["estimator"] = 1 if estimator == "nw" else 0
     g = run_gpu((C, M), K=K, a=a, eng=eng, **cfg)
-    ref = oracle.interp(C, M, K, a, weight_squared=weight_squared)
+    ref = oracle.interp(C, M, K, a, weight_squared=weight_squared, estimator=estimator)
     report = {}
     check_labels_and_distances(C, M, g, ref, report)
-    refb = oracle_on_labels(C, M, K, a, ref["D"], g["L"], weight_squared)
+    refb = oracle_on_labels(C, M, K, a, ref["D"], g["L"], weight_squared, estimator)
     check_graph(C, M, g, refb, report)
     if check_knn_lists and "idx" in g:
         check_knn(M, g, report)
     check_flow(M, g, refb, np.zeros(g["L"].shape, bool), report, a=a,
-               weight_squared=weight_squared)
+               weight_squared=weight_squared, estimator=estimator)
     e2e = np.abs(g["flow"].astype(np.float64) - ref["flow"]).max(-1)
     report["tie_sensitivity_px_p99"] = float(np.percentile(e2e, 99))
     report["tie_sensitivity_px_max"] = float(e2e.max())
