@@ -15,6 +15,8 @@ Prints one JSON line (rank 0).  Keys beyond the common ones:
   e2e           same metric through epic_interp_run_batch_host: pinned host
                 buffers, copies inside the timed region
   plain         the one-pair-at-a-time GPU path on the same pairs
+  pruned        the batched path with the NW consistency pruning of Sec. 4.1
+                (two passes per run)
   cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample
   clocks        nvidia-smi samples taken during the timed region
 
@@ -388,6 +390,33 @@ def run_ours(args, rank, world, local_rank):
     plain_graph_value = sum(p.P for p in pairs) / (g0.elapsed_time(g1) / 1e3) / 1e6
     geng.close()
 
+    # ---- with consistency pruning (Sec. 4.1): two passes per run --------
+    # pruning merges the removed matches' cells into their neighbours', so
+    # the second pass's graph has higher node degrees: wider adjacency rows
+    peng = EpicInterp(local_rank, max_pairs=B, prune=1, max_degree=64)
+    if tile_rules:
+        peng.set_tile_rules(tile_rules)
+    for _ in range(3):
+        peng.run_batch(items)
+    peng.sync()
+    kept = sum(int(peng.get_pruning(i, p.N)[1].numel()) for i, p in enumerate(pairs))
+    steps_p = max(3, args.steps // 5)
+    torch.cuda.synchronize()
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(steps_p):
+        peng.run_batch(items)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    peng.sync()
+    ms_pruned = q0.elapsed_time(q1) / steps_p
+    pruned = {"value": sum(p.P for p in pairs) / (ms_pruned / 1e3) / 1e6, "unit": "Mpix/s",
+              "ms_per_step": ms_pruned, "steps": steps_p,
+              "kept_frac": kept / sum(p.N for p in pairs),
+              "launches_per_run": peng.launches_per_run(B)}
+    peng.close()
+
     # ---- served: continuous batching vs one request at a time ------------
     served = served_plain = None
     if rank == 0 and world == 1:
@@ -443,6 +472,7 @@ def run_ours(args, rank, world, local_rank):
             "plain_graph": {"value": plain_graph_value, "unit": "Mpix/s",
                             "latency_ms_p50": float(np.percentile(glat, 50)),
                             "latency_ms_p99": float(np.percentile(glat, 99))},
+            "pruned": pruned,
             "batched_latency_ms": ms_total / args.steps,
             "served": served,
             "served_plain": served_plain,
