@@ -16,15 +16,24 @@
  *       kernel exp(-a D) (Eq. 1-2, restricted to N_K as in Sec. 3.2);
  *   (d) the dense write-out F(p) = A_{L(p)} p + t_{L(p)} (Algorithm 1, steps
  *       7-8, LA form), returned as flow F(p) - p.
+ * Options: the Nadaraya-Watson estimator of Eq. 1 in place of the LA fit
+ * (the flow is then constant over each cell, Algorithm 1), and the
+ * consistency pruning of Sec. 4.1 ("Pruning of matches") before the
+ * interpolation.
  *
  * Conventions shared by every entry point
  *   - Images are row-major, x = column, y = row; pixel centres are integer.
- *   - cost_map: float32 [H*W], finite and >= 0.
+ *   - cost_map: float32 [H*W], every value finite and in [0, 2) (edge
+ *     strengths).  The relaxation adds exact fixed-point step costs (units
+ *     of 2^-32), so geodesic distances must stay below 512; a value outside
+ *     the range, or a pixel left unreached, is reported as EPIC_ERR_INVALID.
  *   - matches:  float32 [N*4], rows (x, y, x', y').  The source pixel of match
  *     m is (floor(x+0.5), floor(y+0.5)) and must lie inside the image; two
  *     matches may share a source pixel (the smaller index owns it).
  *   - flow_out: float32 [H*W*2], (u, v) = F(p) - p interleaved per pixel.
- *   - Distances and weighted sums are float32; the per-match 3x3 normal
+ *   - At most 4,194,302 matches per pair (22-bit labels).
+ *   - Pixel distances are exact fixed-point sums; graph distances and
+ *     weighted sums are float32 (sums compensated); the per-match 3x3 normal
  *     equations are solved in float64.
  *   - Ties go to the smallest match index (labels, K-th neighbour).
  *   - All device pointers are caller-owned and must stay valid until the
