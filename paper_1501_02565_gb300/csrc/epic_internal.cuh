@@ -123,6 +123,8 @@ struct RunState {
     int status;            // first device error (epic_status_t), 0 = OK
     int passes;            // relaxation verification passes of the last run
     unsigned changed[3];   // per-pass dirty-tile counters (rotating)
+    unsigned work[4];      // relaxation tile dispensers: passes (rotating), phase 1
+    unsigned knn_next;     // K-NN match dispenser
     unsigned compact_done; // CTAs finished in the pruning compaction
     GridBarrier barrier;
 };

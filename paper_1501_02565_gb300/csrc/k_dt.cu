@@ -335,15 +335,25 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
     // the extra CTAs leave at once and the barrier counts only the others
     const unsigned nblocks = min(gridDim.x, (unsigned)a.total_tiles);
     if (blockIdx.x >= nblocks) return;
-    __shared__ int s_pair, s_local;
-
-    // phase 1
-    for (int t = blockIdx.x; t < a.total_tiles; t += nblocks) {
+    __shared__ int s_pair, s_local, s_tile;
+    // tiles are handed out one at a time from a counter, so that CTAs whose
+    // tiles converge quickly take more of them
+    auto next_tile = [&](unsigned *dispenser) {
+        __syncthreads();
         if (threadIdx.x == 0) {
-            s_pair = find_pair(a.tile_base, a.npairs, t);
-            s_local = t - a.tile_base[s_pair];
+            const int t = (int)atomicAdd(dispenser, 1u);
+            s_tile = t;
+            if (t < a.total_tiles) {
+                s_pair = find_pair(a.tile_base, a.npairs, t);
+                s_local = t - a.tile_base[s_pair];
+            }
         }
         __syncthreads();
+        return s_tile;
+    };
+
+    // phase 1
+    for (int t = next_tile(&st->work[3]); t < a.total_tiles; t = next_tile(&st->work[3])) {
         const PairDev &P = a.pairs[s_pair];
         const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, P.apron);
         pkey_t *K = reinterpret_cast<pkey_t *>(smem);
@@ -362,12 +372,8 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
             return;
         }
         unsigned *cnt = &st->changed[pass % 3];
-        for (int t = blockIdx.x; t < a.total_tiles; t += nblocks) {
-            if (threadIdx.x == 0) {
-                s_pair = find_pair(a.tile_base, a.npairs, t);
-                s_local = t - a.tile_base[s_pair];
-            }
-            __syncthreads();
+        unsigned *disp = &st->work[pass % 3];
+        for (int t = next_tile(disp); t < a.total_tiles; t = next_tile(disp)) {
             const PairDev &P = a.pairs[s_pair];
             const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
             __shared__ int s_check;
@@ -384,9 +390,12 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
         }
         if (!grid_sync(st, nblocks)) return;
         const unsigned dirty = ld_acquire(cnt);
-        // the counter of pass-1 (== pass+2 mod 3) was read by every CTA
-        // before this barrier; clear it for pass+2
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->changed[(pass + 2) % 3] = 0;
+        // the counters of pass-1 (== pass+2 mod 3) were last used before
+        // this barrier; clear them for pass+2
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->changed[(pass + 2) % 3] = 0;
+            st->work[(pass + 2) % 3] = 0;
+        }
         if (dirty == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) st->passes = pass + 1;
             return;

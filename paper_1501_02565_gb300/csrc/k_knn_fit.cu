@@ -146,7 +146,6 @@ __device__ void sort_settled(unsigned *rn, float *rd, int n, pkey_t *scratch, in
 
 __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs *__restrict__ ap) {
     const BatchArgs a = *ap;
-    const int warps = blockDim.x >> 5;
     extern __shared__ __align__(16) unsigned char smem[];
     RunState *st = a.state;
     if (get_status(st) != 0) return;
@@ -163,8 +162,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
     const int md = a.max_degree;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (int gm = blockIdx.x * warps + wid; gm < a.total_matches;
-         gm += gridDim.x * warps) {
+    // matches are handed out one at a time from a counter: search costs
+    // vary with the neighbourhood, and a static split leaves a long tail
+    for (;;) {
+        int gm = 0;
+        if (lane == 0) gm = (int)atomicAdd(&st->knn_next, 1u);
+        gm = __shfl_sync(0xffffffffu, gm, 0);
+        if (gm >= a.total_matches) break;
         const int pi = find_pair(a.match_base, a.npairs, gm);
         const PairDev &P = a.pairs[pi];
         const int m = gm - a.match_base[pi];
