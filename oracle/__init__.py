@@ -18,6 +18,9 @@ numpy arrays.  Functions follow the paper's Algorithm 1 (LA form, Sec. 3.4):
   consistency(C, matches, a, ...) -> keep flags of the NW consistency check
                                      (Sec. 4.1, "Pruning of matches")
   interp_pruned(C, matches, K, a) -> the check, then interp on the kept matches
+  interp_exact(C, matches, K, a)  -> the exact variant of Sec. 5.2: distances
+                                     from every pixel to every match and a fit
+                                     per pixel (geodesic or Euclidean)
 
 Parity status of each function and the pins that check it are listed in the
 test files ``tests/test_oracle_*.py``; every function here is pinned.
@@ -81,6 +84,8 @@ def _load():
         lib.epic_oracle_writeout.restype = I
         lib.epic_oracle_nw.argtypes = [I, P, I, P, P, P, D, P]
         lib.epic_oracle_nw.restype = I
+        lib.epic_oracle_fit_points.argtypes = [I, P, I, P, I, P, P, P, D, I, P, P, P]
+        lib.epic_oracle_fit_points.restype = I
         _lib = lib
         return lib
 
@@ -248,3 +253,87 @@ def interp_pruned(C, matches, K, a, threshold=5.0, K_nw=25, weight_squared=True,
     r = interp(C, matches[kept_index], K, a, weight_squared, estimator)
     r.update(keep=keep, kept_index=kept_index.astype(np.int32), deviation=dev)
     return r
+
+
+def fit_points(centres, matches, idx, dist, count, a, weight_squared=True):
+    """Fit of Eq. 2 centred at arbitrary points: model float64 [Np, 6]
+    (flow at the centre = model[:, :2]), fallback int32 [Np], detratio."""
+    lib = _load()
+    centres = np.ascontiguousarray(centres, np.float64).reshape(-1, 2)
+    matches = _f32(matches).reshape(-1, 4)
+    idx = np.ascontiguousarray(idx, np.int32)
+    dist = np.ascontiguousarray(dist, np.float64)
+    count = np.ascontiguousarray(count, np.int32)
+    Np, K = idx.shape
+    model = np.empty((Np, 6), np.float64)
+    fb = np.empty(Np, np.int32)
+    dr = np.empty(Np, np.float64)
+    _check(lib.epic_oracle_fit_points(Np, _ptr(centres), matches.shape[0], _ptr(matches), K,
+                                      _ptr(idx), _ptr(dist), _ptr(count), float(a),
+                                      int(bool(weight_squared)), _ptr(model), _ptr(fb),
+                                      _ptr(dr)), "fit_points")
+    return model, fb, dr
+
+
+def exact_distances(C, matches, metric="geodesic"):
+    """float64 [N, H, W]: distance from every pixel to every match.
+
+    "geodesic": D_G of Eq. 3, one single-source transform per match (the
+    multi-source transform run on that match alone); "euclidean": the
+    distance between pixel centres and the match's source pixel."""
+    matches = _f32(matches).reshape(-1, 4)
+    C = _f32(C)
+    H, W = C.shape
+    N = matches.shape[0]
+    out = np.empty((N, H, W), np.float64)
+    if metric == "geodesic":
+        for m in range(N):
+            out[m], _ = geodesic(C, matches[m:m + 1])
+    elif metric == "euclidean":
+        ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+        sx = np.floor(matches[:, 0].astype(np.float64) + 0.5)
+        sy = np.floor(matches[:, 1].astype(np.float64) + 0.5)
+        for m in range(N):
+            out[m] = np.hypot(xs - sx[m], ys - sy[m])
+    else:
+        raise ValueError(f"unknown metric {metric!r}")
+    return out
+
+
+def interp_exact(C, matches, K, a, metric="geodesic", weight_squared=True,
+                 estimator="la"):
+    """Exact variant (Sec. 5.2, Table 2): every pixel p takes its own K
+    nearest matches under the exact distance (key (d, index)) and its own
+    fit (Eq. 2 centred at p, or the NW estimate of Eq. 1); the flow at p is
+    the model's value at its centre."""
+    matches = _f32(matches).reshape(-1, 4)
+    H, W = np.asarray(C).shape
+    N = matches.shape[0]
+    K = int(min(K, N))
+    Dall = exact_distances(C, matches, metric).reshape(N, -1)
+    P = H * W
+    idx = np.empty((P, K), np.int32)
+    dist = np.empty((P, K), np.float64)
+    order = np.arange(N)
+    for p in range(P):
+        sel = np.lexsort((order, Dall[:, p]))[:K]   # by distance, then index
+        idx[p] = sel
+        dist[p] = Dall[sel, p]
+    count = np.full(P, K, np.int32)
+    ys, xs = np.mgrid[0:H, 0:W]
+    centres = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.float64)
+    if estimator == "la":
+        model, fb, dr = fit_points(centres, matches, idx, dist, count, a, weight_squared)
+    elif estimator == "nw":
+        k = np.exp(-a * dist)
+        u = (matches[idx, 2].astype(np.float64) - matches[idx, 0])
+        v = (matches[idx, 3].astype(np.float64) - matches[idx, 1])
+        model = np.zeros((P, 6))
+        model[:, 0] = (k * u).sum(1) / k.sum(1)
+        model[:, 1] = (k * v).sum(1) / k.sum(1)
+        fb, dr = np.ones(P, np.int32), np.zeros(P)
+    else:
+        raise ValueError(f"unknown estimator {estimator!r}")
+    flow = model[:, :2].reshape(H, W, 2).copy()
+    return dict(flow=flow, idx=idx, dist=dist, count=count, model=model,
+                fallback=fb, detratio=dr, K=K)

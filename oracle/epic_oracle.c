@@ -408,64 +408,89 @@ static void solve3x2(const double Min[3][3], const double r1[3],
 }
 
 /*
- * For every match m, with neighbours n in N_K(p_m) at graph distances d_n:
+ * Locally-weighted affine fit centred at (xc, yc) over c neighbours n (rows
+ * of `matches`) at distances d_n:
  *   k_n = exp(-a d_n)                       (kernel of Eq. 1)
  *   w_n = k_n^2  (weight_squared = 1)  or  k_n  (weight_squared = 0)
- *   minimise sum_n w_n | B (p_n - p_m) + c - (p'_n - p_n) |^2   (Eq. 2)
- * through the 3x3 normal equations in (x~, y~, 1), x~ = x_n - x_m.
- * fallback[m] = 1 when the fit is degenerate and the Nadaraya-Watson
- * estimate (Eq. 1) at p_m is used instead: c = sum k u_n / sum k with
- * u_n = p'_n - p_n (Eq. 1's kernel k, not squared), B = 0.  detratio[m] = det M / (tr M / 3)^3 (0 when fewer
- * than 3 neighbours).
+ *   minimise sum_n w_n | B (p_n - p_c) + c - (p'_n - p_n) |^2   (Eq. 2)
+ * through the 3x3 normal equations in (x~, y~, 1), x~ = x_n - xc.
+ * *fallback = 1 when the fit is degenerate and the Nadaraya-Watson estimate
+ * (Eq. 1) is used instead: c = sum k u_n / sum k with u_n = p'_n - p_n
+ * (Eq. 1's kernel k, not squared), B = 0.  *detratio = det M / (tr M / 3)^3
+ * (0 when fewer than 3 neighbours).
  */
+static void fit_at(double xc, double yc, const float *matches, int c,
+                   const int *nbr, const double *dist, double a,
+                   int weight_squared, double *out, int *fallback,
+                   double *detratio) {
+    double M[3][3] = {{0}}, ru[3] = {0}, rv[3] = {0};
+    double sw = 0, swu = 0, swv = 0;
+    for (int j = 0; j < c; ++j) {
+        int n = nbr[j];
+        double k = exp(-a * dist[j]);
+        double w = weight_squared ? k * k : k;
+        double xn = matches[4 * n + 0], yn = matches[4 * n + 1];
+        double u = (double)matches[4 * n + 2] - xn;
+        double v = (double)matches[4 * n + 3] - yn;
+        double phi[3] = {xn - xc, yn - yc, 1.0};
+        for (int r = 0; r < 3; ++r) {
+            for (int s = 0; s < 3; ++s) M[r][s] += w * phi[r] * phi[s];
+            ru[r] += w * phi[r] * u;
+            rv[r] += w * phi[r] * v;
+        }
+        sw += k;
+        swu += k * u;
+        swv += k * v;
+    }
+    double tr = M[0][0] + M[1][1] + M[2][2];
+    double det = det3(M);
+    double scale = (tr / 3.0) * (tr / 3.0) * (tr / 3.0);
+    *detratio = (c >= 3 && scale > 0) ? det / scale : 0.0;
+    if (c < 3 || !(det > 1e-10 * scale)) {
+        *fallback = 1;
+        out[0] = swu / sw;
+        out[1] = swv / sw;
+        out[2] = out[3] = out[4] = out[5] = 0.0;
+    } else {
+        double bu[3], bv[3];
+        solve3x2(M, ru, rv, bu, bv);
+        *fallback = 0;
+        out[0] = bu[2];
+        out[1] = bv[2];
+        out[2] = bu[0];
+        out[3] = bu[1];
+        out[4] = bv[0];
+        out[5] = bv[1];
+    }
+}
+
+/* Per-match fit (Sec. 3.4): centre p_m, neighbours N_K(p_m) on G. */
 int epic_oracle_fit(int N, const float *matches, int K, const int *idx,
                     const double *dist, const int *count, double a,
                     int weight_squared, double *model, int *fallback,
                     double *detratio) {
     if (N < 1 || K < 1 || !(a > 0)) return ORACLE_ERR_INVALID;
-    for (int m = 0; m < N; ++m) {
-        double xm = matches[4 * m + 0], ym = matches[4 * m + 1];
-        double M[3][3] = {{0}}, ru[3] = {0}, rv[3] = {0};
-        double sw = 0, swu = 0, swv = 0;
-        int c = count[m];
-        for (int j = 0; j < c; ++j) {
-            int n = idx[(long)m * K + j];
-            double k = exp(-a * dist[(long)m * K + j]);
-            double w = weight_squared ? k * k : k;
-            double xn = matches[4 * n + 0], yn = matches[4 * n + 1];
-            double u = (double)matches[4 * n + 2] - xn;
-            double v = (double)matches[4 * n + 3] - yn;
-            double phi[3] = {xn - xm, yn - ym, 1.0};
-            for (int r = 0; r < 3; ++r) {
-                for (int s = 0; s < 3; ++s) M[r][s] += w * phi[r] * phi[s];
-                ru[r] += w * phi[r] * u;
-                rv[r] += w * phi[r] * v;
-            }
-            sw += k;
-            swu += k * u;
-            swv += k * v;
-        }
-        double tr = M[0][0] + M[1][1] + M[2][2];
-        double det = det3(M);
-        double scale = (tr / 3.0) * (tr / 3.0) * (tr / 3.0);
-        detratio[m] = (c >= 3 && scale > 0) ? det / scale : 0.0;
-        double *out = model + 6L * m;
-        if (c < 3 || !(det > 1e-10 * scale)) {
-            fallback[m] = 1;
-            out[0] = swu / sw;
-            out[1] = swv / sw;
-            out[2] = out[3] = out[4] = out[5] = 0.0;
-        } else {
-            double bu[3], bv[3];
-            solve3x2(M, ru, rv, bu, bv);
-            fallback[m] = 0;
-            out[0] = bu[2];
-            out[1] = bv[2];
-            out[2] = bu[0];
-            out[3] = bu[1];
-            out[4] = bv[0];
-            out[5] = bv[1];
-        }
+    for (int m = 0; m < N; ++m)
+        fit_at(matches[4 * m + 0], matches[4 * m + 1], matches, count[m],
+               idx + (long)m * K, dist + (long)m * K, a, weight_squared,
+               model + 6L * m, fallback + m, detratio + m);
+    return ORACLE_OK;
+}
+
+/* Per-point fit (the exact variant of Sec. 5.2, estimation per pixel):
+ * centre (centres[2i], centres[2i+1]), neighbours idx/dist row i. */
+int epic_oracle_fit_points(int Np, const double *centres, int N,
+                           const float *matches, int K, const int *idx,
+                           const double *dist, const int *count, double a,
+                           int weight_squared, double *model, int *fallback,
+                           double *detratio) {
+    if (Np < 0 || N < 1 || K < 1 || !(a > 0)) return ORACLE_ERR_INVALID;
+    for (long i = 0; i < Np; ++i) {
+        for (int j = 0; j < count[i]; ++j)
+            if (idx[i * K + j] < 0 || idx[i * K + j] >= N) return ORACLE_ERR_INVALID;
+        fit_at(centres[2 * i], centres[2 * i + 1], matches, count[i], idx + i * K,
+               dist + i * K, a, weight_squared, model + 6 * i, fallback + i,
+               detratio + i);
     }
     return ORACLE_OK;
 }
