@@ -225,6 +225,26 @@ int epic_interp_enable_stage_timing(epic_interp_t *h, int enable);
 int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages,
                                 int *n_runs);
 
+/* Exact variant (Sec. 5.2, Table 2): every pixel p takes its own K nearest
+ * matches under the exact distance, keyed (distance, index), and its own fit
+ * (Eq. 2 centred at p, or the NW estimate of Eq. 1 with estimator = 1; a
+ * degenerate fit falls back to NW as in the main path).  The flow at p is
+ * the model's value at p.  metric 0: the geodesic distance D_G of Eq. 3,
+ * computed by one single-source relaxation per match (the paper's "exact"
+ * geodesic row); metric 1: the Euclidean distance between pixel centres and
+ * match pixels (the paper's "Euclidean" row).  Device pointers; cost_map,
+ * matches and flow_out as for epic_interp_run; knn_idx_out [H*W*K] int32 and
+ * knn_dist_out [H*W*K] float32 receive every pixel's list in key order (both
+ * NULL, or both set).  K is clamped to N and limited by shared memory
+ * (K * 512 bytes per 64 pixels; K <= 448 on GB300).  With metric 0 the
+ * handle holds N * H * W * 4 bytes of distances plus up to 1 GiB of
+ * relaxation scratch (grown on demand, EPIC_ERR_OOM if it cannot be).  Runs
+ * on `stream` and waits for completion; returns the device status. */
+int epic_exact_interp(epic_interp_t *h, const float *cost_map,
+                      const float *matches, int H, int W, int N, int K,
+                      float a, int metric, float *flow_out, int *knn_idx_out,
+                      float *knn_dist_out, void *stream);
+
 /* Number of kernel launches one run of `n` pairs enqueues. */
 int epic_interp_launches_per_run(epic_interp_t *h, int n);
 

@@ -195,6 +195,23 @@ cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const Launc
                            int max_K);
 cudaError_t launch_writeout(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
 cudaError_t launch_compact(const BatchArgs &a, BatchArgs *dev, const LaunchCfg &lc);
+
+// Exact variant (per-pixel K nearest and fit).
+constexpr int EXACT_THREADS = 64;
+struct ExactArgs {
+    const float *D;          // [N][H*W] distances, or null: Euclidean
+    const float4 *matches;   // [N]
+    float *flow;             // [H*W*2]
+    int *knn_idx;            // [H*W*K] or null
+    float *knn_dist;         // [H*W*K] (with knn_idx)
+    int *fallback;           // [H*W] or null
+    int H, W, N, K;
+    float a, fallback_eps;
+    int weight_squared, estimator;
+};
+size_t exact_smem_bytes(int K);
+cudaError_t launch_keys_to_dist(const pkey_t *keys, long long n, float *D, cudaStream_t stream);
+cudaError_t launch_exact_fit(const ExactArgs &x, cudaStream_t stream);
 cudaError_t launch_split_keys(const PairDev *pair_host_copy, int *labels,
                               float *dist, cudaStream_t stream);
 cudaError_t launch_collect_edges(const PairDev *pair_host_copy, int *em,

@@ -56,6 +56,9 @@ struct epic_interp {
     // device staging for epic_interp_run_host
     float *io_C = nullptr, *io_M = nullptr, *io_F = nullptr;
     size_t io_C_n = 0, io_M_n = 0, io_F_n = 0;
+    // scratch of the exact variant (distance rows, relaxation chunk, tables)
+    char *ex_buf = nullptr;
+    size_t ex_cap = 0;
     // stage timing: NSTAGE+1 events per timed run, reused across enablements
     std::vector<epic_tile_rule_t> rules;  // relaxation tile by frame size
     bool timing = false;
@@ -866,6 +869,146 @@ int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages, i
     return EPIC_OK;
 }
 
+int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matches, int H,
+                      int W, int N, int K, float a, int metric, float *flow_out,
+                      int *knn_idx_out, float *knn_dist_out, void *stream_) {
+    if (!h) return EPIC_ERR_INVALID;
+    epic_pair_desc_t d{cost_map, matches, H, W, N, K, a, flow_out};
+    int rc = validate(h, d, 0);
+    if (rc) return rc;
+    if (metric != 0 && metric != 1) return fail(h, EPIC_ERR_INVALID, "metric must be 0 or 1");
+    if (knn_idx_out && !knn_dist_out)
+        return fail(h, EPIC_ERR_INVALID, "knn_idx_out needs knn_dist_out");
+    const epic_config_t &c = h->cfg;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    K = std::min(K, N);
+    if (epic::exact_smem_bytes(K) > (size_t)h->smem_optin)
+        return fail(h, EPIC_ERR_INVALID, "K too large for the per-pixel lists");
+    const long long P = (long long)H * W;
+    float *D = nullptr;
+    if (metric == 0) {
+        // single-source relaxations, Cm matches at a time, each a pseudo-pair
+        // with one seed; their distances become row m of D [N][P]
+        int tw, th, ap;
+        choose_tiles(c, h->rules, H, W, &tw, &th, &ap);
+        const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th, T = tx * ty;
+        const long long Cm = std::max(1LL, std::min((long long)N, (1LL << 30) / (P * 8)));
+        const size_t small_ints = (size_t)(T + 1) + T + 1 + T + 1 + 1 + 4;  // per pseudo-pair
+        const size_t d_bytes = align_up((size_t)N * P * sizeof(float), 256);
+        const size_t k_bytes = align_up((size_t)Cm * P * sizeof(pkey_t), 256);
+        const size_t s_bytes = align_up((size_t)Cm * small_ints * sizeof(int), 256);
+        const size_t args_bytes = align_up(sizeof(BatchArgs), 256);
+        const size_t pd_bytes = align_up(sizeof(PairDev) * Cm, 256);
+        const size_t pre_stride = align_up(sizeof(int) * (Cm + 1), 256);
+        const size_t t_bytes = args_bytes + pd_bytes + 5 * pre_stride;
+        const size_t need = d_bytes + k_bytes + s_bytes + t_bytes;
+        if (need > h->ex_cap) {
+            if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
+                return cuda_fail(h, e, "cudaStreamSynchronize");
+            if (h->ex_buf) cudaFree(h->ex_buf);
+            h->ex_buf = nullptr;
+            h->ex_cap = 0;
+            e = cudaMalloc(&h->ex_buf, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return cuda_fail(h, e, "exact-variant cudaMalloc");
+            }
+            h->ex_cap = need;
+        }
+        char *b = h->ex_buf;
+        D = reinterpret_cast<float *>(b);
+        pkey_t *keys = reinterpret_cast<pkey_t *>(b + d_bytes);
+        int *small = reinterpret_cast<int *>(b + d_bytes + k_bytes);
+        char *tdev = b + d_bytes + k_bytes + s_bytes;
+        std::vector<char> thost(t_bytes);
+        epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
+        for (long long m0 = 0; m0 < N; m0 += Cm) {
+            const int n = (int)std::min(Cm, (long long)N - m0);
+            std::vector<PairDev> pd(n);
+            for (int j = 0; j < n; ++j) {
+                PairDev &q = pd[j];
+                q = PairDev{};
+                q.C = cost_map;
+                q.matches = reinterpret_cast<const float4 *>(matches) + m0 + j;
+                q.H = H;
+                q.W = W;
+                q.N = 1;
+                q.K = 1;
+                q.a = 1.f;
+                q.tile_w = tw;
+                q.tile_h = th;
+                q.apron = ap;
+                q.tiles_x = tx;
+                q.tiles_y = ty;
+                q.keys = keys + (size_t)j * P;
+                int *sp = small + (size_t)j * small_ints;
+                q.tile_start = sp;
+                q.tile_fill = sp + T + 1;
+                q.tile_seeds = sp + 2 * T + 1;
+                q.tile_stamp = sp + 2 * T + 2;
+                q.deg = sp + 3 * T + 2;
+                q.wmin = reinterpret_cast<unsigned *>(sp + 3 * T + 3);
+                q.info = sp + 3 * T + 4;
+            }
+            std::vector<int> pre(5 * (n + 1), 0);
+            for (int j = 0; j <= n; ++j) {
+                pre[j] = j * T;                 // tiles
+                pre[(n + 1) + j] = j;           // matches
+            }
+            BatchArgs ba{};
+            ba.pairs = reinterpret_cast<const PairDev *>(tdev + args_bytes);
+            ba.npairs = n;
+            auto pre_dev = [&](int k) {
+                return reinterpret_cast<const int *>(tdev + args_bytes + pd_bytes + k * pre_stride);
+            };
+            ba.tile_base = pre_dev(0);
+            ba.match_base = pre_dev(1);
+            ba.chunk_base = pre_dev(2);
+            ba.hash_base = pre_dev(3);
+            ba.clear_base = pre_dev(4);
+            ba.total_tiles = n * T;
+            ba.total_matches = n;
+            ba.max_degree = 1;
+            ba.max_passes = c.max_passes;
+            ba.weight_squared = 1;
+            ba.fallback_eps = c.fallback_eps;
+            ba.state = h->state;
+            memcpy(thost.data(), &ba, sizeof ba);
+            memcpy(thost.data() + args_bytes, pd.data(), sizeof(PairDev) * n);
+            for (int k = 0; k < 5; ++k)
+                memcpy(thost.data() + args_bytes + pd_bytes + k * pre_stride, pre.data() + k * (n + 1),
+                       sizeof(int) * (n + 1));
+            const BatchArgs *dev_a = reinterpret_cast<const BatchArgs *>(tdev);
+            if ((e = cudaMemcpyAsync(tdev, thost.data(), t_bytes, cudaMemcpyHostToDevice, stream)) ||
+                (e = epic::launch_prepare(ba, dev_a, lc)) ||
+                (e = epic::launch_dt(ba, dev_a, lc, tw, th, ap, false, nullptr)) ||
+                (e = epic::launch_keys_to_dist(keys, (long long)n * P, D + m0 * P, stream)) ||
+                (e = cudaStreamSynchronize(stream)))
+                return cuda_fail(h, e, "exact-variant relaxation");
+        }
+    }
+    epic::ExactArgs x{};
+    x.D = D;
+    x.matches = reinterpret_cast<const float4 *>(matches);
+    x.flow = flow_out;
+    x.knn_idx = knn_idx_out;
+    x.knn_dist = knn_idx_out ? knn_dist_out : nullptr;
+    x.H = H;
+    x.W = W;
+    x.N = N;
+    x.K = K;
+    x.a = a;
+    x.fallback_eps = c.fallback_eps;
+    x.weight_squared = c.weight_squared ? 1 : 0;
+    x.estimator = c.estimator;
+    if ((e = epic::launch_exact_fit(x, stream)) != cudaSuccess)
+        return cuda_fail(h, e, "exact-variant fit");
+    h->last_stream = stream;
+    return epic_interp_sync(h);
+}
+
 int epic_interp_launches_per_run(epic_interp_t *h, int n) {
     (void)n;
     // prepare, relaxation, edges, scatter, K-NN + fit, write-out; pruning
@@ -894,6 +1037,7 @@ void epic_interp_destroy(epic_interp_t *h) {
     if (h->io_C) cudaFree(h->io_C);
     if (h->io_M) cudaFree(h->io_M);
     if (h->io_F) cudaFree(h->io_F);
+    if (h->ex_buf) cudaFree(h->ex_buf);
     for (cudaEvent_t x : h->tev) cudaEventDestroy(x);
     delete h;
 }

@@ -39,7 +39,7 @@ EXPORTED = (
     "epic_interp_enable_stage_timing",
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
-    "epic_geodesic_labels_noalloc",
+    "epic_geodesic_labels_noalloc", "epic_exact_interp",
 )
 
 
@@ -139,6 +139,8 @@ def load(path: str | None = None):
     lib.epic_interp_last_error.restype = ctypes.c_char_p
     lib.epic_interp_destroy.argtypes = [P]
     lib.epic_interp_destroy.restype = None
+    lib.epic_exact_interp.argtypes = [P, P, P, I, I, I, I, F, I, P, P, P, P]
+    lib.epic_exact_interp.restype = I
     lib.epic_geodesic_labels_noalloc.argtypes = [P, P, I, I, I, P, P, P]
     lib.epic_geodesic_labels_noalloc.restype = I
     _lib = lib
@@ -305,6 +307,26 @@ class EpicInterp:
                                                     _stream_handle(stream)),
                     "get_models")
         return models, fb
+
+    def exact(self, C, matches, K, a, metric="geodesic", with_knn=False, stream=None):
+        """Exact per-pixel variant (epic_exact_interp); CUDA tensors in,
+        flow [H, W, 2] (and per-pixel K-NN lists) out; waits."""
+        import torch
+        H, W = C.shape
+        N = matches.shape[0]
+        Kc = min(int(K), N)
+        dev = C.device
+        flow = torch.empty((H, W, 2), dtype=torch.float32, device=dev)
+        idx = dist = None
+        if with_knn:
+            idx = torch.empty((H * W, Kc), dtype=torch.int32, device=dev)
+            dist = torch.empty((H * W, Kc), dtype=torch.float32, device=dev)
+        code = {"geodesic": 0, "euclidean": 1}[metric]
+        rc = self.lib.epic_exact_interp(self.h, _ptr(C), _ptr(matches), H, W, N, int(K),
+                                        float(a), code, _ptr(flow), _ptr(idx), _ptr(dist),
+                                        _stream_handle(stream))
+        self._check(rc, "epic_exact_interp")
+        return (flow, idx, dist) if with_knn else flow
 
     def get_pruning(self, pair, N):
         """Consistency pruning of the last run's pair (prune = 1): keep

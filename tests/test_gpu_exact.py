@@ -1,0 +1,117 @@
+"""Exact per-pixel variant on the GPU (epic_exact_interp) vs the FP64 oracle
+(Sec. 5.2, Table 2: "Geodesic (exact)" and "Euclidean").
+
+Tolerances (as in parity.py): distances within 1e-4 d + 1e-6; every pixel's
+K-NN list equal to the oracle's except where the oracle's K-th and (K+1)-th
+keys nearly tie (1e-5 relative); flow within 1e-3 px except at those pixels
+and at ill-conditioned fits (the FP64 flow moves by more than 5e-4 px under a
+1e-6 relative perturbation of the neighbour distances)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_02565_gb300 import synth
+from helpers import random_small_case
+
+pytestmark = pytest.mark.gpu
+
+D_RTOL, D_ATOL, TIE, FLOW_TOL = 1e-4, 1e-6, 1e-5, 1e-3
+
+
+def _gpu_exact(C, M, K, a, metric, **cfg):
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    eng = EpicInterp(0, **cfg)
+    try:
+        flow, idx, dist = eng.exact(torch.from_numpy(np.ascontiguousarray(C)).cuda(),
+                                    torch.from_numpy(np.ascontiguousarray(M)).cuda(),
+                                    K, a, metric=metric, with_knn=True)
+        return flow.cpu().numpy(), idx.cpu().numpy(), dist.cpu().numpy()
+    finally:
+        eng.close()
+
+
+def _reference_with_next(C, M, K, a, metric, estimator):
+    """Oracle result with K neighbours plus the (K+1)-th distance."""
+    N = M.shape[0]
+    Dall = oracle.exact_distances(C, M, metric).reshape(N, -1)
+    ref = oracle.interp_exact(C, M, K, a, metric=metric, estimator=estimator)
+    nxt = np.full(Dall.shape[1], np.inf)
+    if K < N:
+        nxt = np.partition(Dall, K, axis=0)[K] if K < N else nxt
+    return ref, nxt
+
+
+def _ill_conditioned(C, M, ref, a, estimator):
+    if estimator == "nw":
+        return np.zeros(ref["flow"].shape[:2], bool).ravel()
+    H, W = ref["flow"].shape[:2]
+    ys, xs = np.mgrid[0:H, 0:W]
+    centres = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.float64)
+    rng = np.random.default_rng(7)
+    worst = np.zeros(H * W)
+    for _ in range(3):
+        d = ref["dist"] * (1 + 1e-6 * rng.uniform(-1, 1, ref["dist"].shape))
+        mod, _, _ = oracle.fit_points(centres, M, ref["idx"], d, ref["count"], a)
+        worst = np.maximum(worst, np.abs(mod[:, :2] - ref["model"][:, :2]).max(1))
+    dr = ref["detratio"]
+    near_det = (dr >= 1e-11) & (dr <= 1e-9)
+    return (worst > FLOW_TOL / 2) | near_det
+
+
+def _check(C, M, K, a, metric, estimator="la"):
+    K = min(K, M.shape[0])
+    cfg = {"estimator": 1 if estimator == "nw" else 0}
+    flow, idx, dist = _gpu_exact(C, M, K, a, metric, **cfg)
+    ref, nxt = _reference_with_next(C, M, K, a, metric, estimator)
+    kth = ref["dist"][:, -1]
+    tie = nxt - kth <= TIE * np.maximum(kth, 1e-30)
+    # distances of the same neighbour
+    same = (idx == ref["idx"]).all(1)
+    derr = np.abs(dist[same].astype(np.float64) - ref["dist"][same])
+    assert (derr <= D_RTOL * ref["dist"][same] + D_ATOL).all(), derr.max()
+    # lists: equal, or the same set reordered among near-equal keys, or a
+    # K-th near tie
+    bad = ~same & ~tie
+    for p in np.flatnonzero(bad):
+        if set(idx[p]) == set(ref["idx"][p]):
+            bad[p] = False
+    assert not bad.any(), f"{bad.sum()} pixels with different K-NN lists"
+    excl = tie | ~same | _ill_conditioned(C, M, ref, a, estimator)
+    err = np.abs(flow.reshape(-1, 2).astype(np.float64) - ref["flow"].reshape(-1, 2)).max(1)
+    e_in = err[~excl]
+    print(f"\n[exact {metric} {estimator}] px={err.size} excluded={excl.sum()} "
+          f"ties={tie.sum()} max_err={e_in.max() if e_in.size else 0:.3g}")
+    assert (e_in <= FLOW_TOL).all(), e_in.max()
+    return flow, ref
+
+
+@pytest.mark.parametrize("metric", ["geodesic", "euclidean"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_small_random_cases(metric, seed):
+    # 37 x 70: ragged against the 64 x 32 relaxation tiles and the 64-pixel
+    # blocks of the per-pixel kernel
+    C, M = random_small_case(900 + seed, H=37, W=70, N=30, c_lo=0.01, c_hi=1.0)
+    _check(C, M, 8, 1.0, metric)
+
+
+@pytest.mark.parametrize("metric", ["geodesic", "euclidean"])
+def test_config1_pair(metric):
+    p = synth.config_pair(1, 0)
+    flow, ref = _check(p.C, p.matches, p.K, p.a, metric)
+    if metric == "geodesic":
+        # the approximation of Eq. 4 against the exact result (Table 2)
+        approx = oracle.interp(p.C, p.matches, p.K, p.a)["flow"]
+        aee = lambda f: float(np.hypot(*(f - p.gt_flow).transpose(2, 0, 1)).mean())
+        print(f"[exact vs approx] AEE to ground truth: exact {aee(flow):.3f}, "
+              f"approx {aee(approx):.3f}")
+
+
+def test_nw_estimator_and_single_neighbour():
+    C, M = random_small_case(910, H=30, W=41, N=25, c_lo=0.01, c_hi=1.0)
+    _check(C, M, 6, 0.7, "geodesic", estimator="nw")
+    # K = 1: the flow of the nearest match everywhere
+    flow, idx, _ = _gpu_exact(C, M, 1, 1.0, "geodesic")
+    np.testing.assert_allclose(flow.reshape(-1, 2), M[idx[:, 0], 2:] - M[idx[:, 0], :2],
+                               rtol=1e-6, atol=1e-6)
