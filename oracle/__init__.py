@@ -18,6 +18,7 @@ numpy arrays.  Functions follow the paper's Algorithm 1 (LA form, Sec. 3.4):
   consistency(C, matches, a, ...) -> keep flags of the NW consistency check
                                      (Sec. 4.1, "Pruning of matches")
   interp_pruned(C, matches, K, a) -> the check, then interp on the kept matches
+  gradient_cost(image)            -> the ||grad I|| cost map of Table 2
   interp_exact(C, matches, K, a)  -> the exact variant of Sec. 5.2: distances
                                      from every pixel to every match and a fit
                                      per pixel (geodesic or Euclidean)
@@ -337,3 +338,18 @@ def interp_exact(C, matches, K, a, metric="geodesic", weight_squared=True,
     flow = model[:, :2].reshape(H, W, 2).copy()
     return dict(flow=flow, idx=idx, dist=dist, count=count, model=model,
                 fallback=fb, detratio=dr, K=K)
+
+
+def gradient_cost(image, floor=0.0):
+    """Cost map from the image gradient (Table 2, the "||grad_2 I||_2"
+    contour row): C(p) = floor + sqrt(sum over channels of gx^2 + gy^2),
+    with central differences gx = (I(x+1) - I(x-1)) / 2 on the image padded
+    by edge replication (so gx = (I(1) - I(0)) / 2 at the left border).
+    image: [H, W] or [H, W, channels], values in [0, 1]; float64 [H, W] out."""
+    I = np.asarray(image, np.float64)
+    if I.ndim == 2:
+        I = I[..., None]
+    Ip = np.pad(I, ((1, 1), (1, 1), (0, 0)), mode="edge")
+    gx = (Ip[1:-1, 2:] - Ip[1:-1, :-2]) / 2.0
+    gy = (Ip[2:, 1:-1] - Ip[:-2, 1:-1]) / 2.0
+    return floor + np.sqrt((gx * gx + gy * gy).sum(axis=2))

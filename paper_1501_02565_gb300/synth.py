@@ -58,6 +58,7 @@ class Pair:
     K: int
     a: float
     name: str = ""
+    regions: np.ndarray | None = None   # int32 [H, W] region map (for images)
 
     @property
     def N(self) -> int:
@@ -256,7 +257,7 @@ def make_polygon_pair(H, W, n_regions, seed, *, N, K, a=1.0,
         xs, ys = flat % W, flat // W
     m = _make_matches(rng, gt, xs, ys, noise_sd, outlier_frac,
                       t_range if outlier_R is None else outlier_R)
-    return Pair(H, W, C, m, gt.astype(np.float32), K, a, name)
+    return Pair(H, W, C, m, gt.astype(np.float32), K, a, name, R)
 
 
 def make_kitti_pair(H, W, seed, *, N=8000, K=100, a=1.0, n_boxes=20,
@@ -327,7 +328,7 @@ def make_kitti_pair(H, W, seed, *, N=8000, K=100, a=1.0, n_boxes=20,
     flat = np.concatenate([low, hi])
     m = _make_matches(rng, flow, flat % W, flat // W, noise_sd, outlier_frac,
                       max_flow)
-    return Pair(H, W, C, m, flow.astype(np.float32), K, a, name)
+    return Pair(H, W, C, m, flow.astype(np.float32), K, a, name, R)
 
 
 _BATCH_SIZES = ((480, 640), (436, 1024), (375, 1242), (1080, 1920))
@@ -390,3 +391,28 @@ def serving_requests(n: int, rate_hz: float, seed: int = 5000):
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate_hz, size=n)
     return np.cumsum(gaps) - gaps[0]
+
+
+def region_image(pair: Pair, seed: int = 0, channels: int = 3) -> np.ndarray:
+    """A synthetic image float32 [H, W, channels] in [0, 1] of the pair's
+    first frame: a random colour per region, a low-contrast texture (two
+    random plane waves per region) and pixel noise, so that the image
+    gradient is strong at region boundaries and weak inside regions."""
+    if pair.regions is None:
+        raise ValueError("pair has no region map")
+    R = pair.regions
+    H, W = R.shape
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nreg = int(R.max()) + 1
+    base = rng.uniform(0.15, 0.85, size=(nreg, channels))
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = base[R].astype(np.float64)
+    for _ in range(2):
+        ang = rng.uniform(0, math.pi, size=nreg)
+        freq = rng.uniform(0.05, 0.3, size=nreg)
+        amp = rng.uniform(0.0, 0.04, size=nreg)
+        phase = rng.uniform(0, 2 * math.pi, size=nreg)
+        wave = amp[R] * np.sin(freq[R] * (np.cos(ang[R]) * xs + np.sin(ang[R]) * ys) + phase[R])
+        img += wave[..., None]
+    img += rng.normal(0.0, 0.005, size=img.shape)
+    return np.clip(img, 0.0, 1.0).astype(np.float32)
