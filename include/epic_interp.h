@@ -245,6 +245,21 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map,
                       float a, int metric, float *flow_out, int *knn_idx_out,
                       float *knn_dist_out, void *stream);
 
+/* Cost map from an image (Table 2, the "||grad_2 I||_2" contour row, a
+ * stand-in for a learned edge detector): for each of `frames` images
+ * [H][W][channels] float32 (interleaved channels, values in [0, 1],
+ * frames stored back to back), cost_out [frames][H][W] receives
+ *   C(p) = floor + sqrt(sum_c gx_c^2 + gy_c^2),
+ * gx = (I(x+1) - I(x-1)) / 2 and gy likewise, on the image padded by edge
+ * replication (each frame's borders are its own).  With values in [0, 1]
+ * C - floor <= sqrt(channels / 2), inside the interpolator's [0, 2) for up
+ * to 3 channels when floor < 0.77.  channels = 1, 3 or 4; floor finite and
+ * >= 0.  Device pointers on the current device; enqueued on `stream`
+ * without waiting.  Needs no handle. */
+int epic_gradient_cost(const float *image, int frames, int H, int W,
+                       int channels, float floor, float *cost_out,
+                       void *stream);
+
 /* Number of kernel launches one run of `n` pairs enqueues. */
 int epic_interp_launches_per_run(epic_interp_t *h, int n);
 

@@ -212,6 +212,10 @@ struct ExactArgs {
 size_t exact_smem_bytes(int K);
 cudaError_t launch_keys_to_dist(const pkey_t *keys, long long n, float *D, cudaStream_t stream);
 cudaError_t launch_exact_fit(const ExactArgs &x, cudaStream_t stream);
+
+// Image-gradient cost map.
+cudaError_t launch_gradcost(const float *img, int F, int H, int W, int channels, float floor_,
+                            float *C, int num_sms, cudaStream_t stream);
 cudaError_t launch_split_keys(const PairDev *pair_host_copy, int *labels,
                               float *dist, cudaStream_t stream);
 cudaError_t launch_collect_edges(const PairDev *pair_host_copy, int *em,

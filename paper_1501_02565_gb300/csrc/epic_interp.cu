@@ -1009,6 +1009,21 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
     return epic_interp_sync(h);
 }
 
+int epic_gradient_cost(const float *image, int frames, int H, int W, int channels,
+                       float floor_, float *cost_out, void *stream) {
+    if (!image || !cost_out || frames < 1 || H < 1 || W < 1 ||
+        (channels != 1 && channels != 3 && channels != 4) || !(floor_ >= 0.f) ||
+        !std::isfinite(floor_))
+        return EPIC_ERR_INVALID;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    cudaError_t e = epic::launch_gradcost(image, frames, H, W, channels, floor_, cost_out, sms,
+                                          reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
 int epic_interp_launches_per_run(epic_interp_t *h, int n) {
     (void)n;
     // prepare, relaxation, edges, scatter, K-NN + fit, write-out; pruning

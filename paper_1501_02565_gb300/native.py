@@ -39,7 +39,7 @@ EXPORTED = (
     "epic_interp_enable_stage_timing",
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
-    "epic_geodesic_labels_noalloc", "epic_exact_interp",
+    "epic_geodesic_labels_noalloc", "epic_exact_interp", "epic_gradient_cost",
 )
 
 
@@ -139,6 +139,8 @@ def load(path: str | None = None):
     lib.epic_interp_last_error.restype = ctypes.c_char_p
     lib.epic_interp_destroy.argtypes = [P]
     lib.epic_interp_destroy.restype = None
+    lib.epic_gradient_cost.argtypes = [P, I, I, I, I, F, P, P]
+    lib.epic_gradient_cost.restype = I
     lib.epic_exact_interp.argtypes = [P, P, P, I, I, I, I, F, I, P, P, P, P]
     lib.epic_exact_interp.restype = I
     lib.epic_geodesic_labels_noalloc.argtypes = [P, P, I, I, I, P, P, P]
@@ -372,3 +374,26 @@ class EpicInterp:
 
     def launches_per_run(self, n=1):
         return self.lib.epic_interp_launches_per_run(self.h, n)
+
+
+def gradient_cost(image, floor=0.0, out=None, stream=None):
+    """Image-gradient cost map (epic_gradient_cost) of a CUDA float32 tensor
+    [H, W], [H, W, channels] or [frames, H, W, channels]; returns [H, W]
+    (or [frames, H, W]), enqueued on `stream`."""
+    import torch
+    lib = load()
+    x = image
+    if x.dim() == 2:
+        x = x[None, :, :, None]
+    elif x.dim() == 3:
+        x = x[None]
+    if not x.is_contiguous():
+        raise ValueError("image must be contiguous")
+    F, H, W, ch = x.shape
+    if out is None:
+        out = torch.empty((F, H, W), dtype=torch.float32, device=image.device)
+    rc = lib.epic_gradient_cost(_ptr(x), F, H, W, ch, float(floor), _ptr(out),
+                                _stream_handle(stream))
+    if rc != EPIC_OK:
+        raise EpicError(rc, "epic_gradient_cost")
+    return out[0] if image.dim() < 4 else out
