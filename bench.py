@@ -17,6 +17,10 @@ Prints one JSON line (rank 0).  Keys beyond the common ones:
   plain         the one-pair-at-a-time GPU path on the same pairs
   pruned        the batched path with the NW consistency pruning of Sec. 4.1
                 (two passes per run)
+  exact         the exact per-pixel variant of Sec. 5.2 (geodesic and
+                Euclidean) on one pair, against the one-pair path
+  gradient_cost the image-gradient cost map (Table 2) of the step's frames
+                (synthetic region images), one launch, vs the HBM peak
   cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample
   clocks        nvidia-smi samples taken during the timed region
 
@@ -62,6 +66,7 @@ def parse_args():
     ap.add_argument("--cpu-threads", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
+    ap.add_argument("--no-exact", action="store_true", help="skip the exact-variant leg")
     return ap.parse_args()
 
 
@@ -417,6 +422,50 @@ def run_ours(args, rank, world, local_rank):
               "launches_per_run": peng.launches_per_run(B)}
     peng.close()
 
+    # ---- image-gradient cost map (Table 2) on the step's frames -----------
+    from paper_1501_02565_gb300 import synth as _synth
+    from paper_1501_02565_gb300.native import gradient_cost
+    imgs = torch.from_numpy(np.stack([_synth.region_image(p, seed=i) for i, p in
+                                      enumerate(pairs)])).to(dev)
+    gc_out = torch.empty(imgs.shape[:3], dtype=torch.float32, device=dev)
+    for _ in range(3):
+        gradient_cost(imgs, 1e-3, out=gc_out)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    reps = 20
+    g0.record(stream)
+    for _ in range(reps):
+        gradient_cost(imgs, 1e-3, out=gc_out)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gc_ms = g0.elapsed_time(g1) / reps
+    gc_bytes = imgs.numel() * 4 + gc_out.numel() * 4
+    gradcost = {"ms_per_launch": gc_ms, "frames": len(pairs),
+                "algorithmic_bytes": gc_bytes,
+                "achieved_gbs": gc_bytes / (gc_ms / 1e3) / 1e9}
+    del imgs, gc_out
+
+    # ---- exact per-pixel variant (Sec. 5.2, Table 2) on one pair ----------
+    exact = None
+    if rank == 0 and not args.no_exact:
+        p0 = pairs[0]
+        xeng = EpicInterp(local_rank, max_H=p0.H, max_W=p0.W, max_N=p0.N)
+        if tile_rules:
+            xeng.set_tile_rules(tile_rules)
+        exact = {"pair": f"{p0.W}x{p0.H}, N={p0.N}, K={p0.K}"}
+        C0, M0 = items[0][0], items[0][1]
+        for metric in ("geodesic", "euclidean"):
+            xeng.exact(C0, M0, p0.K, p0.a, metric=metric)      # warm-up, allocation
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xeng.exact(C0, M0, p0.K, p0.a, metric=metric)
+            torch.cuda.synchronize()
+            exact[f"{metric}_ms"] = 1e3 * (time.perf_counter() - t0)
+        exact["approx_ms"] = float(np.median(lat))
+        exact["geodesic_over_approx"] = exact["geodesic_ms"] / exact["approx_ms"]
+        xeng.close()
+
     # ---- served: continuous batching vs one request at a time ------------
     served = served_plain = None
     if rank == 0 and world == 1:
@@ -425,6 +474,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- roofline ----------------------------------------------------------
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
+    gradcost["frac_hbm"] = gradcost["achieved_gbs"] / hbm
     stages = {}
     for s in STAGES:
         ms = stage_ms[s] / max(n_runs, 1)
@@ -473,6 +523,8 @@ def run_ours(args, rank, world, local_rank):
                             "latency_ms_p50": float(np.percentile(glat, 50)),
                             "latency_ms_p99": float(np.percentile(glat, 99))},
             "pruned": pruned,
+            "exact": exact,
+            "gradient_cost": gradcost,
             "batched_latency_ms": ms_total / args.steps,
             "served": served,
             "served_plain": served_plain,
