@@ -19,6 +19,8 @@ numpy arrays.  Functions follow the paper's Algorithm 1 (LA form, Sec. 3.4):
                                      (Sec. 4.1, "Pruning of matches")
   interp_pruned(C, matches, K, a) -> the check, then interp on the kept matches
   gradient_cost(image)            -> the ||grad I|| cost map of Table 2
+  refine.refine(I1, I2, flow)     -> the variational refinement of Sec. 4
+                                     (module oracle/refine.py, numpy)
   interp_exact(C, matches, K, a)  -> the exact variant of Sec. 5.2: distances
                                      from every pixel to every match and a fit
                                      per pixel (geodesic or Euclidean)
