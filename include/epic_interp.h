@@ -260,6 +260,38 @@ int epic_gradient_cost(const float *image, int frames, int H, int W,
                        int channels, float floor, float *cost_out,
                        void *stream);
 
+/* Variational refinement (Sec. 4, "Variational Energy Minimization").  The
+ * paper fixes the structure: a data term with colour and gradient constancy
+ * and a normalisation factor, a smoothness term on the flow gradient with
+ * local weight alpha(x) = alpha0 exp(-kappa ||grad I1(x)||), kappa = 5, and
+ * a full-resolution minimisation by `iterations` (5) fixed-point iterations
+ * with `sor_iterations` (30) SOR iterations per linear system.  The
+ * remaining constants are this library's defaults: gamma (weight of the
+ * gradient term) 0.7, robust penaliser sqrt(s^2 + eps^2) with eps 1e-3,
+ * normalisation 1 / (|grad|^2 + zeta^2) with zeta 0.1, alpha0 1, SOR
+ * relaxation omega 1.6. */
+typedef struct {
+    float alpha0, gamma, kappa, eps, zeta, omega;
+    int iterations, sor_iterations;
+} epic_refine_params_t;
+
+void epic_refine_params_default(epic_refine_params_t *p);
+
+/* Refine flow [H*W*2] in place between images I1 and I2 [H*W*channels]
+ * float32 (interleaved channels, values in [0, 1]; channels 1..4).  Each
+ * fixed-point iteration warps I2 by the current flow (bilinear, clamped
+ * coordinates), linearises the data term there with the robust weights
+ * taken at zero update, and solves for the update with red-black SOR in
+ * which each pixel's 2x2 (du, dv) system is solved exactly; derivatives are
+ * central differences on edge-replicated images.  Device pointers; the
+ * handle holds H*W*(channels + 10)*4 bytes of scratch (grown on demand,
+ * EPIC_ERR_OOM if it cannot be).  Enqueued on `stream` without waiting; one
+ * refinement in flight per handle (the scratch is shared).  params NULL =
+ * defaults. */
+int epic_refine(epic_interp_t *h, const float *I1, const float *I2, int H,
+                int W, int channels, float *flow,
+                const epic_refine_params_t *params, void *stream);
+
 /* Number of kernel launches one run of `n` pairs enqueues. */
 int epic_interp_launches_per_run(epic_interp_t *h, int n);
 

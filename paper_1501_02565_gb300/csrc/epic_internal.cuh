@@ -213,6 +213,15 @@ size_t exact_smem_bytes(int K);
 cudaError_t launch_keys_to_dist(const pkey_t *keys, long long n, float *D, cudaStream_t stream);
 cudaError_t launch_exact_fit(const ExactArgs &x, cudaStream_t stream);
 
+// Variational refinement.
+struct RefineArgs {
+    float alpha0, gamma, kappa, eps, zeta, omega;
+    int iterations, sor_iterations;
+};
+size_t refine_scratch_bytes(int H, int W, int C);
+cudaError_t launch_refine(const float *I1, const float *I2, int H, int W, int C, float *flow,
+                          const RefineArgs &r, void *scratch, int num_sms, cudaStream_t stream);
+
 // Image-gradient cost map.
 cudaError_t launch_gradcost(const float *img, int F, int H, int W, int channels, float floor_,
                             float *C, int num_sms, cudaStream_t stream);

@@ -59,6 +59,9 @@ struct epic_interp {
     // scratch of the exact variant (distance rows, relaxation chunk, tables)
     char *ex_buf = nullptr;
     size_t ex_cap = 0;
+    // scratch of the variational refinement
+    void *rf_buf = nullptr;
+    size_t rf_cap = 0;
     // stage timing: NSTAGE+1 events per timed run, reused across enablements
     std::vector<epic_tile_rule_t> rules;  // relaxation tile by frame size
     bool timing = false;
@@ -908,6 +911,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
             if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
                 return cuda_fail(h, e, "cudaStreamSynchronize");
             if (h->ex_buf) cudaFree(h->ex_buf);
+    if (h->rf_buf) cudaFree(h->rf_buf);
             h->ex_buf = nullptr;
             h->ex_cap = 0;
             e = cudaMalloc(&h->ex_buf, need);
@@ -1009,6 +1013,53 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
     return epic_interp_sync(h);
 }
 
+void epic_refine_params_default(epic_refine_params_t *p) {
+    if (!p) return;
+    p->alpha0 = 1.f;
+    p->gamma = 0.7f;
+    p->kappa = 5.f;
+    p->eps = 1e-3f;
+    p->zeta = 0.1f;
+    p->omega = 1.6f;
+    p->iterations = 5;
+    p->sor_iterations = 30;
+}
+
+int epic_refine(epic_interp_t *h, const float *I1, const float *I2, int H, int W, int channels,
+                float *flow, const epic_refine_params_t *params, void *stream_) {
+    if (!h) return EPIC_ERR_INVALID;
+    epic_refine_params_t prm;
+    if (params) prm = *params; else epic_refine_params_default(&prm);
+    if (!I1 || !I2 || !flow || H < 1 || W < 1 || channels < 1 || channels > 4)
+        return fail(h, EPIC_ERR_INVALID, "refine: bad arguments");
+    if (!(prm.alpha0 >= 0.f) || !(prm.gamma >= 0.f) || !(prm.kappa >= 0.f) || !(prm.eps > 0.f) ||
+        !(prm.zeta > 0.f) || !(prm.omega > 0.f && prm.omega < 2.f) || prm.iterations < 0 ||
+        prm.sor_iterations < 0)
+        return fail(h, EPIC_ERR_INVALID, "refine: parameter out of range");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t need = epic::refine_scratch_bytes(H, W, channels);
+    if (need > h->rf_cap) {
+        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaStreamSynchronize");
+        if (h->rf_buf) cudaFree(h->rf_buf);
+        h->rf_buf = nullptr;
+        h->rf_cap = 0;
+        if ((e = cudaMalloc(&h->rf_buf, need)) != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(h, e, "refine cudaMalloc");
+        }
+        h->rf_cap = need;
+    }
+    epic::RefineArgs r{prm.alpha0, prm.gamma, prm.kappa, prm.eps, prm.zeta, prm.omega,
+                       prm.iterations, prm.sor_iterations};
+    e = epic::launch_refine(I1, I2, H, W, channels, flow, r, h->rf_buf, h->num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "refine launch");
+    h->last_stream = stream;
+    return EPIC_OK;
+}
+
 int epic_gradient_cost(const float *image, int frames, int H, int W, int channels,
                        float floor_, float *cost_out, void *stream) {
     if (!image || !cost_out || frames < 1 || H < 1 || W < 1 ||
@@ -1053,6 +1104,7 @@ void epic_interp_destroy(epic_interp_t *h) {
     if (h->io_M) cudaFree(h->io_M);
     if (h->io_F) cudaFree(h->io_F);
     if (h->ex_buf) cudaFree(h->ex_buf);
+    if (h->rf_buf) cudaFree(h->rf_buf);
     for (cudaEvent_t x : h->tev) cudaEventDestroy(x);
     delete h;
 }

@@ -40,6 +40,7 @@ EXPORTED = (
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
     "epic_geodesic_labels_noalloc", "epic_exact_interp", "epic_gradient_cost",
+    "epic_refine_params_default", "epic_refine",
 )
 
 
@@ -54,6 +55,14 @@ class epic_config_t(ctypes.Structure):
         ("max_degree", ctypes.c_int), ("use_graphs", ctypes.c_int),
         ("estimator", ctypes.c_int), ("prune", ctypes.c_int),
         ("prune_threshold", ctypes.c_float), ("prune_K", ctypes.c_int),
+    ]
+
+
+class epic_refine_params_t(ctypes.Structure):
+    _fields_ = [
+        ("alpha0", ctypes.c_float), ("gamma", ctypes.c_float), ("kappa", ctypes.c_float),
+        ("eps", ctypes.c_float), ("zeta", ctypes.c_float), ("omega", ctypes.c_float),
+        ("iterations", ctypes.c_int), ("sor_iterations", ctypes.c_int),
     ]
 
 
@@ -139,6 +148,10 @@ def load(path: str | None = None):
     lib.epic_interp_last_error.restype = ctypes.c_char_p
     lib.epic_interp_destroy.argtypes = [P]
     lib.epic_interp_destroy.restype = None
+    lib.epic_refine_params_default.argtypes = [ctypes.POINTER(epic_refine_params_t)]
+    lib.epic_refine_params_default.restype = None
+    lib.epic_refine.argtypes = [P, P, P, I, I, I, P, ctypes.POINTER(epic_refine_params_t), P]
+    lib.epic_refine.restype = I
     lib.epic_gradient_cost.argtypes = [P, I, I, I, I, F, P, P]
     lib.epic_gradient_cost.restype = I
     lib.epic_exact_interp.argtypes = [P, P, P, I, I, I, I, F, I, P, P, P, P]
@@ -329,6 +342,28 @@ class EpicInterp:
                                         _stream_handle(stream))
         self._check(rc, "epic_exact_interp")
         return (flow, idx, dist) if with_knn else flow
+
+    def refine(self, I1, I2, flow, stream=None, **params):
+        """Variational refinement (epic_refine) of the CUDA tensor flow
+        [H, W, 2] in place, between images I1, I2 [H, W] or [H, W, C]
+        (float32 CUDA tensors in [0, 1]); keyword overrides of the
+        parameters (alpha0, gamma, kappa, eps, zeta, omega, iterations,
+        sor_iterations).  Enqueued on `stream`."""
+        prm = epic_refine_params_t()
+        self.lib.epic_refine_params_default(ctypes.byref(prm))
+        for k, v in params.items():
+            if not hasattr(prm, k):
+                raise TypeError(f"unknown refinement parameter {k}")
+            setattr(prm, k, v)
+        H, W = I1.shape[:2]
+        C = 1 if I1.dim() == 2 else I1.shape[2]
+        for t in (I1, I2, flow):
+            if not t.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+        rc = self.lib.epic_refine(self.h, _ptr(I1), _ptr(I2), H, W, C, _ptr(flow),
+                                  ctypes.byref(prm), _stream_handle(stream))
+        self._check(rc, "epic_refine")
+        return flow
 
     def get_pruning(self, pair, N):
         """Consistency pruning of the last run's pair (prune = 1): keep

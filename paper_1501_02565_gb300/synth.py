@@ -416,3 +416,23 @@ def region_image(pair: Pair, seed: int = 0, channels: int = 3) -> np.ndarray:
         img += wave[..., None]
     img += rng.normal(0.0, 0.005, size=img.shape)
     return np.clip(img, 0.0, 1.0).astype(np.float32)
+
+
+def second_frame(image: np.ndarray, flow: np.ndarray) -> np.ndarray:
+    """A second frame for `image` under `flow` [H, W, 2]: I2(q) = I1(q - u(q)),
+    sampled bilinearly with clamped coordinates (a backward approximation of
+    moving every pixel p to p + u(p), exact for translations)."""
+    H, W = image.shape[:2]
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    X = np.clip(xs - flow[..., 0], 0, W - 1)
+    Y = np.clip(ys - flow[..., 1], 0, H - 1)
+    x0 = np.minimum(np.floor(X).astype(np.int64), max(W - 2, 0))
+    y0 = np.minimum(np.floor(Y).astype(np.int64), max(H - 2, 0))
+    x1 = np.minimum(x0 + 1, W - 1)
+    y1 = np.minimum(y0 + 1, H - 1)
+    ax = (X - x0)[..., None]
+    ay = (Y - y0)[..., None]
+    I = image.astype(np.float64)
+    out = ((1 - ay) * ((1 - ax) * I[y0, x0] + ax * I[y0, x1]) +
+           ay * ((1 - ax) * I[y1, x0] + ax * I[y1, x1]))
+    return out.astype(np.float32)

@@ -1,0 +1,81 @@
+"""Variational refinement on the GPU (epic_refine) vs the FP64 oracle
+(Sec. 4).  The GPU runs the same discretisation in float32; after 5
+fixed-point iterations x 30 red-black SOR iterations its flow is compared
+with the oracle's from the same inputs (tolerance REF_TOL px)."""
+
+import numpy as np
+import pytest
+
+from oracle import refine as R
+from paper_1501_02565_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REF_TOL = 2e-3
+
+
+def _gpu_refine(I1, I2, flow, **prm):
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    eng = EpicInterp(0)
+    try:
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+        f = t(flow)
+        eng.refine(t(I1), t(I2), f, **prm)
+        torch.cuda.synchronize()
+        return f.cpu().numpy()
+    finally:
+        eng.close()
+
+
+def _texture(H, W, seed, C=3):
+    rng = np.random.default_rng(seed)
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = np.full((H, W, C), 0.5)
+    for c in range(C):
+        for _ in range(3):
+            f = rng.uniform(0.1, 0.5, 2)
+            img[..., c] += rng.uniform(0.05, 0.15) * np.sin(f[0] * xs + f[1] * ys + rng.uniform(0, 6))
+    return img.astype(np.float32)
+
+
+@pytest.mark.parametrize("shape", [(37, 70, 3), (20, 33, 1)])
+def test_random_textures(shape):
+    H, W, C = shape
+    I1 = _texture(H, W, 1, C)
+    I2 = _texture(H, W, 2, C)
+    f0 = np.random.default_rng(3).normal(0, 1.0, (H, W, 2)).astype(np.float32)
+    g = _gpu_refine(I1, I2, f0)
+    ref = R.refine(I1, I2, f0)
+    err = np.abs(g - ref).max()
+    print(f"\n[refine {shape}] max |gpu - oracle| = {err:.3g} px, "
+          f"mean update {np.abs(ref - f0).mean():.3g} px")
+    assert err <= REF_TOL
+
+
+def test_identical_frames_keep_zero_flow_exactly():
+    I = _texture(24, 31, 4)
+    g = _gpu_refine(I, I, np.zeros((24, 31, 2), np.float32))
+    assert (g == 0).all()
+
+
+def test_refines_the_interpolated_flow_of_a_pair():
+    # interpolation, then refinement against a second frame made from the
+    # ground-truth flow; the oracle refines the same interpolated flow
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    p = synth.config_pair(1, 0)
+    I1 = synth.region_image(p, seed=1)
+    I2 = synth.second_frame(I1, p.gt_flow)
+    eng = EpicInterp(0)
+    f0 = eng.run(torch.from_numpy(p.C).cuda(), torch.from_numpy(p.matches).cuda(), p.K, p.a)
+    eng.sync()
+    flow0 = f0.cpu().numpy()
+    eng.close()
+    g = _gpu_refine(I1, I2, flow0)
+    ref = R.refine(I1, I2, flow0)
+    err = np.abs(g - ref).max()
+    aee = lambda f: float(np.hypot(*(f - p.gt_flow).transpose(2, 0, 1)).mean())
+    print(f"\n[refine config1] max |gpu - oracle| = {err:.3g} px; AEE to ground truth "
+          f"{aee(flow0):.3f} interpolated -> {aee(g):.3f} refined")
+    assert err <= REF_TOL
