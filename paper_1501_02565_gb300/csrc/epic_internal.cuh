@@ -9,6 +9,7 @@
 // the batch contents.
 #pragma once
 
+#include <cuda.h>            // CUtensorMap (type only; no driver library is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -111,6 +112,15 @@ struct PairDev {
     float4 *pruned;         // [N] kept matches, in their original order
     int *kept_index;        // [N] original index of each kept match
     int K2;                 // K of the second (LA) pass
+    // TMA staging of the relaxation's cost tiles (tma_cost = 0: plain loads):
+    // 2D tensor maps over C (W x H float32) with boxes of (bw, RH) for the
+    // phase-1 region (tile + apron + ring) and the re-solve region (tile +
+    // ring); bw covers the region from its x origin rounded down to a
+    // multiple of 4, as TMA requires 16-byte-aligned x coordinates.
+    int tma_cost;
+    int tma_bw_fresh, tma_bw_again;
+    CUtensorMap tm_cost_fresh;
+    CUtensorMap tm_cost_again;
 };
 
 struct GridBarrier {

@@ -189,6 +189,55 @@ PairDev make_pair_desc(const epic_config_t &c, const std::vector<epic_tile_rule_
     return P;
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver once through the runtime
+// (no link dependency on the driver library); null if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor maps for TMA staging of the relaxation's cost tiles; leaves
+// tma_cost = 0 (plain loads) when a TMA requirement does not hold: a
+// 16-byte-aligned base, a row pitch that is a multiple of 16 bytes, and box
+// sides of at most 256 elements.
+void encode_cost_maps(PairDev &P) {
+    P.tma_cost = 0;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || ((uintptr_t)P.C % 16) != 0 || ((size_t)P.W * 4) % 16 != 0) return;
+    const int rh_f = P.tile_h + 2 * P.apron + 2, rh_a = P.tile_h + 2;
+    const int bw_f = (P.tile_w + 2 * P.apron + 2 + 3 + 3) / 4 * 4;
+    const int bw_a = (P.tile_w + 2 + 3 + 3) / 4 * 4;
+    if (bw_f > 256 || rh_f > 256 || bw_a > 256 || rh_a > 256) return;
+    const cuuint64_t dims[2] = {(cuuint64_t)P.W, (cuuint64_t)P.H};
+    const cuuint64_t strides[1] = {(cuuint64_t)P.W * 4};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint32_t box_f[2] = {(cuuint32_t)bw_f, (cuuint32_t)rh_f};
+    const cuuint32_t box_a[2] = {(cuuint32_t)bw_a, (cuuint32_t)rh_a};
+    void *base = const_cast<float *>(P.C);
+    if (fn(&P.tm_cost_fresh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box_f, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        fn(&P.tm_cost_again, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box_a, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    P.tma_bw_fresh = bw_f;
+    P.tma_bw_again = bw_a;
+    P.tma_cost = 1;
+}
+
 int validate(epic_interp_t *h, const epic_pair_desc_t &d, int i) {
     char buf[256];
     if (!d.cost_map || !d.matches || !d.flow_out) {
@@ -410,6 +459,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     int rc = ensure_arena(h, off);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
+        encode_cost_maps(P[i]);
         char *b = h->arena;
         P[i].keys = reinterpret_cast<pkey_t *>(b + L[i].keys);
         P[i].tile_start = reinterpret_cast<int *>(b + L[i].tile_start);

@@ -184,26 +184,109 @@ __device__ int local_solve(pkey_t *K, const unsigned *h, const Region &g,
     return any;
 }
 
+// TMA staging: one mbarrier per CTA; every use is separated from the next by
+// __syncthreads, and all threads track its phase in `phase`.
+struct Tma {
+    unsigned mbar;   // shared-space address of the barrier
+    unsigned phase;
+};
+
+__device__ __forceinline__ void tma_init(Tma &t, unsigned long long *bar) {
+    t.mbar = (unsigned)__cvta_generic_to_shared(bar);
+    t.phase = 0;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(t.mbar) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// Thread 0 starts a 2D tensor copy of `bytes` bytes at (x, y) into `dst`.
+__device__ __forceinline__ void tma_load_2d(const Tma &t, const CUtensorMap *map, void *dst,
+                                            int x, int y, unsigned bytes) {
+    if (threadIdx.x != 0) return;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(t.mbar), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(d),
+        "l"(map), "r"(x), "r"(y), "r"(t.mbar)
+        : "memory");
+}
+
+// All threads wait for the copy, at most TMA_LIMIT_NS; on time-out the run
+// reports EPIC_ERR_TIMEOUT.
+constexpr unsigned long long TMA_LIMIT_NS = 1000000000ull;
+__device__ __forceinline__ void tma_wait(Tma &t, RunState *st) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+            " selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(t.mbar), "r"(t.phase)
+            : "memory");
+        if (done) break;
+        if (global_ns() - t0 > TMA_LIMIT_NS) {
+            set_status(st, EPIC_ERR_TIMEOUT);
+            break;
+        }
+    }
+    t.phase ^= 1u;
+}
+
 // Half-costs of the region in fixed-point units; a cost outside [0, C_MAX)
-// (or not finite) is an invalid input.
+// (or not finite) is an invalid input.  With TMA the region's costs are
+// first copied as one box into `stage` (free shared memory, 128-byte
+// aligned), from the region's x origin rounded down to a multiple of 4;
+// cells outside the image are filled with zeros by the copy and get h = 0
+// here, as on the plain path.
 __device__ __forceinline__ void load_costs(const PairDev &P, const Region &g,
-                                           unsigned *h, RunState *st) {
+                                           unsigned *h, RunState *st, bool fresh,
+                                           float *stage, Tma &tma) {
     bool bad = false;
-    for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
-        int r = i / g.RW, c = i - r * g.RW;
-        int gx = g.x0 + c, gy = g.y0 + r;
-        bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
-        h[r * g.P + c] = in ? half_cost(__ldg(P.C + (size_t)gy * P.W + gx), &bad) : 0u;
+    if (P.tma_cost) {
+        const int bw = fresh ? P.tma_bw_fresh : P.tma_bw_again;
+        const int xa = g.x0 - (((g.x0 % 4) + 4) % 4);
+        tma_load_2d(tma, fresh ? &P.tm_cost_fresh : &P.tm_cost_again, stage, xa, g.y0,
+                    (unsigned)(bw * g.RH * 4));
+        tma_wait(tma, st);
+        const int off = g.x0 - xa;
+        for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
+            int r = i / g.RW, c = i - r * g.RW;
+            int gx = g.x0 + c, gy = g.y0 + r;
+            bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+            h[r * g.P + c] = in ? half_cost(stage[r * bw + c + off], &bad) : 0u;
+        }
+        __syncthreads();   // the stage area is reused by the caller
+    } else {
+        for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
+            int r = i / g.RW, c = i - r * g.RW;
+            int gx = g.x0 + c, gy = g.y0 + r;
+            bool in = gx >= 0 && gx < P.W && gy >= 0 && gy < P.H;
+            h[r * g.P + c] = in ? half_cost(__ldg(P.C + (size_t)gy * P.W + gx), &bad) : 0u;
+        }
     }
     if (bad) set_status(st, EPIC_ERR_INVALID);
 }
 
+// The relaxation's shared memory: keys (RH x P), half-costs (RH x P); the
+// key area doubles as the TMA stage for the costs, which are converted
+// before the keys are written.
+__device__ __forceinline__ float *stage_area(unsigned char *smem) {
+    return reinterpret_cast<float *>(((uintptr_t)smem + 127) & ~(uintptr_t)127);
+}
+
 // Phase 1: solve tile (tx, ty) on its region from its seeds alone.
 __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
-                            unsigned *h, RunState *st) {
+                            unsigned *h, RunState *st, float *stage, Tma &tma) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, P.apron);
-    load_costs(P, g, h, st);
+    load_costs(P, g, h, st, true, stage, tma);
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         K[r * g.P + c] = KEY_INF;
@@ -286,10 +369,10 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
 
 // Phase 2 re-solve of tile (tx, ty) from the current keys (tile + ring).
 __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
-                            unsigned *h, RunState *st, int pass) {
+                            unsigned *h, RunState *st, int pass, float *stage, Tma &tma) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, 0);
-    load_costs(P, g, h, st);
+    load_costs(P, g, h, st, false, stage, tma);
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         int gx = g.x0 + c, gy = g.y0 + r;
@@ -336,6 +419,10 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
     const unsigned nblocks = min(gridDim.x, (unsigned)a.total_tiles);
     if (blockIdx.x >= nblocks) return;
     __shared__ int s_pair, s_local, s_tile;
+    __shared__ __align__(8) unsigned long long s_bar;
+    Tma tma;
+    tma_init(tma, &s_bar);
+    float *stage = stage_area(smem);
     // tiles are handed out one at a time from a counter, so that CTAs whose
     // tiles converge quickly take more of them
     auto next_tile = [&](unsigned *dispenser) {
@@ -358,7 +445,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
         const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, P.apron);
         pkey_t *K = reinterpret_cast<pkey_t *>(smem);
         unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-        solve_fresh(P, s_local % P.tiles_x, s_local / P.tiles_x, K, h, st);
+        solve_fresh(P, s_local % P.tiles_x, s_local / P.tiles_x, K, h, st, stage, tma);
     }
     if (!grid_sync(st, nblocks)) return;
 
@@ -383,7 +470,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                 const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                 pkey_t *K = reinterpret_cast<pkey_t *>(smem);
                 unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-                solve_again(P, tx, ty, K, h, st, pass + 1);
+                solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
                 if (threadIdx.x == 0) atomicAdd(cnt, 1u);
             }
             __syncthreads();
@@ -408,7 +495,9 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
 size_t dt_smem_bytes(int tile_w, int tile_h, int apron) {
     int RW = tile_w + 2 * apron + 2, RH = tile_h + 2 * apron + 2;
     int P = RW | 1;
-    return (size_t)RH * P * (sizeof(pkey_t) + sizeof(unsigned));
+    // keys and half-costs, plus alignment slack for the TMA stage; the stage
+    // (RH x (RW + 6) floats at most) fits in the key area (RH x P x 8 bytes)
+    return (size_t)RH * P * (sizeof(pkey_t) + sizeof(unsigned)) + 128;
 }
 
 cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,

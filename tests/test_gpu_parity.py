@@ -135,3 +135,27 @@ def test_graph_replay_matches_plain_launches():
             assert np.array_equal(fg, fp)
     eng_g.close()
     eng_p.close()
+
+
+def test_tma_and_plain_cost_staging_agree():
+    # the relaxation stages cost tiles by TMA when the cost map is 16-byte
+    # aligned with a row pitch that is a multiple of 16 bytes, else with
+    # plain loads: a cost map placed 4 bytes off alignment takes the plain
+    # path, and every result must be bit-identical
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    p = synth.config_pair(1, 2)
+    M = torch.from_numpy(p.matches).cuda()
+    out = []
+    for offset in (0, 1):
+        buf = torch.zeros(p.P + 4, dtype=torch.float32, device="cuda")
+        C = buf[offset:offset + p.P].view(p.H, p.W)
+        C.copy_(torch.from_numpy(p.C))
+        eng = EpicInterp(0, keep_intermediates=1)
+        flow = eng.run(C, M, p.K, p.a)
+        eng.sync()
+        L, D = eng.get_labels(0, p.H, p.W)
+        out.append((flow.cpu().numpy(), L.cpu().numpy(), D.cpu().numpy()))
+        eng.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
