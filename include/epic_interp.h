@@ -105,6 +105,8 @@ typedef struct {
                              passes, the pair keeps all its matches. */
     float prune_threshold; /* px (default 5) */
     int prune_K;          /* neighbours of the NW pass (default 25) */
+    int sweep;            /* relaxation sweep schedule when no tile rule
+                             applies (see epic_tile_rule_t; default 0) */
 } epic_config_t;
 
 /* One frame pair of a batch; pointers are device pointers. */
@@ -117,10 +119,13 @@ typedef struct {
 } epic_pair_desc_t;
 
 /* A relaxation tile rule: frames of at most max_pixels pixels use tiles of
- * tile_w x tile_h with the given first-pass apron. */
+ * tile_w x tile_h with the given first-pass apron and sweep schedule
+ * (0: lines cut into segments so every thread of the CTA has one; 1: a
+ * thread sweeps whole lines). */
 typedef struct {
     long long max_pixels;
     int tile_w, tile_h, apron;
+    int sweep;
 } epic_tile_rule_t;
 
 /* Fill *cfg with defaults (sizes for a 1024x436 frame, 5000 matches,

@@ -86,6 +86,7 @@ struct PairDev {
     int H, W, N, K;
     float a;
     int tile_w, tile_h, apron;
+    int sweep;              // relaxation sweep schedule (0 segmented lines, 1 whole lines)
     int tiles_x, tiles_y;
     int hash_cap;           // power of two
     int flow_vec_ok;        // flow pointer is 16-byte aligned

@@ -109,19 +109,21 @@ int next_pow2(long long x) {
 // Tile shape for the relaxation of an H x W frame: the first installed rule
 // covering the frame, else the configured tile (64 x 32, apron 4 by default).
 void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &rules, int H,
-                  int W, int *tw, int *th, int *ap) {
+                  int W, int *tw, int *th, int *ap, int *sweep = nullptr) {
     const long long P = (long long)H * W;
     for (const auto &r : rules) {
         if (P <= r.max_pixels) {
             *tw = r.tile_w;
             *th = r.tile_h;
             *ap = r.apron;
+            if (sweep) *sweep = r.sweep;
             return;
         }
     }
     *tw = c.tile_w > 0 ? c.tile_w : 64;
     *th = c.tile_h > 0 ? c.tile_h : 32;
     *ap = c.apron >= 0 ? c.apron : 4;
+    if (sweep) *sweep = c.sweep;
 }
 
 struct Layout {
@@ -181,7 +183,7 @@ PairDev make_pair_desc(const epic_config_t &c, const std::vector<epic_tile_rule_
         P.K = std::min(c.prune_K, d.N);
     }
     P.a = d.a;
-    choose_tiles(c, rules, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron);
+    choose_tiles(c, rules, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron, &P.sweep);
     P.tiles_x = (d.W + P.tile_w - 1) / P.tile_w;
     P.tiles_y = (d.H + P.tile_h - 1) / P.tile_h;
     P.hash_cap = std::max(1024, next_pow2(8LL * d.N));
@@ -377,6 +379,7 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     if (!(c.fallback_eps > 0.f)) c.fallback_eps = 1e-10f;
     if (c.max_pairs <= 0) c.max_pairs = 1;
     if (c.prune_K <= 0) c.prune_K = 25;
+    if (c.sweep != 0 && c.sweep != 1) c.sweep = 0;
     if ((c.estimator != 0 && c.estimator != 1) || !(c.prune_threshold >= 0.f) ||
         !std::isfinite(c.prune_threshold)) {
         int r = fail(h, EPIC_ERR_INVALID, "estimator must be 0 or 1, prune_threshold finite >= 0");
@@ -878,7 +881,8 @@ int epic_interp_set_tile_rules(epic_interp_t *h, const epic_tile_rule_t *rules, 
     std::vector<epic_tile_rule_t> v(rules, rules + n);
     for (const auto &r : v) {
         if (r.tile_w < 8 || r.tile_h < 8 || r.tile_w > 256 || r.tile_h > 256 || r.apron < 0 ||
-            r.apron > 64 || r.apron + 1 > std::min(r.tile_w, r.tile_h) || r.max_pixels < 1)
+            r.apron > 64 || r.apron + 1 > std::min(r.tile_w, r.tile_h) || r.max_pixels < 1 ||
+            (r.sweep != 0 && r.sweep != 1))
             return fail(h, EPIC_ERR_INVALID, "tile rule out of range");
         if (epic::dt_smem_bytes(r.tile_w, r.tile_h, r.apron) > (size_t)h->smem_optin)
             return fail(h, EPIC_ERR_INVALID, "tile rule does not fit in shared memory");
@@ -944,8 +948,8 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
     if (metric == 0) {
         // single-source relaxations, Cm matches at a time, each a pseudo-pair
         // with one seed; their distances become row m of D [N][P]
-        int tw, th, ap;
-        choose_tiles(c, h->rules, H, W, &tw, &th, &ap);
+        int tw, th, ap, sw;
+        choose_tiles(c, h->rules, H, W, &tw, &th, &ap, &sw);
         const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th, T = tx * ty;
         const long long Cm = std::max(1LL, std::min((long long)N, (1LL << 30) / (P * 8)));
         const size_t small_ints = (size_t)(T + 1) + T + 1 + T + 1 + 1 + 4;  // per pseudo-pair
@@ -994,6 +998,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
                 q.tile_w = tw;
                 q.tile_h = th;
                 q.apron = ap;
+                q.sweep = sw;
                 q.tiles_x = tx;
                 q.tiles_y = ty;
                 q.keys = keys + (size_t)j * P;

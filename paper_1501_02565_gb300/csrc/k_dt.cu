@@ -130,52 +130,82 @@ __device__ __forceinline__ int relax3(pkey_t *K, const unsigned *h, int idx,
 }
 
 // Sweep the region to its fixed point.  Returns 1 if any key changed.
+//
+// Sweep schedule: a vertical sweep runs down (or up) every column of the
+// region, a horizontal one along every row.  With whole = 0 each line is cut
+// into segments so that all threads of the CTA have a segment (more threads
+// busy, but a key crosses one segment boundary per iteration); with whole = 1
+// a thread runs whole lines (fewer threads busy, fewer iterations).  A
+// thread takes work items (column or row segments) with a stride of the
+// CTA size, so regions with more lines than threads are covered too; lanes
+// of a warp step through adjacent lines together.  Any schedule reaches the
+// same fixed point.
 __device__ int local_solve(pkey_t *K, const unsigned *h, const Region &g,
-                           RunState *st) {
+                           RunState *st, int whole) {
     const int ncols = g.bx1 - g.bx0 + 1, nrows = g.by1 - g.by0 + 1;
     if (ncols <= 0 || nrows <= 0) return 0;
     const int T = blockDim.x, tid = threadIdx.x, P = g.P;
-    // vertical sweeps: a thread owns a column segment
-    const int nsegV = max(1, T / ncols);
+    const int nsegV = whole ? 1 : max(1, T / ncols);
     const int segV = (nrows + nsegV - 1) / nsegV;
-    const bool vu = tid < ncols * nsegV;
-    const int vx = g.bx0 + tid % ncols;
-    const int vy0 = g.by0 + (tid / ncols) * segV;
-    const int vy1 = min(g.by1, vy0 + segV - 1);
-    // horizontal sweeps: a thread owns a row segment
-    const int nsegH = max(1, T / nrows);
+    const int itemsV = ncols * nsegV, roundsV = (itemsV + T - 1) / T;
+    const int nsegH = whole ? 1 : max(1, T / nrows);
     const int segH = (ncols + nsegH - 1) / nsegH;
-    const bool hu = tid < nrows * nsegH;
-    const int hy = g.by0 + tid % nrows;
-    const int hx0 = g.bx0 + (tid / nrows) * segH;
-    const int hx1 = min(g.bx1, hx0 + segH - 1);
+    const int itemsH = nrows * nsegH, roundsH = (itemsH + T - 1) / T;
 
     const int cap = g.RW * g.RH;  // Bellman-Ford bound on useful iterations
     int any = 0;
     for (int it = 0; it < cap; ++it) {
         int ch = 0;
-        for (int s = 0; s < segV; ++s) {  // down: from the row above
-            int y = vy0 + s;
-            if (vu && y <= vy1) ch |= relax3(K, h, y * P + vx, -P, -P - 1, -P + 1);
-            __syncwarp();
+        for (int rv = 0; rv < roundsV; ++rv) {   // down: from the row above
+            const int w = tid + rv * T;
+            const bool vu = w < itemsV;
+            const int vx = g.bx0 + w % ncols;
+            const int vy0 = g.by0 + (w / ncols) * segV;
+            const int vy1 = min(g.by1, vy0 + segV - 1);
+            for (int s = 0; s < segV; ++s) {
+                int y = vy0 + s;
+                if (vu && y <= vy1) ch |= relax3(K, h, y * P + vx, -P, -P - 1, -P + 1);
+                __syncwarp();
+            }
         }
         __syncthreads();
-        for (int s = 0; s < segV; ++s) {  // up: from the row below
-            int y = vy1 - s;
-            if (vu && y >= vy0) ch |= relax3(K, h, y * P + vx, P, P - 1, P + 1);
-            __syncwarp();
+        for (int rv = 0; rv < roundsV; ++rv) {   // up: from the row below
+            const int w = tid + rv * T;
+            const bool vu = w < itemsV;
+            const int vx = g.bx0 + w % ncols;
+            const int vy0 = g.by0 + (w / ncols) * segV;
+            const int vy1 = min(g.by1, vy0 + segV - 1);
+            for (int s = 0; s < segV; ++s) {
+                int y = vy1 - s;
+                if (vu && y >= vy0) ch |= relax3(K, h, y * P + vx, P, P - 1, P + 1);
+                __syncwarp();
+            }
         }
         __syncthreads();
-        for (int s = 0; s < segH; ++s) {  // right: from the column on the left
-            int x = hx0 + s;
-            if (hu && x <= hx1) ch |= relax3(K, h, hy * P + x, -1, -1 - P, -1 + P);
-            __syncwarp();
+        for (int rh = 0; rh < roundsH; ++rh) {   // right: from the column on the left
+            const int w = tid + rh * T;
+            const bool hu = w < itemsH;
+            const int hy = g.by0 + w % nrows;
+            const int hx0 = g.bx0 + (w / nrows) * segH;
+            const int hx1 = min(g.bx1, hx0 + segH - 1);
+            for (int s = 0; s < segH; ++s) {
+                int x = hx0 + s;
+                if (hu && x <= hx1) ch |= relax3(K, h, hy * P + x, -1, -1 - P, -1 + P);
+                __syncwarp();
+            }
         }
         __syncthreads();
-        for (int s = 0; s < segH; ++s) {  // left: from the column on the right
-            int x = hx1 - s;
-            if (hu && x >= hx0) ch |= relax3(K, h, hy * P + x, 1, 1 - P, 1 + P);
-            __syncwarp();
+        for (int rh = 0; rh < roundsH; ++rh) {   // left: from the column on the right
+            const int w = tid + rh * T;
+            const bool hu = w < itemsH;
+            const int hy = g.by0 + w % nrows;
+            const int hx0 = g.bx0 + (w / nrows) * segH;
+            const int hx1 = min(g.bx1, hx0 + segH - 1);
+            for (int s = 0; s < segH; ++s) {
+                int x = hx1 - s;
+                if (hu && x >= hx0) ch |= relax3(K, h, hy * P + x, 1, 1 - P, 1 + P);
+                __syncwarp();
+            }
         }
         if (!__syncthreads_or(ch)) return any;
         any = 1;
@@ -312,7 +342,7 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
         }
     }
     __syncthreads();
-    local_solve(K, h, g, st);
+    local_solve(K, h, g, st, P.sweep);
     // write the tile's own pixels and mark it written in pass 0
     if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = 0;
     const int off = P.apron + 1;
@@ -380,7 +410,7 @@ __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
         K[r * g.P + c] = in ? ld_key(P.keys + (size_t)gy * P.W + gx) : KEY_INF;
     }
     __syncthreads();
-    if (local_solve(K, h, g, st)) {
+    if (local_solve(K, h, g, st, P.sweep)) {
         for (int i = threadIdx.x; i < P.tile_w * P.tile_h; i += blockDim.x) {
             int ly = i / P.tile_w, lx = i - ly * P.tile_w;
             int gx = gx0 + lx, gy = gy0 + ly;

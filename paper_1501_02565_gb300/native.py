@@ -55,6 +55,7 @@ class epic_config_t(ctypes.Structure):
         ("max_degree", ctypes.c_int), ("use_graphs", ctypes.c_int),
         ("estimator", ctypes.c_int), ("prune", ctypes.c_int),
         ("prune_threshold", ctypes.c_float), ("prune_K", ctypes.c_int),
+        ("sweep", ctypes.c_int),
     ]
 
 
@@ -78,7 +79,7 @@ class epic_pair_desc_t(ctypes.Structure):
 class epic_tile_rule_t(ctypes.Structure):
     _fields_ = [
         ("max_pixels", ctypes.c_longlong), ("tile_w", ctypes.c_int),
-        ("tile_h", ctypes.c_int), ("apron", ctypes.c_int),
+        ("tile_h", ctypes.c_int), ("apron", ctypes.c_int), ("sweep", ctypes.c_int),
     ]
 
 
@@ -386,11 +387,13 @@ class EpicInterp:
     STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout", "prune")
 
     def set_tile_rules(self, rules):
-        """rules: iterable of (max_pixels, tile_w, tile_h, apron)."""
+        """rules: iterable of (max_pixels, tile_w, tile_h, apron[, sweep])."""
         rules = list(rules)
         arr = (epic_tile_rule_t * max(len(rules), 1))()
-        for i, (mp, tw, th, ap) in enumerate(rules):
-            arr[i] = epic_tile_rule_t(int(mp), int(tw), int(th), int(ap))
+        for i, r in enumerate(rules):
+            mp, tw, th, ap = r[:4]
+            sw = r[4] if len(r) > 4 else 0
+            arr[i] = epic_tile_rule_t(int(mp), int(tw), int(th), int(ap), int(sw))
         self._check(self.lib.epic_interp_set_tile_rules(self.h, arr, len(rules)),
                     "set_tile_rules")
 

@@ -1,13 +1,15 @@
-"""Autotuner for the relaxation's tile shape.
+"""Autotuner for the relaxation's tile shape and sweep schedule.
 
 The tile (width x height, plus the apron of context used in the first pass)
-changes only speed, never results: every tiling reaches the same fixed point
-of the relaxation.  Which tile is fastest depends on the frame size (how
-many tiles there are to fill the GPU), the batch size and the match density,
-so the tuner times candidate shapes on sample pairs of each size class with
-the library's own per-stage CUDA-event timing and installs the winners as
-tile rules (``epic_interp_set_tile_rules``).  Results are cached in a JSON
-file keyed by GPU name and size class.
+and the sweep schedule (lines cut into segments for every thread, or whole
+lines per thread) change only speed, never results: every tiling and
+schedule reaches the same fixed point of the relaxation.  Which is fastest
+depends on the frame size (how many tiles there are to fill the GPU), the
+batch size and the match density, so the tuner times candidates on sample
+pairs of each size class with the library's own per-stage CUDA-event
+timing and installs the winners as tile rules
+(``epic_interp_set_tile_rules``).  Results are cached in a JSON file keyed
+by GPU name and size class.
 """
 
 from __future__ import annotations
@@ -15,11 +17,12 @@ from __future__ import annotations
 import json
 import os
 
-# (tile_w, tile_h, apron): the region (tile + 2 apron) stays within shared
-# memory at 256 threads per CTA
+# (tile_w, tile_h, apron, sweep): the region (tile + 2 apron) stays within
+# shared memory at 256 threads per CTA
 CANDIDATES = (
-    (64, 32, 4), (32, 32, 4), (64, 32, 0), (64, 32, 8), (48, 48, 8),
-    (64, 64, 8), (96, 32, 4), (128, 32, 4), (32, 16, 2), (128, 64, 8),
+    (64, 32, 4, 0), (32, 32, 4, 0), (64, 32, 0, 0), (64, 32, 8, 0), (48, 48, 8, 0),
+    (64, 64, 8, 0), (96, 32, 4, 0), (128, 32, 4, 0), (32, 16, 2, 0), (128, 64, 8, 0),
+    (64, 32, 8, 1), (48, 48, 8, 1), (32, 32, 4, 1),
 )
 
 # size classes: upper pixel bounds (a frame uses the first class that holds it)
@@ -42,7 +45,7 @@ def group_by_class(pairs):
 
 
 def rules_from_choice(choice):
-    """{class bound: (tw, th, apron)} -> sorted rule list for the library."""
+    """{class bound: (tw, th, apron[, sweep])} -> sorted rule list for the library."""
     return [(bound, *choice[bound]) for bound in sorted(choice)]
 
 
@@ -51,8 +54,9 @@ def time_candidate(pairs, tile, device=0, reps=3, warmup=2):
     tile affects) on one batch of `pairs`."""
     import torch
     from .native import EpicInterp
-    tw, th, ap = tile
-    eng = EpicInterp(device, tile_w=tw, tile_h=th, apron=ap, max_pairs=len(pairs))
+    tw, th, ap = tile[:3]
+    sw = tile[3] if len(tile) > 3 else 0
+    eng = EpicInterp(device, tile_w=tw, tile_h=th, apron=ap, sweep=sw, max_pairs=len(pairs))
     try:
         dev = torch.device("cuda", device)
         items = [(torch.from_numpy(p.C).to(dev), torch.from_numpy(p.matches).to(dev), p.K, p.a,
@@ -84,8 +88,9 @@ def autotune(pairs, device=0, candidates=CANDIDATES, reps=3, max_batch=32, log=N
                     log(f"tile {tile} skipped: {exc}")
         best = min(times, key=times.get)
         choice[bound] = best
-        report[bound] = {"best": list(best), "ms": {f"{t[0]}x{t[1]}+{t[2]}": v
-                                                    for t, v in times.items()},
+        report[bound] = {"best": list(best),
+                         "ms": {f"{t[0]}x{t[1]}+{t[2]}" + ("w" if len(t) > 3 and t[3] else ""): v
+                                for t, v in times.items()},
                          "pairs": len(sample)}
     return rules_from_choice(choice), report
 

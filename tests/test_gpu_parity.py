@@ -33,12 +33,14 @@ def test_small_random_cases_several_tiles_ragged_tail(seed):
     _print(f"random{seed}", rep)
 
 
-@pytest.mark.parametrize("tile", [(8, 8, 0), (16, 8, 3), (32, 32, 0), (64, 32, 4), (128, 64, 8)])
+@pytest.mark.parametrize("tile", [(8, 8, 0, 0), (16, 8, 3, 1), (32, 32, 0, 0), (64, 32, 4, 1),
+                                  (128, 64, 8, 0), (256, 16, 8, 0), (256, 16, 8, 1)])
 def test_tile_shapes_give_identical_keys(tile):
-    # every tile shape reaches the same fixed point bit for bit
+    # every tile shape and sweep schedule reaches the same fixed point bit
+    # for bit (256-wide tiles have more region columns than CTA threads)
     p = synth.config_pair(1, 1)
-    tw, th, ap = tile
-    g = run_gpu(p, tile_w=tw, tile_h=th, apron=ap)
+    tw, th, ap, sw = tile
+    g = run_gpu(p, tile_w=tw, tile_h=th, apron=ap, sweep=sw)
     base = run_gpu(p, tile_w=64, tile_h=32, apron=4)
     assert np.array_equal(g["L"], base["L"])
     assert np.array_equal(g["D"], base["D"])

@@ -31,9 +31,11 @@ def test_cache_round_trip(tmp_path):
 
 
 def test_candidates_are_valid_tiles():
-    for tw, th, ap in tune.CANDIDATES:
+    for tw, th, ap, sw in tune.CANDIDATES:
         assert 8 <= tw <= 256 and 8 <= th <= 256 and 0 <= ap <= 64
         assert ap + 1 <= min(tw, th)
+        assert sw in (0, 1)
+    assert any(c[3] == 1 for c in tune.CANDIDATES) and any(c[3] == 0 for c in tune.CANDIDATES)
 
 
 @pytest.mark.gpu
