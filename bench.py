@@ -399,9 +399,7 @@ def run_ours(args, rank, world, local_rank):
     geng.close()
 
     # ---- with consistency pruning (Sec. 4.1): two passes per run --------
-    # pruning merges the removed matches' cells into their neighbours', so
-    # the second pass's graph has higher node degrees: wider adjacency rows
-    peng = EpicInterp(local_rank, max_pairs=B, prune=1, max_degree=64)
+    peng = EpicInterp(local_rank, max_pairs=B, prune=1)
     if tile_rules:
         peng.set_tile_rules(tile_rules)
     for _ in range(3):

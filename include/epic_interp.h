@@ -86,7 +86,8 @@ typedef struct {
     int apron;            /* extra context around a tile in the first
                              relaxation pass (-1 = chosen per frame size) */
     int keep_intermediates; /* 1: keep K-NN lists for epic_interp_get_knn */
-    int max_degree;       /* match-graph adjacency row capacity (default 32) */
+    int max_degree;       /* ignored: the match graph is stored as CSR rows
+                             with no degree limit */
     int use_graphs;       /* 1: capture the launch sequence once per table
                              slot and replay it as a CUDA graph (needs a
                              non-default stream, K <= max_K and tiles no

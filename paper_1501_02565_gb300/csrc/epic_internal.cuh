@@ -97,9 +97,10 @@ struct PairDev {
     int *tile_stamp;        // [tiles] last relaxation pass that wrote the tile
     pkey_t *hkeys;           // [hash_cap] (m << 32 | n), m < n
     unsigned *hw;           // [hash_cap] float bits of the edge weight
-    int *deg;               // [N] node degree in G
+    int *deg;               // [N] node degree in G, then the CSR fill cursor
     unsigned *wmin;         // [N] float bits of the lightest edge at each node
-    pkey_t *adj;             // [N * max_degree] (w bits << 32 | neighbour)
+    int *row;               // [N + 1] CSR row offsets into adj
+    pkey_t *adj;             // [2 * hash_cap] CSR rows (w bits << 32 | neighbour)
     float4 *models;         // [N * 2] (c_u, c_v, b11, b12), (b21, b22, x_m, y_m)
     int *fallback;          // [N]
     int *knn_idx;           // [N*K] or null

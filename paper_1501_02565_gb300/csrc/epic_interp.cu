@@ -127,7 +127,7 @@ void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &r
 }
 
 struct Layout {
-    size_t keys, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, adj, models,
+    size_t keys, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, row, adj, models,
         fallback, knn_idx, knn_dist, knn_count, info, keep, pruned, kept_index, end;
 };
 
@@ -153,7 +153,10 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep, boo
     L.hw = take((size_t)P.hash_cap * sizeof(unsigned));
     L.deg = take((size_t)P.N * sizeof(int));
     L.wmin = take((size_t)P.N * sizeof(unsigned));
-    L.adj = take((size_t)P.N * max_degree * sizeof(pkey_t));
+    L.row = take(((size_t)P.N + 1) * sizeof(int));
+    // CSR adjacency: at most one entry per direction of every table slot
+    L.adj = take((size_t)P.hash_cap * 2 * sizeof(pkey_t));
+    (void)max_degree;
     L.models = take((size_t)P.N * 2 * sizeof(float4));
     L.fallback = take((size_t)P.N * sizeof(int));
     L.knn_idx = keep ? take((size_t)P.N * knn_cap(P) * sizeof(int)) : 0;
@@ -473,6 +476,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         P[i].hw = reinterpret_cast<unsigned *>(b + L[i].hw);
         P[i].deg = reinterpret_cast<int *>(b + L[i].deg);
         P[i].wmin = reinterpret_cast<unsigned *>(b + L[i].wmin);
+        P[i].row = reinterpret_cast<int *>(b + L[i].row);
         P[i].adj = reinterpret_cast<pkey_t *>(b + L[i].adj);
         P[i].models = reinterpret_cast<float4 *>(b + L[i].models);
         P[i].fallback = reinterpret_cast<int *>(b + L[i].fallback);
@@ -502,8 +506,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         tm += P[i].N;
         tc += ((long long)P[i].H * P[i].W + epic::WRITEOUT_CHUNK - 1) / epic::WRITEOUT_CHUNK;
         th += P[i].hash_cap;
-        tcl += ((long long)P[i].hash_cap + (long long)P[i].N * c.max_degree +
-                epic::CLEAR_CHUNK - 1) / epic::CLEAR_CHUNK;
+        tcl += ((long long)P[i].hash_cap + epic::CLEAR_CHUNK - 1) / epic::CLEAR_CHUNK;
     }
     if (tt > INT32_MAX || tm > INT32_MAX || tc > INT32_MAX || th > INT32_MAX || tcl > INT32_MAX)
         return fail(h, EPIC_ERR_INVALID, "batch too large");
@@ -1132,9 +1135,9 @@ int epic_gradient_cost(const float *image, int frames, int H, int W, int channel
 
 int epic_interp_launches_per_run(epic_interp_t *h, int n) {
     (void)n;
-    // prepare, relaxation, edges, scatter, K-NN + fit, write-out; pruning
-    // adds the first pass's five and the compaction
-    return h && h->cfg.prune ? 12 : 6;
+    // prepare, relaxation, edges, CSR offsets, scatter, K-NN + fit,
+    // write-out; pruning adds the first pass's six and the compaction
+    return h && h->cfg.prune ? 14 : 7;
 }
 
 const char *epic_interp_last_error(epic_interp_t *h) {

@@ -19,9 +19,14 @@
 //                open-addressing table.  A match whose source pixel is owned
 //                by a smaller index (a duplicate) is joined to the owner at
 //                distance D = 0.
+//                The insertion that creates an edge counts it in both
+//                endpoints' degrees; every insertion lowers both endpoints'
+//                lightest-edge weight.
+// offsets_kernel one CTA per pair: exclusive scan of the degrees into the
+//                CSR row offsets; the degree array becomes the fill cursor.
 // scatter_kernel every occupied slot appends (w, n) to row m and (w, m) to
-//                row n of a fixed-capacity adjacency array, and lowers the
-//                lightest-edge weight of both nodes.
+//                row n of the CSR adjacency (order within a row unspecified;
+//                the K-NN search does not depend on it).
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -36,10 +41,18 @@ __device__ __forceinline__ unsigned hash_slot(pkey_t k, int cap) {
 __device__ __forceinline__ void table_insert(const PairDev &P, pkey_t k,
                                              unsigned wbits, RunState *st) {
     unsigned s = hash_slot(k, P.hash_cap);
+    const unsigned m = (unsigned)(k >> 32), n = (unsigned)k;
     for (int probe = 0; probe < P.hash_cap; ++probe) {
         pkey_t prev = atomicCAS(P.hkeys + s, EMPTY64, k);
         if (prev == EMPTY64 || prev == k) {
             atomicMin(P.hw + s, wbits);  // weights are >= 0: bit order = value order
+            if (prev == EMPTY64) {       // a new edge
+                atomicAdd(P.deg + m, 1);
+                atomicAdd(P.deg + n, 1);
+                atomicAdd(P.info + 0, 1);
+            }
+            atomicMin(P.wmin + m, wbits);
+            atomicMin(P.wmin + n, wbits);
             return;
         }
         s = (s + 1) & (unsigned)(P.hash_cap - 1);
@@ -176,11 +189,67 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
     }
 }
 
+// Exclusive scan of v[0..n) into out[0..n] (out[n] = total) and v[i] =
+// out[i], by one CTA; returns the largest v[i] to thread 0.
+__device__ int block_offsets(int *v, int *out, int n) {
+    __shared__ int warp_sums[32];
+    __shared__ int carry, vmax;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) { carry = 0; vmax = 0; }
+    __syncthreads();
+    int mx = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        const int x = i < n ? v[i] : 0;
+        mx = max(mx, x);
+        int sc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += t;
+        }
+        if (lane == 31) warp_sums[wid] = sc;
+        __syncthreads();
+        if (wid == 0) {
+            int ws = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += t;
+            }
+            warp_sums[lane] = ws;
+        }
+        __syncthreads();
+        const int excl = carry + sc - x + (wid > 0 ? warp_sums[wid - 1] : 0);
+        if (i < n) {
+            out[i] = excl;
+            v[i] = excl;   // the fill cursor of row i
+        }
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = excl + x;
+        __syncthreads();
+    }
+    atomicMax(&vmax, mx);
+    __syncthreads();
+    if (tid == 0) out[n] = carry;
+    return vmax;
+}
+
+__global__ void __launch_bounds__(1024) offsets_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
+    if (get_status(a.state) != 0) return;
+    for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {
+        const PairDev &P = a.pairs[p];
+        const int mx = block_offsets(P.deg, P.row, P.N);
+        if (threadIdx.x == 0) P.info[1] = mx;
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256) scatter_kernel(const BatchArgs *__restrict__ ap) {
     const BatchArgs a = *ap;
     RunState *st = a.state;
     if (get_status(st) != 0) return;
-    const int md = a.max_degree;
     for (int gs = blockIdx.x * blockDim.x + threadIdx.x; gs < a.total_hash;
          gs += gridDim.x * blockDim.x) {
         const int p = find_pair(a.hash_base, a.npairs, gs);
@@ -194,15 +263,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(const BatchArgs *__restric
             continue;
         }
         const pkey_t wb = (pkey_t)P.hw[s] << 32;
-        const int pm = atomicAdd(P.deg + m, 1);
-        const int pn = atomicAdd(P.deg + n, 1);
-        if (pm < md) P.adj[(size_t)m * md + pm] = wb | n;
-        if (pn < md) P.adj[(size_t)n * md + pn] = wb | m;
-        if (pm >= md || pn >= md) set_status(st, EPIC_ERR_CAPACITY);
-        atomicMin(P.wmin + m, P.hw[s]);
-        atomicMin(P.wmin + n, P.hw[s]);
-        atomicAdd(P.info + 0, 1);
-        atomicMax(P.info + 1, max(pm, pn) + 1);
+        P.adj[atomicAdd(P.deg + m, 1)] = wb | n;
+        P.adj[atomicAdd(P.deg + n, 1)] = wb | m;
     }
 }
 
@@ -238,7 +300,10 @@ cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchC
 }
 
 cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
-    (void)a;
+    int g = a.npairs < lc.num_sms ? a.npairs : lc.num_sms;
+    offsets_kernel<<<g < 1 ? 1 : g, 1024, 0, lc.stream>>>(dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     scatter_kernel<<<lc.num_sms * 4, 256, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }

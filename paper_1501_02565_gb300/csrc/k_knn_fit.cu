@@ -24,8 +24,8 @@
 // sorted (warp bitonic network) so that exactly the K smallest keys are
 // kept, and the finished list is sorted once more (all keys) before the fit.  All edges of all batch nodes are relaxed in one
 // pass: lanes take (node, edge) pairs found from a warp prefix sum of the
-// batch nodes' degrees.  A newly pushed node's adjacency row, degree and
-// lightest edge are prefetched into L1 for when it is settled.
+// batch nodes' degrees (CSR row lengths).  A newly pushed node's row offsets
+// and lightest edge are prefetched into L1 for when it is settled.
 //
 // The fit uses centred coordinates x~ = p_n - p_m and fits the flow
 // u = p' - p (the same least-squares problem as fitting p', Eq. 2, with
@@ -159,7 +159,6 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
     unsigned *hv = hk + HS;
     unsigned *rn = hv + HS;
     float *rd = reinterpret_cast<float *>(rn + KM);
-    const int md = a.max_degree;
     const unsigned lt_mask = (1u << lane) - 1u;
 
     // matches are handed out one at a time from a counter: search costs
@@ -308,7 +307,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                 const int bi = b0 + lane;
                 const bool hb = bi < nb;
                 const pkey_t vk = hb ? make_key(rd[c0 + bi], rn[c0 + bi]) : EMPTY64;
-                const int dg = hb ? min(__ldg(P.deg + key_label(vk)), md) : 0;
+                // CSR row of the batch node: its first entry and its degree
+                int rbeg = 0, dg = 0;
+                if (hb) {
+                    const unsigned v = key_label(vk);
+                    rbeg = __ldg(P.row + v);
+                    dg = __ldg(P.row + v + 1) - rbeg;
+                }
                 int incl = dg;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -329,13 +334,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                     }
                     const pkey_t ok = __shfl_sync(0xffffffffu, vk, owner);
                     const int oex = __shfl_sync(0xffffffffu, excl, owner);
+                    const int obeg = __shfl_sync(0xffffffffu, rbeg, owner);
                     const bool act = e < total;
                     bool push = false;
                     unsigned slot = 0, u = 0;
                     float nd = 0.f;
                     if (act) {
-                        const unsigned v = key_label(ok);
-                        const pkey_t ed = __ldg(adj + (size_t)v * md + (e - oex));
+                        const pkey_t ed = __ldg(adj + obeg + (e - oex));
                         u = (unsigned)ed;
                         nd = __fadd_rn(key_dist(ok), __uint_as_float((unsigned)(ed >> 32)));
                         unsigned sl = node_slot(u, HS);
@@ -390,11 +395,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                         const int p = fn + __popc(bal & lt_mask);
                         fk[p] = make_key(nd, u);
                         fs[p] = slot;
-                        const pkey_t *row = adj + (size_t)u * md;
-                        prefetch_l1(row);
-                        if (md > 16) prefetch_l1(row + 16);
+                        prefetch_l1(P.row + u);
                         prefetch_l1(wmin + u);
-                        prefetch_l1(P.deg + u);
                     }
                     fn += np;
                     overflow = __any_sync(0xffffffffu, overflow);

@@ -5,8 +5,8 @@
 //   place the seeds that fall inside its region without scanning all N
 //   matches.  A match's source pixel is (floor(x+0.5), floor(y+0.5)); one
 //   outside the image is an invalid input and sets EPIC_ERR_INVALID.
-// * The match-graph edge table and the adjacency rows are reset so that the
-//   graph stage can insert with atomics.
+// * The match-graph edge table, the node degrees and lightest edges are
+//   reset so that the graph stage can insert with atomics.
 // * The run's grid-barrier and pass counters are reset.
 #include "epic_internal.cuh"
 
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
     }
     // seed binning: one CTA per pair at a time
     for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {
-        const PairDev P = a.pairs[p];
+        const PairDev &P = a.pairs[p];
         const int T = P.tiles_x * P.tiles_y;
         for (int t = threadIdx.x; t < T; t += blockDim.x) P.tile_start[t] = 0;
         for (int m = threadIdx.x; m < P.N; m += blockDim.x) {
@@ -108,20 +108,16 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
         }
         __syncthreads();
     }
-    // clearing: edge table slots and adjacency rows, CLEAR_CHUNK items each
+    // clearing: edge table slots, CLEAR_CHUNK items each (the CSR adjacency
+    // is written in full by the scatter and needs no clearing)
     for (int c = blockIdx.x; c < a.total_clear; c += gridDim.x) {
         int p = find_pair(a.clear_base, a.npairs, c);
-        const PairDev P = a.pairs[p];
+        const PairDev &P = a.pairs[p];
         long long i0 = (long long)(c - a.clear_base[p]) * CLEAR_CHUNK;
         long long n_hash = P.hash_cap;
-        long long n_adj = (long long)P.N * a.max_degree;
-        for (long long i = i0 + threadIdx.x; i < i0 + CLEAR_CHUNK; i += blockDim.x) {
-            if (i < n_hash) {
-                P.hkeys[i] = EMPTY64;
-                P.hw[i] = 0xFFFFFFFFu;
-            } else if (i - n_hash < n_adj) {
-                P.adj[i - n_hash] = EMPTY64;
-            }
+        for (long long i = i0 + threadIdx.x; i < i0 + CLEAR_CHUNK && i < n_hash; i += blockDim.x) {
+            P.hkeys[i] = EMPTY64;
+            P.hw[i] = 0xFFFFFFFFu;
         }
     }
 }
