@@ -99,13 +99,15 @@ def test_unsquared_weight_reading():
     _print("unsquared", rep)
 
 
-@pytest.mark.parametrize("config", [2, 3])
-def test_full_size_workloads_full_parity(config):
-    # every pixel and every match of the Sintel- and KITTI-shaped pairs,
-    # in the default launch configuration
-    p = synth.config_pair(config, 0)
+@pytest.mark.parametrize("config,index", [(2, 0), (3, 0), (4, 4), (5, 5)])
+def test_full_size_workloads_full_parity(config, index):
+    # every pixel and every match of the Sintel- and KITTI-shaped pairs and
+    # of the largest batch and serving sizes (1920x1080 with 20,000 matches
+    # and K = 128; 2048x1024 with 22,478 matches), in the default launch
+    # configuration
+    p = synth.config_pair(config, index)
     g, ref, rep = full_parity(p)
-    _print(f"config{config}", rep)
+    _print(f"config{config}.{index} {p.W}x{p.H} N={p.N} K={p.K}", rep)
     assert rep["flow_excluded_px"] < 0.02 * p.P
 
 
