@@ -481,7 +481,7 @@ def run_ours(args, rank, world, local_rank):
         refine = {"pair": f"{p0.W}x{p0.H}", "ms": times[30], "sor_ms": sor_ms,
                   "sor_algorithmic_bytes": sor_bytes,
                   "sor_achieved_gbs": sor_bytes / (sor_ms / 1e3) / 1e9 if sor_ms > 0 else None,
-                  "launches": 5 * (3 + 60), "aee_interpolated": aee0, "aee_refined": aee1}
+                  "launches": 5 * (3 + 10), "aee_interpolated": aee0, "aee_refined": aee1}
         reng.close()
         del I1t, I2t, ftmp
 

@@ -289,8 +289,9 @@ void epic_refine_params_default(epic_refine_params_t *p);
  * coordinates), linearises the data term there with the robust weights
  * taken at zero update, and solves for the update with red-black SOR in
  * which each pixel's 2x2 (du, dv) system is solved exactly; derivatives are
- * central differences on edge-replicated images.  Device pointers; the
- * handle holds H*W*(channels + 10)*4 bytes of scratch (grown on demand,
+ * central differences on edge-replicated images.  Device pointers (flow
+ * 8-byte aligned, else EPIC_ERR_INVALID); the
+ * handle holds about H*W*(channels + 12)*4 bytes of scratch (grown on demand,
  * EPIC_ERR_OOM if it cannot be).  Enqueued on `stream` without waiting; one
  * refinement in flight per handle (the scratch is shared).  params NULL =
  * defaults. */

@@ -1090,6 +1090,8 @@ int epic_refine(epic_interp_t *h, const float *I1, const float *I2, int H, int W
     if (params) prm = *params; else epic_refine_params_default(&prm);
     if (!I1 || !I2 || !flow || H < 1 || W < 1 || channels < 1 || channels > 4)
         return fail(h, EPIC_ERR_INVALID, "refine: bad arguments");
+    if (((uintptr_t)flow % 8) != 0)
+        return fail(h, EPIC_ERR_INVALID, "refine: flow must be 8-byte aligned");
     if (!(prm.alpha0 >= 0.f) || !(prm.gamma >= 0.f) || !(prm.kappa >= 0.f) || !(prm.eps > 0.f) ||
         !(prm.zeta > 0.f) || !(prm.omega > 0.f && prm.omega < 2.f) || prm.iterations < 0 ||
         prm.sor_iterations < 0)

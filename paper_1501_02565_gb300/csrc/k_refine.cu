@@ -9,9 +9,10 @@
 //   coeff_kernel   per pixel the 2x2 data matrix A, right-hand side b (with
 //                  the robust weights taken at zero update) and the
 //                  smoothness weight phi = alpha Psi'(|grad u|^2 + |grad v|^2);
-//   sor_kernel     one half-sweep (one colour) of point-coupled SOR: the
-//                  2x2 system of (du, dv) at a pixel is solved exactly from
-//                  the current neighbours and over-relaxed;
+//   sor_block_kernel  several half-sweeps (colours alternating) of
+//                  point-coupled SOR on overlapped tiles in shared memory:
+//                  the 2x2 system of (du, dv) at a pixel is solved exactly
+//                  from the current neighbours and over-relaxed;
 //   update_kernel  w += (du, dv).
 // Derivatives are central differences on the edge-replicated image, nested
 // the same way for second derivatives (the derivative image is itself
@@ -129,41 +130,107 @@ __global__ void coeff_kernel(Img I1, Img I2w, const float *__restrict__ flow, Re
     }
 }
 
-// One half-sweep: every pixel of `colour` ((x + y) & 1 == colour).  Thread t
-// of row y takes column 2 t + ((y + colour) & 1), so consecutive threads
-// take consecutive pixels of that colour.
-__global__ void sor_kernel(const float *__restrict__ flow, const float *__restrict__ coef, int H,
-                           int W, float omega, int colour, float *__restrict__ d) {
-    const int half = (W + 1) / 2;
-    const long long n = (long long)H * half;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(i / half);
-        const int x = 2 * (int)(i - (long long)y * half) + ((y + colour) & 1);
-        if (x >= W) continue;
+// The point-coupled SOR update of one pixel from the neighbour sums
+// S = sum s_pq, r1 = sum s_pq (u_q + du_q - u_p) (and r2 for v), each edge
+// weight s_pq = (phi_p + phi_q) / 2; cp = (A11, A12, A22, b1, b2).  Returns
+// false (no update) if the 2x2 system is not positive definite.
+__device__ __forceinline__ bool sor_point(float S, float r1, float r2, float a11, float a12,
+                                          float a22, float b1, float b2, float dup, float dvp,
+                                          float omega, float &du, float &dv) {
+    r1 -= b1;
+    r2 -= b2;
+    const float a = a11 + S, b = a12, dd = a22 + S;
+    const float det = a * dd - b * b;
+    if (!(det > 0.f)) return false;
+    const float nu = (dd * r1 - b * r2) / det, nv = (a * r2 - b * r1) / det;
+    du = (1.f - omega) * dup + omega * nu;
+    dv = (1.f - omega) * dvp + omega * nv;
+    return true;
+}
+
+// SOR_H half-sweeps per launch on overlapped tiles.  A CTA loads a region of
+// (SOR_TX + 2 SOR_H) x (SOR_TY + 2 SOR_H) pixels (flow, update, coefficients)
+// into shared memory and runs the half-sweeps there, red first.  Cells on
+// the region's outer ring are never updated; a wrong value spreads inward by
+// one pixel per half-sweep, so after SOR_H half-sweeps the core SOR_TX x
+// SOR_TY pixels hold exactly what the half-sweeps over the whole image would
+// give (each update is the same arithmetic on the same values).  The core is
+// written to a second update buffer (the neighbours' halos still read the
+// first), and the buffers swap between launches.
+constexpr int SOR_TX = 32, SOR_TY = 32, SOR_H = 6;
+constexpr int SOR_RW = SOR_TX + 2 * SOR_H, SOR_RH = SOR_TY + 2 * SOR_H, SOR_N = SOR_RW * SOR_RH;
+constexpr size_t SOR_SMEM = 10 * SOR_N * sizeof(float);
+
+__global__ void __launch_bounds__(256) sor_block_kernel(const float *__restrict__ flow,
+                                                        const float *__restrict__ coef, int H,
+                                                        int W, float omega, int nhalf,
+                                                        const float *__restrict__ din,
+                                                        float *__restrict__ dout) {
+    extern __shared__ float sb[];
+    float *su = sb, *sv = su + SOR_N, *sdu = sv + SOR_N, *sdv = sdu + SOR_N, *sph = sdv + SOR_N;
+    float *sc = sph + SOR_N;   // 5 x SOR_N: A11, A12, A22, b1, b2
+    const int rx0 = blockIdx.x * SOR_TX - SOR_H, ry0 = blockIdx.y * SOR_TY - SOR_H;
+    for (int i = threadIdx.x; i < SOR_N; i += blockDim.x) {
+        const int r = i / SOR_RW, c = i - r * SOR_RW;
+        const int x = rx0 + c, y = ry0 + r;
+        if (x < 0 || x >= W || y < 0 || y >= H) continue;
         const size_t p = (size_t)y * W + x;
-        const float *cp = coef + p * 8;
-        const float phip = cp[5];
-        const float up = flow[2 * p], vp = flow[2 * p + 1];
-        float S = 0.f, r1 = 0.f, r2 = 0.f;
-        auto nb = [&](size_t q) {
-            const float s = 0.5f * (phip + coef[q * 8 + 5]);
-            S += s;
-            r1 += s * (flow[2 * q] + d[2 * q] - up);
-            r2 += s * (flow[2 * q + 1] + d[2 * q + 1] - vp);
-        };
-        if (x + 1 < W) nb(p + 1);
-        if (x > 0) nb(p - 1);
-        if (y + 1 < H) nb(p + W);
-        if (y > 0) nb(p - W);
-        r1 -= cp[3];
-        r2 -= cp[4];
-        const float a = cp[0] + S, b = cp[1], dd = cp[2] + S;
-        const float det = a * dd - b * b;
-        if (!(det > 0.f)) continue;
-        const float nu = (dd * r1 - b * r2) / det, nv = (a * r2 - b * r1) / det;
-        d[2 * p] = (1.f - omega) * d[2 * p] + omega * nu;
-        d[2 * p + 1] = (1.f - omega) * d[2 * p + 1] + omega * nv;
+        const float2 f = reinterpret_cast<const float2 *>(flow)[p];
+        const float2 dd = reinterpret_cast<const float2 *>(din)[p];
+        const float4 c0 = reinterpret_cast<const float4 *>(coef)[2 * p];
+        const float4 c1 = reinterpret_cast<const float4 *>(coef)[2 * p + 1];
+        su[i] = f.x;
+        sv[i] = f.y;
+        sdu[i] = dd.x;
+        sdv[i] = dd.y;
+        sph[i] = c1.y;
+        sc[i] = c0.x;
+        sc[SOR_N + i] = c0.y;
+        sc[2 * SOR_N + i] = c0.z;
+        sc[3 * SOR_N + i] = c0.w;
+        sc[4 * SOR_N + i] = c1.x;
+    }
+    __syncthreads();
+    static_assert(SOR_RW % 2 == 0, "a region row holds SOR_RW / 2 cells of each colour");
+    constexpr int HALF_RW = SOR_RW / 2;
+    for (int h = 0; h < nhalf; ++h) {
+        const int colour = h & 1;
+        // enumerate only this colour's cells: in row r they are the columns
+        // c with (rx0 + c + ry0 + r) even (red) or odd (black)
+        for (int k = threadIdx.x; k < SOR_RH * HALF_RW; k += blockDim.x) {
+            const int r = k / HALF_RW;
+            const int c = 2 * (k - r * HALF_RW) + ((colour + rx0 + ry0 + r) & 1);
+            if (r == 0 || c == 0 || r == SOR_RH - 1 || c == SOR_RW - 1) continue;
+            const int x = rx0 + c, y = ry0 + r;
+            if (x < 0 || x >= W || y < 0 || y >= H) continue;
+            const int i = r * SOR_RW + c;
+            const float php = sph[i], up = su[i], vp = sv[i];
+            float S = 0.f, r1 = 0.f, r2 = 0.f;
+            auto nb = [&](int q) {   // right, left, down, up
+                const float sw = 0.5f * (php + sph[q]);
+                S += sw;
+                r1 += sw * ((su[q] + sdu[q]) - up);
+                r2 += sw * ((sv[q] + sdv[q]) - vp);
+            };
+            if (x + 1 < W) nb(i + 1);
+            if (x > 0) nb(i - 1);
+            if (y + 1 < H) nb(i + SOR_RW);
+            if (y > 0) nb(i - SOR_RW);
+            float du, dv;
+            if (sor_point(S, r1, r2, sc[i], sc[SOR_N + i], sc[2 * SOR_N + i], sc[3 * SOR_N + i],
+                          sc[4 * SOR_N + i], sdu[i], sdv[i], omega, du, dv)) {
+                sdu[i] = du;
+                sdv[i] = dv;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < SOR_TX * SOR_TY; i += blockDim.x) {
+        const int r = SOR_H + i / SOR_TX, c = SOR_H + i % SOR_TX;
+        const int x = rx0 + c, y = ry0 + r;
+        if (x >= W || y >= H) continue;
+        const int j = r * SOR_RW + c;
+        reinterpret_cast<float2 *>(dout)[(size_t)y * W + x] = make_float2(sdu[j], sdv[j]);
     }
 }
 
@@ -184,31 +251,49 @@ unsigned grid_for(long long n, int num_sms) {
 
 }  // namespace
 
+// Scratch layout: warped image [P][C], coefficients [P][8], two update
+// buffers [P][2]; every region starts on a 256-byte boundary (the blocked
+// SOR reads coefficients as float4 and updates as float2).
+static size_t rf_align(size_t b) { return (b + 255) / 256 * 256; }
+
 size_t refine_scratch_bytes(int H, int W, int C) {
     const size_t P = (size_t)H * W;
-    return P * C * sizeof(float) + P * 8 * sizeof(float) + P * 2 * sizeof(float);
+    return rf_align(P * C * sizeof(float)) + rf_align(P * 8 * sizeof(float)) +
+           2 * rf_align(P * 2 * sizeof(float));
 }
 
 cudaError_t launch_refine(const float *I1, const float *I2, int H, int W, int C, float *flow,
                           const RefineArgs &r, void *scratch, int num_sms, cudaStream_t stream) {
     const long long P = (long long)H * W;
-    float *I2w = static_cast<float *>(scratch);
-    float *coef = I2w + P * C;
-    float *d = coef + P * 8;
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(float) * 2 * P, stream);
+    char *base = static_cast<char *>(scratch);
+    float *I2w = reinterpret_cast<float *>(base);
+    base += rf_align((size_t)P * C * sizeof(float));
+    float *coef = reinterpret_cast<float *>(base);
+    base += rf_align((size_t)P * 8 * sizeof(float));
+    float *dbuf[2] = {reinterpret_cast<float *>(base),
+                      reinterpret_cast<float *>(base + rf_align((size_t)P * 2 * sizeof(float)))};
+    cudaError_t e = cudaMemsetAsync(dbuf[0], 0, sizeof(float) * 2 * P, stream);
     if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(sor_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SOR_SMEM)) != cudaSuccess)
+        return e;
     const unsigned gP = grid_for(P, num_sms);
-    const unsigned gH = grid_for((long long)H * ((W + 1) / 2), num_sms);
     const unsigned g2 = grid_for(2 * P, num_sms);
+    const dim3 gS((W + SOR_TX - 1) / SOR_TX, (H + SOR_TY - 1) / SOR_TY);
     Img i1{I1, H, W, C}, i2w{I2w, H, W, C};
+    int cur = 0;   // the update buffer holding zeros / the latest update
     for (int it = 0; it < r.iterations; ++it) {
         warp_kernel<<<gP, 256, 0, stream>>>(I2, flow, H, W, C, I2w);
         coeff_kernel<<<gP, 256, 0, stream>>>(i1, i2w, flow, r, coef);
-        for (int s = 0; s < r.sor_iterations; ++s) {
-            sor_kernel<<<gH, 256, 0, stream>>>(flow, coef, H, W, r.omega, 0, d);
-            sor_kernel<<<gH, 256, 0, stream>>>(flow, coef, H, W, r.omega, 1, d);
+        // 2 * sor_iterations half-sweeps, SOR_H per launch (red first each
+        // time, as SOR_H is even)
+        for (int done = 0; done < 2 * r.sor_iterations; done += SOR_H) {
+            const int nh = 2 * r.sor_iterations - done < SOR_H ? 2 * r.sor_iterations - done : SOR_H;
+            sor_block_kernel<<<gS, 256, SOR_SMEM, stream>>>(flow, coef, H, W, r.omega, nh,
+                                                            dbuf[cur], dbuf[cur ^ 1]);
+            cur ^= 1;
         }
-        update_kernel<<<g2, 256, 0, stream>>>(flow, d, 2 * P);
+        update_kernel<<<g2, 256, 0, stream>>>(flow, dbuf[cur], 2 * P);   // adds, then zeroes
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

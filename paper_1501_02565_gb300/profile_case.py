@@ -7,7 +7,7 @@ run (12 with --prune).
 --what gradcost: the image-gradient cost map of `--batch` synthetic frames,
 one launch per run.
 --what refine: the variational refinement of the first pair's interpolated
-flow (one interpolation run first), 5 x (3 + 60) launches per run.
+flow (one interpolation run first), 5 x (3 + 10) launches per run.
 
 Nothing else launches kernels of the library, so a profiler can skip the
 warm-up launches by count and capture the runs that follow.
@@ -88,7 +88,7 @@ def _other(args):
         eng.refine(I1, I2, f)
     torch.cuda.synchronize()
     eng.close()
-    print("1 pair, 6 interpolation launches, then 5 x (3 + 60) refinement launches per run")
+    print("1 pair, 7 interpolation launches, then 5 x (3 + 10) refinement launches per run")
     return 0
 
 
