@@ -84,3 +84,23 @@ def test_bad_request_is_refused_at_submission():
     with pytest.raises(ValueError):
         srv.submit(Request(C, np.array([[1, 1, 0, 0]], np.float32), 4, 1.0))
     srv.stop()
+
+
+def test_host_buffer_batch_matches_device_batch():
+    # the host-buffer entry point (copies in, one batched run, copies out)
+    # gives the same flows as the device-buffer batch
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    pairs = [synth.config_pair(1, i) for i in range(9)] + [synth.config_pair(2, 0)]
+    eng = EpicInterp(0, max_pairs=len(pairs))
+    dev = [(torch.from_numpy(p.C).cuda(), torch.from_numpy(p.matches).cuda(), p.K, p.a,
+            torch.empty((p.H, p.W, 2), dtype=torch.float32, device="cuda")) for p in pairs]
+    eng.run_batch(dev)
+    eng.sync()
+    host = [(torch.from_numpy(p.C).pin_memory(), torch.from_numpy(p.matches).pin_memory(), p.K,
+             p.a, torch.empty((p.H, p.W, 2), dtype=torch.float32).pin_memory()) for p in pairs]
+    for _ in range(2):
+        eng.run_batch_host(host)
+        for d, hh in zip(dev, host):
+            assert torch.equal(d[4].cpu(), hh[4])
+    eng.close()
