@@ -152,63 +152,55 @@ __device__ int local_solve(pkey_t *K, const unsigned *h, const Region &g,
     const int segH = (ncols + nsegH - 1) / nsegH;
     const int itemsH = nrows * nsegH, roundsH = (itemsH + T - 1) / T;
 
-    const int cap = g.RW * g.RH;  // Bellman-Ford bound on useful iterations
-    int any = 0;
-    for (int it = 0; it < cap; ++it) {
+    // Sweeps run in the cyclic order down, up, right, left.  The region is
+    // at its fixed point once four consecutive sweeps (one per direction,
+    // hence every pixel against all eight neighbours) changed nothing, which
+    // can happen in the middle of a cycle.
+    const int cap = 4 * g.RW * g.RH;  // Bellman-Ford bound on useful sweeps
+    int any = 0, quiet = 0;
+    for (int sw = 0; sw < cap; ++sw) {
+        const int dir = sw & 3;
         int ch = 0;
-        for (int rv = 0; rv < roundsV; ++rv) {   // down: from the row above
-            const int w = tid + rv * T;
-            const bool vu = w < itemsV;
-            const int vx = g.bx0 + w % ncols;
-            const int vy0 = g.by0 + (w / ncols) * segV;
-            const int vy1 = min(g.by1, vy0 + segV - 1);
-            for (int s = 0; s < segV; ++s) {
-                int y = vy0 + s;
-                if (vu && y <= vy1) ch |= relax3(K, h, y * P + vx, -P, -P - 1, -P + 1);
-                __syncwarp();
+        if (dir < 2) {
+            // down (dir 0): from the row above; up (dir 1): from the row below
+            const int off = dir == 0 ? -P : P;
+            for (int rv = 0; rv < roundsV; ++rv) {
+                const int w = tid + rv * T;
+                const bool vu = w < itemsV;
+                const int vx = g.bx0 + w % ncols;
+                const int vy0 = g.by0 + (w / ncols) * segV;
+                const int vy1 = min(g.by1, vy0 + segV - 1);
+                for (int s = 0; s < segV; ++s) {
+                    const int y = dir == 0 ? vy0 + s : vy1 - s;
+                    if (vu && y >= vy0 && y <= vy1)
+                        ch |= relax3(K, h, y * P + vx, off, off - 1, off + 1);
+                    __syncwarp();
+                }
+            }
+        } else {
+            // right (dir 2): from the column on the left; left (dir 3): from
+            // the column on the right
+            const int off = dir == 2 ? -1 : 1;
+            for (int rh = 0; rh < roundsH; ++rh) {
+                const int w = tid + rh * T;
+                const bool hu = w < itemsH;
+                const int hy = g.by0 + w % nrows;
+                const int hx0 = g.bx0 + (w / nrows) * segH;
+                const int hx1 = min(g.bx1, hx0 + segH - 1);
+                for (int s = 0; s < segH; ++s) {
+                    const int x = dir == 2 ? hx0 + s : hx1 - s;
+                    if (hu && x >= hx0 && x <= hx1)
+                        ch |= relax3(K, h, hy * P + x, off, off - P, off + P);
+                    __syncwarp();
+                }
             }
         }
-        __syncthreads();
-        for (int rv = 0; rv < roundsV; ++rv) {   // up: from the row below
-            const int w = tid + rv * T;
-            const bool vu = w < itemsV;
-            const int vx = g.bx0 + w % ncols;
-            const int vy0 = g.by0 + (w / ncols) * segV;
-            const int vy1 = min(g.by1, vy0 + segV - 1);
-            for (int s = 0; s < segV; ++s) {
-                int y = vy1 - s;
-                if (vu && y >= vy0) ch |= relax3(K, h, y * P + vx, P, P - 1, P + 1);
-                __syncwarp();
-            }
+        if (__syncthreads_or(ch)) {
+            any = 1;
+            quiet = 0;
+        } else if (++quiet == 4) {
+            return any;
         }
-        __syncthreads();
-        for (int rh = 0; rh < roundsH; ++rh) {   // right: from the column on the left
-            const int w = tid + rh * T;
-            const bool hu = w < itemsH;
-            const int hy = g.by0 + w % nrows;
-            const int hx0 = g.bx0 + (w / nrows) * segH;
-            const int hx1 = min(g.bx1, hx0 + segH - 1);
-            for (int s = 0; s < segH; ++s) {
-                int x = hx0 + s;
-                if (hu && x <= hx1) ch |= relax3(K, h, hy * P + x, -1, -1 - P, -1 + P);
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int rh = 0; rh < roundsH; ++rh) {   // left: from the column on the right
-            const int w = tid + rh * T;
-            const bool hu = w < itemsH;
-            const int hy = g.by0 + w % nrows;
-            const int hx0 = g.bx0 + (w / nrows) * segH;
-            const int hx1 = min(g.bx1, hx0 + segH - 1);
-            for (int s = 0; s < segH; ++s) {
-                int x = hx1 - s;
-                if (hu && x >= hx0) ch |= relax3(K, h, hy * P + x, 1, 1 - P, 1 + P);
-                __syncwarp();
-            }
-        }
-        if (!__syncthreads_or(ch)) return any;
-        any = 1;
     }
     if (tid == 0) set_status(st, EPIC_ERR_NOT_CONVERGED);
     return any;
