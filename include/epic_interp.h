@@ -299,6 +299,17 @@ int epic_refine(epic_interp_t *h, const float *I1, const float *I2, int H,
                 int W, int channels, float *flow,
                 const epic_refine_params_t *params, void *stream);
 
+/* Self-test of failure detection without a GPU fault.  Every device wait
+ * of the library is bounded: the relaxation's grid barrier (2 s) and the TMA
+ * staging's mbarrier wait (1 s) give up, record EPIC_ERR_TIMEOUT and let the
+ * kernel return.  This runs one of those waits with a limit of limit_ms
+ * (1..10000) where the awaited event never happens: which = 0, a grid
+ * barrier that expects a second CTA which does not exist; which = 1, an
+ * mbarrier whose transaction is never issued.  Returns the status the wait
+ * recorded (EPIC_ERR_TIMEOUT when the bound works) and leaves the handle and
+ * the context usable.  Waits for completion. */
+int epic_selftest_wait_timeout(epic_interp_t *h, int which, int limit_ms);
+
 /* Number of kernel launches one run of `n` pairs enqueues. */
 int epic_interp_launches_per_run(epic_interp_t *h, int n);
 

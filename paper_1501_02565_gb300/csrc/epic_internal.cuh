@@ -225,6 +225,10 @@ size_t exact_smem_bytes(int K);
 cudaError_t launch_keys_to_dist(const pkey_t *keys, long long n, float *D, cudaStream_t stream);
 cudaError_t launch_exact_fit(const ExactArgs &x, cudaStream_t stream);
 
+// Self-test of the bounded device waits (grid barrier, TMA mbarrier).
+cudaError_t launch_wait_selftest(RunState *st, int which, unsigned long long limit_ns,
+                                 cudaStream_t stream);
+
 // Variational refinement.
 struct RefineArgs {
     float alpha0, gamma, kappa, eps, zeta, omega;

@@ -1071,6 +1071,20 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
     return epic_interp_sync(h);
 }
 
+int epic_selftest_wait_timeout(epic_interp_t *h, int which, int limit_ms) {
+    if (!h || (which != 0 && which != 1) || limit_ms < 1 || limit_ms > 10000)
+        return EPIC_ERR_INVALID;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    cudaStream_t s = h->last_stream;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "sync");
+    if ((e = cudaMemsetAsync(h->state, 0, sizeof(RunState), s)) != cudaSuccess ||
+        (e = epic::launch_wait_selftest(h->state, which, (unsigned long long)limit_ms * 1000000ull,
+                                        s)) != cudaSuccess)
+        return cuda_fail(h, e, "wait self-test");
+    return epic_interp_sync(h);   // the recorded status (then cleared)
+}
+
 void epic_refine_params_default(epic_refine_params_t *p) {
     if (!p) return;
     p->alpha0 = 1.f;

@@ -51,7 +51,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Sense-free generation barrier over all CTAs of a cooperative launch.  The
 // wait gives up after BARRIER_LIMIT_NS (or as soon as another CTA has given
 // up) and reports EPIC_ERR_TIMEOUT instead of spinning forever.
-__device__ bool grid_sync(RunState *st, unsigned nblocks) {
+__device__ bool grid_sync(RunState *st, unsigned nblocks,
+                          unsigned long long limit_ns = BARRIER_LIMIT_NS) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -68,7 +69,7 @@ __device__ bool grid_sync(RunState *st, unsigned nblocks) {
             unsigned long long t0 = global_ns();
             while (ld_acquire(&b->gen) == g) {
                 if (get_status(st) == EPIC_ERR_TIMEOUT) { ok = 0; break; }
-                if (global_ns() - t0 > BARRIER_LIMIT_NS) {
+                if (global_ns() - t0 > limit_ns) {
                     set_status(st, EPIC_ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -242,7 +243,8 @@ __device__ __forceinline__ void tma_load_2d(const Tma &t, const CUtensorMap *map
 // All threads wait for the copy, at most TMA_LIMIT_NS; on time-out the run
 // reports EPIC_ERR_TIMEOUT.
 constexpr unsigned long long TMA_LIMIT_NS = 1000000000ull;
-__device__ __forceinline__ void tma_wait(Tma &t, RunState *st) {
+__device__ __forceinline__ void tma_wait(Tma &t, RunState *st,
+                                         unsigned long long limit_ns = TMA_LIMIT_NS) {
     const unsigned long long t0 = global_ns();
     for (;;) {
         unsigned done;
@@ -253,7 +255,7 @@ __device__ __forceinline__ void tma_wait(Tma &t, RunState *st) {
             : "r"(t.mbar), "r"(t.phase)
             : "memory");
         if (done) break;
-        if (global_ns() - t0 > TMA_LIMIT_NS) {
+        if (global_ns() - t0 > limit_ns) {
             set_status(st, EPIC_ERR_TIMEOUT);
             break;
         }
@@ -512,7 +514,29 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
     }
 }
 
+// Self-test of the bounded waits (failure detection without a GPU fault):
+// one CTA waits for a second CTA that does not exist at the grid barrier
+// (which = 0), or for a TMA transaction that is never issued on an
+// mbarrier (which = 1).  Either wait must give up after limit_ns and record
+// EPIC_ERR_TIMEOUT, leaving the context usable.
+__global__ void wait_selftest_kernel(RunState *st, int which, unsigned long long limit_ns) {
+    if (which == 0) {
+        grid_sync(st, 2u, limit_ns);
+    } else {
+        __shared__ __align__(8) unsigned long long bar;
+        Tma t;
+        tma_init(t, &bar);
+        tma_wait(t, st, limit_ns);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(RunState *st, int which, unsigned long long limit_ns,
+                                 cudaStream_t stream) {
+    wait_selftest_kernel<<<1, 32, 0, stream>>>(st, which, limit_ns);
+    return cudaGetLastError();
+}
 
 size_t dt_smem_bytes(int tile_w, int tile_h, int apron) {
     int RW = tile_w + 2 * apron + 2, RH = tile_h + 2 * apron + 2;

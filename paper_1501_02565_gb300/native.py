@@ -40,7 +40,7 @@ EXPORTED = (
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
     "epic_geodesic_labels_noalloc", "epic_exact_interp", "epic_gradient_cost",
-    "epic_refine_params_default", "epic_refine",
+    "epic_refine_params_default", "epic_refine", "epic_selftest_wait_timeout",
 )
 
 
@@ -153,6 +153,8 @@ def load(path: str | None = None):
     lib.epic_refine_params_default.restype = None
     lib.epic_refine.argtypes = [P, P, P, I, I, I, P, ctypes.POINTER(epic_refine_params_t), P]
     lib.epic_refine.restype = I
+    lib.epic_selftest_wait_timeout.argtypes = [P, I, I]
+    lib.epic_selftest_wait_timeout.restype = I
     lib.epic_gradient_cost.argtypes = [P, I, I, I, I, F, P, P]
     lib.epic_gradient_cost.restype = I
     lib.epic_exact_interp.argtypes = [P, P, P, I, I, I, I, F, I, P, P, P, P]
@@ -365,6 +367,11 @@ class EpicInterp:
                                   ctypes.byref(prm), _stream_handle(stream))
         self._check(rc, "epic_refine")
         return flow
+
+    def selftest_wait_timeout(self, which, limit_ms=50):
+        """Status recorded by a bounded device wait that never completes
+        (0: grid barrier, 1: TMA mbarrier); EPIC_ERR_TIMEOUT expected."""
+        return self.lib.epic_selftest_wait_timeout(self.h, int(which), int(limit_ms))
 
     def get_pruning(self, pair, N):
         """Consistency pruning of the last run's pair (prune = 1): keep
