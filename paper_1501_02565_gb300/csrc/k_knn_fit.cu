@@ -25,7 +25,9 @@
 // kept, and the finished list is sorted once more (all keys) before the fit.  All edges of all batch nodes are relaxed in one
 // pass: lanes take (node, edge) pairs found from a warp prefix sum of the
 // batch nodes' degrees (CSR row lengths).  A newly pushed node's row offsets
-// and lightest edge are prefetched into L1 for when it is settled.
+// are prefetched into L1 for when it is settled; its lightest edge is read
+// at once, since the step's bound is kept as a running minimum over the
+// entries pushed and kept (no separate pass over the frontier).
 //
 // The fit uses centred coordinates x~ = p_n - p_m and fits the flow
 // u = p' - p (the same least-squares problem as fitting p', Eq. 2, with
@@ -106,7 +108,7 @@ __device__ __forceinline__ F2 warp_sum(F2 v) {
 __device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.lo; }
 
 __host__ __device__ __forceinline__ size_t knn_warp_bytes(int hs, int fs, int km) {
-    return (size_t)fs * 12 + (size_t)hs * 8 + (size_t)km * 8;
+    return (size_t)fs * 16 + (size_t)hs * 8 + (size_t)km * 8;
 }
 
 __device__ __forceinline__ void prefetch_l1(const void *p) {
@@ -155,7 +157,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
     unsigned char *base = smem + per_warp * wid;
     pkey_t *fk = reinterpret_cast<pkey_t *>(base);
     unsigned *fs = reinterpret_cast<unsigned *>(fk + FS);
-    unsigned *hk = fs + FS;
+    float *fw = reinterpret_cast<float *>(fs + FS);   // t + lightest edge of each entry
+    unsigned *hk = reinterpret_cast<unsigned *>(fw + FS);
     unsigned *hv = hk + HS;
     unsigned *rn = hv + HS;
     float *rd = reinterpret_cast<float *>(rn + KM);
@@ -180,29 +183,28 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
             hv[i] = 0x7F800000u;  // +inf
         }
         __syncwarp();
+        // each lane's running minimum of the keys and of t + w_min over the
+        // frontier entries it kept or pushed since the last step: the step's
+        // smallest key and bound B are their warp minima.  Stale entries
+        // (a node pushed again with a smaller key) only add larger values
+        // than the node's current entry, so the minima are exact.
+        pkey_t rk = EMPTY64;
+        float rb = __int_as_float(0x7f800000);
         if (lane == 0) {
             const unsigned s0 = node_slot((unsigned)m, HS);
             hk[s0] = (unsigned)m;
             hv[s0] = 0u;
-            fk[0] = make_key(0.f, (unsigned)m);
+            fk[0] = rk = make_key(0.f, (unsigned)m);
             fs[0] = s0;
+            fw[0] = rb = __fadd_rn(0.f, __uint_as_float(__ldg(wmin + m)));
         }
         __syncwarp();
         int fn = 1, cnt = 0;
         bool overflow = false;
         while (cnt < K) {
             // (1) smallest current key and the batch bound B
-            pkey_t kmin = EMPTY64;
-            float bound = __int_as_float(0x7f800000);
-            for (int i = lane; i < fn; i += 32) {
-                const pkey_t k = fk[i];
-                const unsigned cur = hv[fs[i]];
-                if (!(cur & SETTLED) && cur == (unsigned)(k >> 32)) {
-                    kmin = k < kmin ? k : kmin;
-                    const float wm = __uint_as_float(__ldg(wmin + key_label(k)));
-                    bound = fminf(bound, __fadd_rn(key_dist(k), wm));
-                }
-            }
+            pkey_t kmin = rk;
+            float bound = rb;
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
                 const pkey_t ok = __shfl_xor_sync(0xffffffffu, kmin, o);
@@ -210,6 +212,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                 bound = fminf(bound, __shfl_xor_sync(0xffffffffu, bound, o));
             }
             if (kmin == EMPTY64) break;  // component exhausted
+            rk = EMPTY64;
+            rb = __int_as_float(0x7f800000);
             // (2) the batch: current entries below the bound (and the
             //     smallest).  A batch that reaches K is finished by sorting it
             //     in lanes; one reaching K with more than a warp of entries is
@@ -237,10 +241,12 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                 const int i = b0 + lane;
                 pkey_t k = EMPTY64;
                 unsigned sl = 0;
+                float tw = 0.f;
                 bool valid = false;
                 if (i < fn) {
                     k = fk[i];
                     sl = fs[i];
+                    tw = fw[i];
                     const unsigned cur = hv[sl];
                     valid = !(cur & SETTLED) && cur == (unsigned)(k >> 32);
                 }
@@ -254,6 +260,9 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                     const int p = wpos + __popc(kb & lt_mask);
                     fk[p] = k;
                     fs[p] = sl;
+                    fw[p] = tw;
+                    rk = k < rk ? k : rk;
+                    rb = fminf(rb, tw);
                 }
                 if (final_batch) {
                     unsigned rem = bb;
@@ -372,10 +381,12 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                             const int i = q0 + lane;
                             pkey_t k = 0;
                             unsigned sl2 = 0;
+                            float tw2 = 0.f;
                             bool keep = false;
                             if (i < fn) {
                                 k = fk[i];
                                 sl2 = fs[i];
+                                tw2 = fw[i];
                                 const unsigned cur = hv[sl2];
                                 keep = !(cur & SETTLED) && cur == (unsigned)(k >> 32);
                             }
@@ -384,6 +395,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                             if (keep) {
                                 fk[w2 + __popc(kb & lt_mask)] = k;
                                 fs[w2 + __popc(kb & lt_mask)] = sl2;
+                                fw[w2 + __popc(kb & lt_mask)] = tw2;
                             }
                             w2 += __popc(kb);
                             __syncwarp();
@@ -393,10 +405,14 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                     }
                     if (push && !overflow) {
                         const int p = fn + __popc(bal & lt_mask);
-                        fk[p] = make_key(nd, u);
+                        const pkey_t nk = make_key(nd, u);
+                        const float tw = __fadd_rn(nd, __uint_as_float(__ldg(wmin + u)));
+                        fk[p] = nk;
                         fs[p] = slot;
+                        fw[p] = tw;
+                        rk = nk < rk ? nk : rk;
+                        rb = fminf(rb, tw);
                         prefetch_l1(P.row + u);
-                        prefetch_l1(wmin + u);
                     }
                     fn += np;
                     overflow = __any_sync(0xffffffffu, overflow);
