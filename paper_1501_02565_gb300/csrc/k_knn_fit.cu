@@ -218,8 +218,10 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
             //     smallest).  A batch that reaches K is finished by sorting it
             //     in lanes; one reaching K with more than a warp of entries is
             //     cut to the smallest key alone.
+            // (fn counts every frontier entry, an upper bound on the batch:
+            // while cnt + fn < K the batch cannot reach K and is not counted)
             int nwin = 0;
-            for (int b0 = 0; b0 < fn; b0 += 32) {
+            for (int b0 = 0; cnt + fn >= K && b0 < fn; b0 += 32) {
                 const int i = b0 + lane;
                 bool inb = false;
                 if (i < fn) {
