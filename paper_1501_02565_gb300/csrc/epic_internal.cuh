@@ -100,7 +100,8 @@ struct PairDev {
     int *deg;               // [N] node degree in G, then the CSR fill cursor
     unsigned *wmin;         // [N] float bits of the lightest edge at each node
     int *row;               // [N + 1] CSR row offsets into adj
-    pkey_t *adj;             // [2 * hash_cap] CSR rows (w bits << 32 | neighbour)
+    uint4 *adj;              // [2 * hash_cap] CSR rows: (neighbour, w bits, the
+                             // neighbour's lightest-edge bits, 0)
     float4 *models;         // [N * 2] (c_u, c_v, b11, b12), (b21, b22, x_m, y_m)
     int *fallback;          // [N]
     int *knn_idx;           // [N*K] or null
@@ -137,6 +138,7 @@ struct RunState {
     unsigned changed[3];   // per-pass dirty-tile counters (rotating)
     unsigned work[4];      // relaxation tile dispensers: passes (rotating), phase 1
     unsigned knn_next;     // K-NN match dispenser
+    unsigned edge_next;    // boundary-edge tile dispenser
     unsigned compact_done; // CTAs finished in the pruning compaction
     GridBarrier barrier;
 };

@@ -155,7 +155,7 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep, boo
     L.wmin = take((size_t)P.N * sizeof(unsigned));
     L.row = take(((size_t)P.N + 1) * sizeof(int));
     // CSR adjacency: at most one entry per direction of every table slot
-    L.adj = take((size_t)P.hash_cap * 2 * sizeof(pkey_t));
+    L.adj = take((size_t)P.hash_cap * 2 * sizeof(uint4));
     (void)max_degree;
     L.models = take((size_t)P.N * 2 * sizeof(float4));
     L.fallback = take((size_t)P.N * sizeof(int));
@@ -477,7 +477,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         P[i].deg = reinterpret_cast<int *>(b + L[i].deg);
         P[i].wmin = reinterpret_cast<unsigned *>(b + L[i].wmin);
         P[i].row = reinterpret_cast<int *>(b + L[i].row);
-        P[i].adj = reinterpret_cast<pkey_t *>(b + L[i].adj);
+        P[i].adj = reinterpret_cast<uint4 *>(b + L[i].adj);
         P[i].models = reinterpret_cast<float4 *>(b + L[i].models);
         P[i].fallback = reinterpret_cast<int *>(b + L[i].fallback);
         if (c.keep_intermediates) {

@@ -13,10 +13,11 @@
 //                down-left, down, down-right: each unordered pixel pair once)
 //                and forms (min label, max label, weight).  Candidates are
 //                merged per tile (64 x 32 pixels hold only tens of distinct
-//                label pairs): first across the lanes of a warp, then in a
+//                label pairs): first over the pixel's four directions, then
+//                across the lanes of a warp (match.any groups), then in a
 //                shared-memory table with atomicMin on the weight; the tile's
 //                unique entries are then inserted into the pair's global
-//                open-addressing table.  A match whose source pixel is owned
+//                open-addressing table.  Tiles are taken from a counter.  A match whose source pixel is owned
 //                by a smaller index (a duplicate) is joined to the owner at
 //                distance D = 0.
 //                The insertion that creates an edge counts it in both
@@ -24,9 +25,11 @@
 //                lightest-edge weight.
 // offsets_kernel one CTA per pair: exclusive scan of the degrees into the
 //                CSR row offsets; the degree array becomes the fill cursor.
-// scatter_kernel every occupied slot appends (w, n) to row m and (w, m) to
-//                row n of the CSR adjacency (order within a row unspecified;
-//                the K-NN search does not depend on it).
+// scatter_kernel every occupied slot appends (n, w, w_min(n)) to row m and
+//                (m, w, w_min(m)) to row n of the CSR adjacency (order within
+//                a row unspecified; the K-NN search does not depend on it).
+//                Carrying the neighbour's lightest edge in the entry saves
+//                the search a dependent load per pushed node.
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -62,39 +65,37 @@ __device__ __forceinline__ void table_insert(const PairDev &P, pkey_t k,
 
 constexpr int TILE_TABLE = 1024;  // shared-memory slots per CTA (power of two)
 
-// Insert into the CTA's shared table; false if the probe sequence is full.
-__device__ __forceinline__ bool smem_insert(pkey_t *sk, unsigned *sw, pkey_t k,
-                                            unsigned wbits) {
+// Claim the shared-table slot of key k (or find it); -1 if the probe
+// sequence is full.
+__device__ __forceinline__ int smem_claim(pkey_t *sk, pkey_t k) {
     unsigned s = hash_slot(k, TILE_TABLE);
     for (int probe = 0; probe < 64; ++probe) {
         const pkey_t prev = atomicCAS(sk + s, EMPTY64, k);
-        if (prev == EMPTY64 || prev == k) {
-            atomicMin(sw + s, wbits);
-            return true;
-        }
+        if (prev == EMPTY64 || prev == k) return (int)s;
         s = (s + 1) & (TILE_TABLE - 1);
     }
-    return false;
+    return -1;
 }
 
-// Insert one candidate per active lane, merging equal label pairs in the
-// warp first; the leader of each group inserts into the shared table (or,
-// if that is full, straight into the global table).
+// Insert one candidate per active lane.  Lanes holding the same label pair
+// are grouped with one match.any; the group's lowest lane claims the slot in
+// the shared table and every member lowers the slot's weight (or, if the
+// table is full, inserts straight into the global table).
 __device__ __forceinline__ void warp_insert(const PairDev &P, bool have, pkey_t k,
                                             unsigned wbits, pkey_t *sk, unsigned *sw,
                                             RunState *st) {
+    if (!__any_sync(0xffffffffu, have)) return;
     const unsigned lane = threadIdx.x & 31;
-    unsigned pend = __ballot_sync(0xffffffffu, have);
-    while (pend) {
-        const int leader = __ffs(pend) - 1;
-        const pkey_t lk = __shfl_sync(0xffffffffu, k, leader);
-        const bool mine = have && k == lk;
-        const unsigned grp = __ballot_sync(0xffffffffu, mine);
-        const unsigned wmin = __reduce_min_sync(0xffffffffu, mine ? wbits : 0xFFFFFFFFu);
-        if (lane == (unsigned)leader && !smem_insert(sk, sw, lk, wmin))
-            table_insert(P, lk, wmin, st);
-        pend &= ~grp;
-        if (mine) have = false;
+    const unsigned grp = __match_any_sync(0xffffffffu, have ? k : EMPTY64);
+    const int leader = __ffs(grp) - 1;
+    int slot = -1;
+    if (have && lane == (unsigned)leader) slot = smem_claim(sk, k);
+    slot = __shfl_sync(0xffffffffu, slot, leader);
+    if (have) {
+        if (slot >= 0)
+            atomicMin(sw + slot, wbits);
+        else
+            table_insert(P, k, wbits, st);
     }
 }
 
@@ -102,14 +103,22 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
     const BatchArgs a = *ap;
     RunState *st = a.state;
     if (get_status(st) != 0) return;
-    __shared__ int s_pair, s_local;
+    __shared__ int s_tile, s_pair, s_local;
     __shared__ pkey_t sk[TILE_TABLE];
     __shared__ unsigned sw[TILE_TABLE];
-    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+    // tiles are handed out from a counter: their cost varies with the number
+    // of cell boundaries they hold
+    for (;;) {
         if (threadIdx.x == 0) {
-            s_pair = find_pair(a.tile_base, a.npairs, t);
-            s_local = t - a.tile_base[s_pair];
+            const int t = (int)atomicAdd(&st->edge_next, 1u);
+            s_tile = t;
+            if (t < a.total_tiles) {
+                s_pair = find_pair(a.tile_base, a.npairs, t);
+                s_local = t - a.tile_base[s_pair];
+            }
         }
+        __syncthreads();
+        if (s_tile >= a.total_tiles) break;
         for (int i = threadIdx.x; i < TILE_TABLE; i += blockDim.x) {
             sk[i] = EMPTY64;
             sw[i] = 0xFFFFFFFFu;
@@ -131,6 +140,12 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                 kp = __ldg(P.keys + (size_t)y * W + x);
                 hp = half_cost(__ldg(P.C + (size_t)y * W + x), &bad);
             }
+            // the four forward candidates of this pixel; a label pair seen in
+            // an earlier direction is folded into that one (min weight), so
+            // a pixel inserts each pair once
+            pkey_t ck[4];
+            unsigned cw[4];
+            bool cv[4];
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
                 const int dx = d == 0 ? 1 : d == 1 ? -1 : d == 2 ? 0 : 1;
@@ -163,8 +178,19 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                         wb = __float_as_uint(w);
                     }
                 }
-                warp_insert(P, have, k, wb, sk, sw, st);
+#pragma unroll
+                for (int j = 0; j < d; ++j) {
+                    if (have && cv[j] && ck[j] == k) {
+                        cw[j] = min(cw[j], wb);
+                        have = false;
+                    }
+                }
+                ck[d] = k;
+                cw[d] = wb;
+                cv[d] = have;
             }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) warp_insert(P, cv[d], ck[d], cw[d], sk, sw, st);
         }
         __syncthreads();
         // flush the tile's unique edges to the pair's table
@@ -262,9 +288,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(const BatchArgs *__restric
             set_status(st, EPIC_ERR_INVALID);
             continue;
         }
-        const pkey_t wb = (pkey_t)P.hw[s] << 32;
-        P.adj[atomicAdd(P.deg + m, 1)] = wb | n;
-        P.adj[atomicAdd(P.deg + n, 1)] = wb | m;
+        const unsigned wb = P.hw[s];
+        P.adj[atomicAdd(P.deg + m, 1)] = make_uint4(n, wb, P.wmin[n], 0u);
+        P.adj[atomicAdd(P.deg + n, 1)] = make_uint4(m, wb, P.wmin[m], 0u);
     }
 }
 
@@ -295,7 +321,15 @@ __global__ void collect_kernel(const pkey_t *hkeys, const unsigned *hw, int cap_
 
 cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
     (void)a;
-    edges_kernel<<<lc.num_sms * 8, EDGE_THREADS, 0, lc.stream>>>(dev);
+    // one resident wave: every CTA keeps taking tiles until none are left
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_kernel,
+                                                                      EDGE_THREADS, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    edges_kernel<<<lc.num_sms * per_sm, EDGE_THREADS, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

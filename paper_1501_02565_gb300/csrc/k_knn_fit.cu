@@ -22,12 +22,14 @@
 //   * the settled list (node, distance).
 // Batches are appended in frontier order; only the batch that crosses K is
 // sorted (warp bitonic network) so that exactly the K smallest keys are
-// kept, and the finished list is sorted once more (all keys) before the fit.  All edges of all batch nodes are relaxed in one
+// kept, and every batch of the finished list is sorted before the fit.  All edges of all batch nodes are relaxed in one
 // pass: lanes take (node, edge) pairs found from a warp prefix sum of the
 // batch nodes' degrees (CSR row lengths).  A newly pushed node's row offsets
-// are prefetched into L1 for when it is settled; its lightest edge is read
-// at once, since the step's bound is kept as a running minimum over the
-// entries pushed and kept (no separate pass over the frontier).
+// are prefetched into L1 for when it is settled; its lightest edge comes
+// with the adjacency entry, since the step's bound is kept as a running
+// minimum over the entries pushed and kept (no separate pass over the
+// frontier).  The step's smallest key and bound are then two 32-bit warp
+// reductions (redux.sync).
 //
 // The fit uses centred coordinates x~ = p_n - p_m and fits the flow
 // u = p' - p (the same least-squares problem as fitting p', Eq. 2, with
@@ -108,37 +110,28 @@ __device__ __forceinline__ F2 warp_sum(F2 v) {
 __device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.lo; }
 
 __host__ __device__ __forceinline__ size_t knn_warp_bytes(int hs, int fs, int km) {
-    return (size_t)fs * 16 + (size_t)hs * 8 + (size_t)km * 8;
+    return (size_t)fs * 16 + (size_t)hs * 8 + (size_t)km * 8 + (((size_t)km * 2 + 7) & ~(size_t)7);
 }
 
 __device__ __forceinline__ void prefetch_l1(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// Sort the settled list (node, distance) by key (distance, node) in place,
-// using `scratch` (>= next power of two of n keys) as workspace; one warp.
-__device__ void sort_settled(unsigned *rn, float *rd, int n, pkey_t *scratch, int lane) {
-    int np2 = 1;
-    while (np2 < n) np2 <<= 1;
-    for (int i = lane; i < np2; i += 32)
-        scratch[i] = i < n ? make_key(rd[i], rn[i]) : EMPTY64;
-    __syncwarp();
-    for (int kk = 2; kk <= np2; kk <<= 1) {
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int i = lane; i < np2; i += 32) {
-                const int pr = i ^ j;
-                if (pr > i) {
-                    const pkey_t x = scratch[i], y = scratch[pr];
-                    const bool asc = (i & kk) == 0;
-                    if ((x > y) == asc) {
-                        scratch[i] = y;
-                        scratch[pr] = x;
-                    }
-                }
-            }
-            __syncwarp();
-        }
+// Sort the settled list (node, distance) by key (distance, node) in place.
+// Batches were appended in key order (every key of a batch is below the
+// bound B of its step, every later key at least B), so an entry's sorted
+// position is its batch's start plus its rank within the batch; bs[i] holds
+// the start of entry i's batch.  `scratch` (>= n keys) is workspace; one warp.
+__device__ void sort_settled(unsigned *rn, float *rd, const unsigned short *bs, int n,
+                             pkey_t *scratch, int lane) {
+    for (int i = lane; i < n; i += 32) {
+        const int b = bs[i];
+        const pkey_t ki = make_key(rd[i], rn[i]);
+        int r = 0;
+        for (int j = b; j < n && bs[j] == b; ++j) r += make_key(rd[j], rn[j]) < ki;
+        scratch[b + r] = ki;
     }
+    __syncwarp();
     for (int i = lane; i < n; i += 32) {
         rn[i] = key_label(scratch[i]);
         rd[i] = key_dist(scratch[i]);
@@ -162,6 +155,9 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
     unsigned *hv = hk + HS;
     unsigned *rn = hv + HS;
     float *rd = reinterpret_cast<float *>(rn + KM);
+    // batch start of each settled entry (K stays far below 65536: the tables of one
+    // warp must fit in shared memory)
+    unsigned short *bs = reinterpret_cast<unsigned short *>(rd + KM);
     const unsigned lt_mask = (1u << lane) - 1u;
 
     // matches are handed out one at a time from a counter: search costs
@@ -175,7 +171,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
         const PairDev &P = a.pairs[pi];
         const int m = gm - a.match_base[pi];
         const int K = P.K;
-        const pkey_t *adj = P.adj;
+        const uint4 *adj = P.adj;
         const unsigned *wmin = P.wmin;
 
         for (int i = lane; i < HS; i += 32) {
@@ -202,15 +198,14 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
         int fn = 1, cnt = 0;
         bool overflow = false;
         while (cnt < K) {
-            // (1) smallest current key and the batch bound B
-            pkey_t kmin = rk;
-            float bound = rb;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const pkey_t ok = __shfl_xor_sync(0xffffffffu, kmin, o);
-                kmin = ok < kmin ? ok : kmin;
-                bound = fminf(bound, __shfl_xor_sync(0xffffffffu, bound, o));
-            }
+            // (1) smallest current key and the batch bound B, as warp
+            //     reductions of 32-bit words: distances are non-negative, so
+            //     their float bits order like the values (+inf included)
+            const unsigned kd = __reduce_min_sync(0xffffffffu, (unsigned)(rk >> 32));
+            const unsigned kn =
+                __reduce_min_sync(0xffffffffu, (unsigned)(rk >> 32) == kd ? (unsigned)rk : EMPTY32);
+            const pkey_t kmin = ((pkey_t)kd << 32) | kn;
+            const float bound = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(rb)));
             if (kmin == EMPTY64) break;  // component exhausted
             rk = EMPTY64;
             rb = __int_as_float(0x7f800000);
@@ -281,6 +276,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                         hv[sl] |= SETTLED;
                         rn[p] = key_label(k);
                         rd[p] = key_dist(k);
+                        bs[p] = (unsigned short)cnt;
                     }
                     nb += __popc(bb);
                 }
@@ -304,6 +300,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                 if (cnt + lane < K) {
                     rn[cnt + lane] = key_label(bk);
                     rd[cnt + lane] = key_dist(bk);
+                    bs[cnt + lane] = (unsigned short)cnt;
                 }
                 cnt = K;
                 __syncwarp();
@@ -325,35 +322,40 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                     rbeg = __ldg(P.row + v);
                     dg = __ldg(P.row + v + 1) - rbeg;
                 }
+                // the chunk's batch nodes sit in lanes [0, nbc): the scan and
+                // the owner search need only ceil(log2 nbc) levels (batches
+                // average ~5 nodes)
+                const int nbc = min(nb - b0, 32);
+                int top = 1;
+                while (top < nbc) top <<= 1;
                 int incl = dg;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
+                for (int o = 1; o < top; o <<= 1) {
                     const int t = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += t;
                 }
                 const int excl = incl - dg;
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const int total = __shfl_sync(0xffffffffu, incl, nbc - 1);
                 for (int e0 = 0; e0 < total; e0 += 32) {
                     const int e = e0 + lane;
                     // owner: the last lane whose edge range starts at or before e
                     int owner = 0;
-#pragma unroll
-                    for (int stp = 16; stp; stp >>= 1) {
+                    for (int stp = top >> 1; stp; stp >>= 1) {
                         const int cand = owner + stp;
                         const int ex = __shfl_sync(0xffffffffu, excl, cand & 31);
-                        if (cand < 32 && ex <= e) owner = cand;
+                        if (cand < nbc && ex <= e) owner = cand;
                     }
                     const pkey_t ok = __shfl_sync(0xffffffffu, vk, owner);
                     const int oex = __shfl_sync(0xffffffffu, excl, owner);
                     const int obeg = __shfl_sync(0xffffffffu, rbeg, owner);
                     const bool act = e < total;
                     bool push = false;
-                    unsigned slot = 0, u = 0;
+                    unsigned slot = 0, u = 0, uw = 0;
                     float nd = 0.f;
                     if (act) {
-                        const pkey_t ed = __ldg(adj + obeg + (e - oex));
-                        u = (unsigned)ed;
-                        nd = __fadd_rn(key_dist(ok), __uint_as_float((unsigned)(ed >> 32)));
+                        const uint4 ed = __ldg(adj + obeg + (e - oex));
+                        u = ed.x;
+                        uw = ed.z;
+                        nd = __fadd_rn(key_dist(ok), __uint_as_float(ed.y));
                         unsigned sl = node_slot(u, HS);
                         int probes = 0;
                         for (;;) {
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                     if (push && !overflow) {
                         const int p = fn + __popc(bal & lt_mask);
                         const pkey_t nk = make_key(nd, u);
-                        const float tw = __fadd_rn(nd, __uint_as_float(__ldg(wmin + u)));
+                        const float tw = __fadd_rn(nd, __uint_as_float(uw));
                         fk[p] = nk;
                         fs[p] = slot;
                         fw[p] = tw;
@@ -431,10 +433,10 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
         if (cnt > K) cnt = K;
         __syncwarp();
         // batches are appended in frontier order, which follows the order
-        // of the adjacency rows (filled with atomics); sorting the list by
+        // of the adjacency rows (filled with atomics); sorting each batch by
         // key restores Dijkstra's settle order, so the fit below sums in a
         // canonical order and the result is bit-for-bit reproducible
-        sort_settled(rn, rd, cnt, fk, lane);
+        sort_settled(rn, rd, bs, cnt, fk, lane);
 
         // locally-weighted affine fit over the cnt settled neighbours
         const float4 pm = __ldg(P.matches + m);

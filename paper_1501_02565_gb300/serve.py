@@ -34,7 +34,7 @@ from .native import EpicInterp
 # bytes of library scratch per pixel and per match (keys, bins, edge table,
 # adjacency, models; see the arena layout in csrc/epic_interp.cu)
 _SCRATCH_PER_PIXEL = 8.2
-_SCRATCH_PER_MATCH = 16 * 12 + 16 * 2 * 8 + 96   # edge table, CSR adjacency, per-node
+_SCRATCH_PER_MATCH = 16 * 12 + 16 * 2 * 16 + 96   # edge table, CSR adjacency, per-node
 
 
 @dataclasses.dataclass
