@@ -34,7 +34,7 @@
 // The fit uses centred coordinates x~ = p_n - p_m and fits the flow
 // u = p' - p (the same least-squares problem as fitting p', Eq. 2, with
 // A = I + B): 12 weighted sums, warp-reduced, then the 3x3 normal equations
-// solved in float64.  The sums stay in float32 registers but are carried as
+// solved in float64 by cofactors, spread over the lanes of the warp.  The sums stay in float32 registers but are carried as
 // unevaluated pairs hi + lo: every product w * t is split exactly with an FMA
 // (TwoProduct) and every addition with TwoSum, so the accumulated sums keep
 // about twice float32's precision.  Kernel weights span many decades when a
@@ -475,46 +475,70 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
             acc_prod(s[13], k, uh); s[13].lo = __fmaf_rn(k, ul, s[13].lo);
             acc_prod(s[14], k, vh); s[14].lo = __fmaf_rn(k, vl, s[14].lo);
         }
-        double S[15];
+        // The totals are on every lane.  The float64 part runs lane-parallel:
+        // float64 throughput is a small fraction of float32's here, and every
+        // warp instruction costs the same however few lanes are active, so
+        // each conversion, cofactor, quotient and coefficient goes to its own
+        // lane and the operands travel by shuffles.
+        F2 mine = F2{0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < 15; ++i) S[i] = to_d(warp_sum(s[i]));
+        for (int i = 0; i < 15; ++i) {
+            const F2 t = warp_sum(s[i]);
+            if (lane == i) mine = t;
+        }
+        // lane i < 15 holds sum i: M00 M01 M02 M11 M12 M22 (0-5), the
+        // right-hand sides ru (6-8), rv (9-11), and the NW sums (12-14)
+        const double Sl = to_d(mine);
+        auto S = [&](int src) { return __shfl_sync(0xffffffffu, Sl, src); };
+        // cofactors of the symmetric matrix M, c00 c01 c02 c11 c12 c22 on
+        // lanes 0-5, each c = x y - z w with the operands' sum indices packed
+        // in nibbles
+        const int cj = lane < 6 ? lane : 0;
+        const double cx = S((0x010143 >> (4 * cj)) & 15), cy = S((0x325425 >> (4 * cj)) & 15);
+        const double cz = S((0x102314 >> (4 * cj)) & 15), cw = S((0x142254 >> (4 * cj)) & 15);
+        const double Cl = __fma_rn(cx, cy, -__dmul_rn(cz, cw));
+        auto Cf = [&](int src) { return __shfl_sync(0xffffffffu, Cl, src); };
+        const double M00 = S(0), M01 = S(1), M02 = S(2), M11 = S(3), M22 = S(5);
+        const double c00 = Cf(0), c01 = Cf(1), c02 = Cf(2);
+        const double det = __fma_rn(M02, c02, __fma_rn(M01, c01, __dmul_rn(M00, c00)));
+        const double tr = __dadd_rn(__dadd_rn(M00, M11), M22);
+        // one division for four quotients: 1/det, the NW flow sum13/sum12
+        // and sum14/sum12 (Eq. 1), and tr M / 3
+        const double sk = S(12), s13 = S(13), s14 = S(14);
+        const double qn = lane == 1 ? s13 : lane == 2 ? s14 : lane == 3 ? tr : 1.0;
+        const double qd = lane == 0 ? det : lane == 3 ? 3.0 : lane < 3 ? sk : 1.0;
+        const double q = qn / qd;
+        const double id = __shfl_sync(0xffffffffu, q, 0);
+        const double nwu = __shfl_sync(0xffffffffu, q, 1);
+        const double nwv = __shfl_sync(0xffffffffu, q, 2);
+        const double tr3 = __shfl_sync(0xffffffffu, q, 3);
+        const bool fit_ok = a.estimator == 0 && cnt >= 3 &&
+                            det > (double)a.fallback_eps * tr3 * tr3 * tr3;
+        // affine coefficients bu0 bu1 bu2 bv0 bv1 bv2 on lanes 0-5:
+        // (row k of the adjugate) . (ru or rv), times 1/det
+        const int bk = lane < 6 ? lane : 0;
+        const int rr = bk % 3, rbase = bk < 3 ? 6 : 9;
+        const double bx0 = Cf(rr), bx1 = Cf(rr == 0 ? 1 : rr == 1 ? 3 : 4),
+                     bx2 = Cf(rr == 0 ? 2 : rr == 1 ? 4 : 5);
+        const double by0 = S(rbase), by1 = S(rbase + 1), by2 = S(rbase + 2);
+        const float bl =
+            (float)__dmul_rn(__fma_rn(bx2, by2, __fma_rn(bx1, by1, __dmul_rn(bx0, by0))), id);
+        auto B = [&](int src) { return __shfl_sync(0xffffffffu, bl, src); };
+        const float bu0 = B(0), bu1 = B(1), bu2 = B(2), bv0 = B(3), bv1 = B(4), bv2 = B(5);
         if (lane == 0) {
-            const double M00 = S[0], M01 = S[1], M02 = S[2], M11 = S[3], M12 = S[4], M22 = S[5];
-            // cofactors of the symmetric matrix M
-            const double c00 = M11 * M22 - M12 * M12;
-            const double c01 = M12 * M02 - M01 * M22;
-            const double c02 = M01 * M12 - M11 * M02;
-            const double c11 = M00 * M22 - M02 * M02;
-            const double c12 = M01 * M02 - M00 * M12;
-            const double c22 = M00 * M11 - M01 * M01;
-            const double det = M00 * c00 + M01 * c01 + M02 * c02;
-            const double tr3 = (M00 + M11 + M22) / 3.0;
             float4 r0, r1;
             int fb;
-            // Nadaraya-Watson estimate at p_m (Eq. 1), as a flow: the
-            // kernel-weighted mean of the neighbours' flows p'_n - p_n
-            const double sk = S[12];
-            const double nwu = S[13] / sk, nwv = S[14] / sk;
             if (a.write_keep) {
                 // consistency check (Sec. 4.1): keep the match when its own
-                // flow is within the threshold of the estimate
+                // flow is within the threshold of the NW estimate
                 const double du = nwu - ((double)pm.z - (double)pm.x);
                 const double dv = nwv - ((double)pm.w - (double)pm.y);
                 const double thr = (double)a.prune_threshold;
                 P.keep[m] = du * du + dv * dv <= thr * thr ? 1 : 0;
             }
-            if (a.estimator == 0 && cnt >= 3 && det > (double)a.fallback_eps * tr3 * tr3 * tr3) {
-                const double ru0 = S[6], ru1 = S[7], ru2 = S[8];
-                const double rv0 = S[9], rv1 = S[10], rv2 = S[11];
-                const double id = 1.0 / det;
-                const double bu0 = (c00 * ru0 + c01 * ru1 + c02 * ru2) * id;
-                const double bu1 = (c01 * ru0 + c11 * ru1 + c12 * ru2) * id;
-                const double bu2 = (c02 * ru0 + c12 * ru1 + c22 * ru2) * id;
-                const double bv0 = (c00 * rv0 + c01 * rv1 + c02 * rv2) * id;
-                const double bv1 = (c01 * rv0 + c11 * rv1 + c12 * rv2) * id;
-                const double bv2 = (c02 * rv0 + c12 * rv1 + c22 * rv2) * id;
-                r0 = make_float4((float)bu2, (float)bv2, (float)bu0, (float)bu1);
-                r1 = make_float4((float)bv0, (float)bv1, pm.x, pm.y);
+            if (fit_ok) {
+                r0 = make_float4(bu2, bv2, bu0, bu1);
+                r1 = make_float4(bv0, bv1, pm.x, pm.y);
                 fb = 0;
             } else {
                 // the NW estimator, or the LA fit's fallback: the flow is
