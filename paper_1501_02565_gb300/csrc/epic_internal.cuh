@@ -138,6 +138,8 @@ struct RunState {
     unsigned changed[3];   // per-pass dirty-tile counters (rotating)
     unsigned work[4];      // relaxation tile dispensers: passes (rotating), phase 1
     unsigned knn_next;     // K-NN match dispenser
+    unsigned knn_overflow; // matches whose search outgrew the small tables
+    unsigned knn_retry;    // dispenser of the retry pass over those matches
     unsigned edge_next;    // boundary-edge tile dispenser
     unsigned compact_done; // CTAs finished in the pruning compaction
     GridBarrier barrier;
@@ -154,7 +156,8 @@ struct BatchArgs {
     const int *clear_base;   // [npairs+1] prefix of clear chunks
     int total_tiles, total_matches, total_chunks, total_hash, total_clear;
     int max_degree;
-    int knn_hs, knn_fs, knn_kmax;  // per-warp K-NN table sizes (powers of 2) and K bound
+    int knn_hs, knn_fs, knn_kmax;  // main-pass K-NN table sizes per warp, and K bound
+    int *knn_retry_list;   // [KNN_RETRY_CAP] global match indices to search again
     int max_passes;
     int weight_squared;
     float fallback_eps;
@@ -187,6 +190,7 @@ constexpr int WRITEOUT_CHUNK = 1024;  // pixels per write-out work item
 constexpr int CLEAR_CHUNK = 4096;     // 8-byte words per clear work item
 constexpr int DT_THREADS = 256;
 constexpr int KNN_WARPS = 8;          // warps (= matches in flight) per CTA
+constexpr int KNN_RETRY_CAP = 4096;   // matches the large-table retry pass can take
 constexpr int EDGE_THREADS = 256;
 
 // Host-side launchers (one per kernel file).
@@ -250,6 +254,7 @@ cudaError_t launch_collect_edges(const PairDev *pair_host_copy, int *em,
                                  cudaStream_t stream);
 size_t dt_smem_bytes(int tile_w, int tile_h, int apron);
 void knn_table_sizes(int max_K, int *hs, int *fs);
+void knn_retry_table_sizes(int max_K, int smem_limit, int *hs, int *fs);
 size_t knn_smem_per_warp(int max_K);
 int knn_warps_per_cta(int max_K, int smem_limit);
 

@@ -403,7 +403,8 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     if (e != cudaSuccess) { delete h; return EPIC_ERR_CUDA; }
     h->num_sms = prop.multiProcessorCount;
     h->smem_optin = (int)prop.sharedMemPerBlockOptin;
-    e = cudaMalloc(&h->state, sizeof(RunState) + 64);
+    // the run state, a scratch counter, then the K-NN retry list
+    e = cudaMalloc(&h->state, sizeof(RunState) + 64 + sizeof(int) * epic::KNN_RETRY_CAP);
     if (e != cudaSuccess) { delete h; return EPIC_ERR_OOM; }
     h->scratch_count = reinterpret_cast<int *>(reinterpret_cast<char *>(h->state) + sizeof(RunState) + 32);
     cudaMemset(h->state, 0, sizeof(RunState) + 64);
@@ -567,6 +568,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     a.max_degree = c.max_degree;
     epic::knn_table_sizes(knn_K, &a.knn_hs, &a.knn_fs);
     a.knn_kmax = knn_K;
+    a.knn_retry_list = reinterpret_cast<int *>(reinterpret_cast<char *>(h->state) + sizeof(RunState) + 64);
     a.max_passes = c.max_passes;
     a.weight_squared = c.weight_squared ? 1 : 0;
     a.fallback_eps = c.fallback_eps;
@@ -1151,9 +1153,10 @@ int epic_gradient_cost(const float *image, int frames, int H, int W, int channel
 
 int epic_interp_launches_per_run(epic_interp_t *h, int n) {
     (void)n;
-    // prepare, relaxation, edges, CSR offsets, scatter, K-NN + fit,
-    // write-out; pruning adds the first pass's six and the compaction
-    return h && h->cfg.prune ? 14 : 7;
+    // prepare, relaxation, edges, CSR offsets, scatter, K-NN + fit and its
+    // retry pass, write-out; pruning adds the first pass's seven and the
+    // compaction
+    return h && h->cfg.prune ? 16 : 8;
 }
 
 const char *epic_interp_last_error(epic_interp_t *h) {

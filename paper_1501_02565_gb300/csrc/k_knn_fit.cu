@@ -14,35 +14,42 @@
 // place going to the smaller index.  A batch is usually several nodes, so a
 // match needs ~5x fewer steps than one-node-at-a-time settling.
 // Per-warp shared memory holds
-//   * the frontier: packed keys (t bits << 32 | node) and their table slots,
-//     rebuilt every step so that only current entries survive; the step's
-//     batch is moved to the tail of the same arrays,
-//   * an open-addressing table node -> tentative distance (bit 31 = settled),
-//     updated with compare-and-swap so several lanes may relax into one node,
-//   * the settled list (node, distance).
+//   * the frontier: packed keys (t bits << 32 | node), their table slots and
+//     t + w_min, rebuilt every step so that only current entries survive,
+//   * an open-addressing table node -> tentative distance (bit 31 =
+//     settled), updated with compare-and-swap so several lanes may relax
+//     into one node,
+//   * the settled list (node, distance, start of its batch).
+// The main pass sizes these tables for the searches seen on optical-flow
+// match graphs (about 1.5 K nodes touched) so that four CTAs of eight warps
+// share an SM; a search that outgrows them is queued and run again by a
+// second launch with one warp per CTA and tables ~20x larger, so no
+// neighbourhood shape fails.
 // Batches are appended in frontier order; only the batch that crosses K is
 // sorted (warp bitonic network) so that exactly the K smallest keys are
-// kept, and every batch of the finished list is sorted before the fit.  All edges of all batch nodes are relaxed in one
-// pass: lanes take (node, edge) pairs found from a warp prefix sum of the
-// batch nodes' degrees (CSR row lengths).  A newly pushed node's row offsets
-// are prefetched into L1 for when it is settled; its lightest edge comes
-// with the adjacency entry, since the step's bound is kept as a running
-// minimum over the entries pushed and kept (no separate pass over the
-// frontier).  The step's smallest key and bound are then two 32-bit warp
-// reductions (redux.sync).
+// kept, and every batch of the finished list is sorted before the fit.  All
+// edges of all batch nodes are relaxed in one pass: lanes take (node, edge)
+// pairs found from a warp prefix sum of the batch nodes' degrees (CSR row
+// lengths).  A newly pushed node's row offsets are prefetched into L1 for
+// when it is settled; its lightest edge comes with the adjacency entry,
+// since the step's bound is kept as a running minimum over the entries
+// pushed and kept (no separate pass over the frontier).  The step's smallest
+// key and bound are then two 32-bit warp reductions (redux.sync).
 //
 // The fit uses centred coordinates x~ = p_n - p_m and fits the flow
 // u = p' - p (the same least-squares problem as fitting p', Eq. 2, with
 // A = I + B): 12 weighted sums, warp-reduced, then the 3x3 normal equations
-// solved in float64 by cofactors, spread over the lanes of the warp.  The sums stay in float32 registers but are carried as
-// unevaluated pairs hi + lo: every product w * t is split exactly with an FMA
+// solved in float64 by cofactors, spread over the lanes of the warp.  The
+// sums stay in float32 registers but are carried as unevaluated pairs hi + lo: every product w * t is split exactly with an FMA
 // (TwoProduct) and every addition with TwoSum, so the accumulated sums keep
 // about twice float32's precision.  Kernel weights span many decades when a
 // neighbourhood crosses strong edges, and the normal matrix is then nearly
-// singular along some direction; plain float32 sums lose that direction.  A degenerate fit (fewer than 3 neighbours or
-// det M <= eps (tr M/3)^3) falls back to the Nadaraya-Watson estimate of
+// singular along some direction; plain float32 sums lose that direction.  A
+// degenerate fit (fewer than 3 neighbours or det M <= eps (tr M/3)^3) falls back to the Nadaraya-Watson estimate of
 // Eq. 1 at p_m (kernel weights k), kept as a constant flow over the cell.
 #include "epic_internal.cuh"
+
+#include <algorithm>
 
 namespace epic {
 
@@ -61,7 +68,7 @@ __device__ __forceinline__ float key_dist(pkey_t k) {
 __device__ __forceinline__ unsigned key_label(pkey_t k) { return (unsigned)k; }
 
 __device__ __forceinline__ unsigned node_slot(unsigned u, int hs) {
-    return (u * 0x9E3779B1u) >> 7 & (unsigned)(hs - 1);
+    return __umulhi(u * 0x9E3779B1u, (unsigned)hs);   // any table size
 }
 
 // Compensated float32 accumulator: the value is hi + lo.
@@ -139,20 +146,24 @@ __device__ void sort_settled(unsigned *rn, float *rd, const unsigned short *bs, 
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs *__restrict__ ap) {
+// HS, FS: this launch's table sizes; retry = 0 for the main pass (small
+// tables, several CTAs per SM; a match that outgrows them is queued), 1 for
+// the pass over the queued matches (large tables, one warp per CTA).
+__global__ void __launch_bounds__(KNN_WARPS * 32, 4)
+    knn_fit_kernel(const BatchArgs *__restrict__ ap, int HS, int FS, int retry) {
     const BatchArgs a = *ap;
     extern __shared__ __align__(16) unsigned char smem[];
     RunState *st = a.state;
     if (get_status(st) != 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int HS = a.knn_hs, FS = a.knn_fs, KM = a.knn_kmax;
+    const int KM = a.knn_kmax;
     const size_t per_warp = knn_warp_bytes(HS, FS, KM);
     unsigned char *base = smem + per_warp * wid;
     pkey_t *fk = reinterpret_cast<pkey_t *>(base);
     unsigned *fs = reinterpret_cast<unsigned *>(fk + FS);
     float *fw = reinterpret_cast<float *>(fs + FS);   // t + lightest edge of each entry
-    unsigned *hk = reinterpret_cast<unsigned *>(fw + FS);
-    unsigned *hv = hk + HS;
+    unsigned *hk = reinterpret_cast<unsigned *>(fw + FS);   // node table: node
+    unsigned *hv = hk + HS;                                 // tentative distance | SETTLED
     unsigned *rn = hv + HS;
     float *rd = reinterpret_cast<float *>(rn + KM);
     // batch start of each settled entry (K stays far below 65536: the tables of one
@@ -164,9 +175,18 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
     // vary with the neighbourhood, and a static split leaves a long tail
     for (;;) {
         int gm = 0;
-        if (lane == 0) gm = (int)atomicAdd(&st->knn_next, 1u);
-        gm = __shfl_sync(0xffffffffu, gm, 0);
-        if (gm >= a.total_matches) break;
+        if (retry) {
+            const unsigned nq = min(*(volatile unsigned *)&st->knn_overflow, (unsigned)KNN_RETRY_CAP);
+            unsigned q = 0;
+            if (lane == 0) q = atomicAdd(&st->knn_retry, 1u);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            if (q >= nq) break;
+            gm = a.knn_retry_list[q];
+        } else {
+            if (lane == 0) gm = (int)atomicAdd(&st->knn_next, 1u);
+            gm = __shfl_sync(0xffffffffu, gm, 0);
+            if (gm >= a.total_matches) break;
+        }
         const int pi = find_pair(a.match_base, a.npairs, gm);
         const PairDev &P = a.pairs[pi];
         const int m = gm - a.match_base[pi];
@@ -361,10 +381,9 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                         for (;;) {
                             const unsigned prev = atomicCAS(hk + sl, EMPTY32, u);
                             if (prev == EMPTY32 || prev == u) break;
-                            sl = (sl + 1) & (unsigned)(HS - 1);
+                            sl = sl + 1 == (unsigned)HS ? 0u : sl + 1;
                             if (++probes >= HS) { overflow = true; break; }
                         }
-                        slot = sl;
                         if (!overflow) {
                             const unsigned nb_bits = __float_as_uint(nd);
                             unsigned cur = hv[sl];
@@ -374,6 +393,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
                                 cur = old;
                             }
                         }
+                        slot = sl;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, push);
                     const int np = __popc(bal);
@@ -427,6 +447,18 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
             if (overflow) break;
         }
         if (overflow) {
+            if (!retry) {
+                // queued for the pass with large tables
+                if (lane == 0) {
+                    const unsigned q = atomicAdd(&st->knn_overflow, 1u);
+                    if (q < (unsigned)KNN_RETRY_CAP)
+                        a.knn_retry_list[q] = gm;
+                    else
+                        set_status(st, EPIC_ERR_CAPACITY);
+                }
+                __syncwarp();
+                continue;
+            }
             if (lane == 0) set_status(st, EPIC_ERR_CAPACITY);
             cnt = 0;
         }
@@ -562,17 +594,24 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_fit_kernel(const BatchArgs
     }
 }
 
-int next_pow2(int x) {
-    int p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-
 }  // namespace
 
+// Main-pass tables: ~3.84 K node slots (the searches here touch about 1.5 K
+// nodes) and ~1.92 K frontier entries, so that 8 warps' tables fit four CTAs
+// on an SM; a search that outgrows them is run again with large tables.
 void knn_table_sizes(int max_K, int *hs, int *fs) {
-    *hs = next_pow2(max_K * 4 > 64 ? max_K * 4 : 64);
-    *fs = next_pow2(max_K * 2 > 64 ? max_K * 2 : 64);
+    const int k = max_K > 1 ? max_K : 1;
+    *hs = std::max(64, (k * 384 / 100 + 31) / 32 * 32);
+    *fs = std::max(64, (k * 192 / 100 + 31) / 32 * 32);
+}
+
+// Retry-pass tables: the largest power-of-two node table (and a frontier
+// half its size) whose tables fit one warp per CTA.
+void knn_retry_table_sizes(int max_K, int smem_limit, int *hs, int *fs) {
+    int h = 64;
+    while (knn_warp_bytes(2 * h, h, max_K) <= (size_t)smem_limit && h < (1 << 20)) h *= 2;
+    *hs = h;
+    *fs = h / 2;
 }
 
 size_t knn_smem_per_warp(int max_K) {
@@ -594,16 +633,25 @@ cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const Launc
     (void)a;
     int warps = knn_warps_per_cta(max_K, lc.smem_optin);
     if (warps < 1) return cudaErrorInvalidValue;
-    size_t smem = knn_smem_per_warp(max_K) * warps;
-    cudaError_t e = cudaFuncSetAttribute(
-        knn_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int hs, fs, rhs, rfs;
+    knn_table_sizes(max_K, &hs, &fs);
+    knn_retry_table_sizes(max_K, lc.smem_optin, &rhs, &rfs);
+    const size_t smem = knn_warp_bytes(hs, fs, max_K) * warps;
+    const size_t rsmem = knn_warp_bytes(rhs, rfs, max_K);
+    cudaError_t e = cudaFuncSetAttribute(knn_fit_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max(smem, rsmem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_fit_kernel,
                                                       warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    knn_fit_kernel<<<per_sm * lc.num_sms, warps * 32, smem, lc.stream>>>(dev);
+    knn_fit_kernel<<<per_sm * lc.num_sms, warps * 32, smem, lc.stream>>>(dev, hs, fs, 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the queued matches (usually none: every warp exits at once)
+    knn_fit_kernel<<<lc.num_sms, 32, rsmem, lc.stream>>>(dev, rhs, rfs, 1);
     return cudaGetLastError();
 }
 

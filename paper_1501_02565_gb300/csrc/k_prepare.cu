@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
         st->changed[0] = st->changed[1] = st->changed[2] = 0;
         st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
         st->knn_next = 0;
+        st->knn_overflow = 0;
+        st->knn_retry = 0;
         st->edge_next = 0;
         st->barrier.count = 0;
         st->compact_done = 0;

@@ -47,6 +47,29 @@ def test_tile_shapes_give_identical_keys(tile):
     assert np.array_equal(g["flow"], base["flow"])
 
 
+def test_hub_graph_searches_outgrow_the_small_tables():
+    # one match at the centre and 150 on a circle around it: the centre's
+    # cell touches ~80 other cells, so a search that settles the centre
+    # pushes ~80 nodes at once, more than the main pass's frontier holds at
+    # K = 30 (64 entries).  Those searches are queued and run again with
+    # large tables; the result must still agree with the oracle.
+    rng = np.random.default_rng(77)
+    H = W = 256
+    C = (0.5 + rng.uniform(-0.01, 0.01, size=(H, W))).astype(np.float32)
+    ang = np.linspace(0.0, 2.0 * np.pi, 150, endpoint=False)
+    xs = np.r_[128.0, np.round(128.0 + 100.0 * np.cos(ang))]
+    ys = np.r_[128.0, np.round(128.0 + 100.0 * np.sin(ang))]
+    M = np.stack([xs, ys, xs + 1.5 + 0.01 * ys, ys - 0.5 + 0.01 * xs], 1).astype(np.float32)
+    D, L = oracle.geodesic(C, M)
+    em, en, _ = oracle.graph(C, D, L, M)
+    deg = np.bincount(np.r_[em, en], minlength=len(M))
+    assert deg[0] > 64
+    # a = 0.05 keeps every kernel weight exp(-2 a D) of these long-range
+    # neighbourhoods (D up to ~100) inside float32's range
+    g, ref, rep = full_parity((C, M), K=30, a=0.05)
+    _print("hub", rep)
+
+
 def test_image_smaller_than_one_tile_and_single_match():
     C = np.full((5, 7), 0.3, np.float32)
     M = np.array([[3, 2, 5.5, 1.25]], np.float32)
