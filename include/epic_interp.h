@@ -164,7 +164,23 @@ int epic_interp_run_host(epic_interp_t *h, const float *cost_map,
 int epic_interp_run_batch_host(epic_interp_t *h, const epic_pair_desc_t *pairs,
                                int n, void *stream);
 
-/* Wait for the last run's stream and return its device status (then clear
+/* Streaming form of epic_interp_run_batch_host, for a sequence of batches
+ * with HOST buffers.  Enqueues the batch's uploads, its run and the
+ * downloads of its flows, and returns without waiting, so that consecutive
+ * calls overlap: a batch's uploads run on a copy stream while the previous
+ * batch computes, and its downloads on a second copy stream while the next
+ * one computes (the run itself goes on a third, internal stream).  At most
+ * two batches are in flight: a third call first waits, on the host, until
+ * the downloads of the batch two calls back have finished.  The host buffers
+ * must stay valid, and the inputs unchanged, until epic_interp_sync(h)
+ * returns; sync waits for every submitted batch and returns the device
+ * status.  Pinned host memory is needed for the copies to overlap.  The
+ * device staging (two buffers of the batch's inputs and flows) is owned by
+ * the handle.  Errors as epic_interp_run_batch. */
+int epic_interp_submit_batch_host(epic_interp_t *h, const epic_pair_desc_t *pairs, int n);
+
+/* Wait for the last run's stream (and for every batch submitted with
+ * epic_interp_submit_batch_host) and return the device status (then clear
  * it).  EPIC_OK when every stage completed within its limits. */
 int epic_interp_sync(epic_interp_t *h);
 

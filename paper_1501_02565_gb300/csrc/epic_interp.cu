@@ -53,6 +53,17 @@ struct epic_interp {
     bool pruned = false;            // last run pruned (device N, K changed)
     std::vector<int> n_submitted;   // last run's match counts as submitted
     cudaStream_t last_stream = nullptr;
+    // streaming host batches (epic_interp_submit_batch_host): internal
+    // streams for uploads, runs and downloads, and two staging buffers used
+    // alternately, each with the events of its batch's three phases
+    cudaStream_t st_up = nullptr, st_run = nullptr, st_down = nullptr;
+    struct HostSlot {
+        char *buf = nullptr;
+        size_t cap = 0;
+        cudaEvent_t up = nullptr, ran = nullptr, down = nullptr;
+        bool busy = false;
+    } hslot[2];
+    int next_hslot = 0;
     // device staging for epic_interp_run_host
     float *io_C = nullptr, *io_M = nullptr, *io_F = nullptr;
     size_t io_C_n = 0, io_M_n = 0, io_F_n = 0;
@@ -777,8 +788,90 @@ int epic_interp_run_batch_host(epic_interp_t *h, const epic_pair_desc_t *descs, 
     return epic_interp_sync(h);
 }
 
+int epic_interp_submit_batch_host(epic_interp_t *h, const epic_pair_desc_t *descs, int n) {
+    if (!h) return EPIC_ERR_INVALID;
+    if (!descs || n < 1) return fail(h, EPIC_ERR_INVALID, "empty batch");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(h, descs[i], i);
+        if (rc) return rc;
+    }
+    if (!h->st_up) {
+        cudaStream_t *ss[3] = {&h->st_up, &h->st_run, &h->st_down};
+        for (cudaStream_t *x : ss)
+            if ((e = cudaStreamCreateWithFlags(x, cudaStreamNonBlocking)))
+                return cuda_fail(h, e, "cudaStreamCreate");
+        for (auto &hs : h->hslot) {
+            cudaEvent_t *ev[3] = {&hs.up, &hs.ran, &hs.down};
+            for (cudaEvent_t *x : ev)
+                if ((e = cudaEventCreateWithFlags(x, cudaEventDisableTiming)))
+                    return cuda_fail(h, e, "cudaEventCreate");
+        }
+    }
+    Handle::HostSlot &hs = h->hslot[h->next_hslot];
+    h->next_hslot ^= 1;
+    if (hs.busy) {
+        // the batch two calls back: its downloads (hence its run) are done
+        if ((e = cudaEventSynchronize(hs.down))) return cuda_fail(h, e, "cudaEventSynchronize");
+        hs.busy = false;
+    }
+    // staging layout: per pair C, matches, flow (256-byte aligned)
+    std::vector<size_t> oc(n), om(n), of(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)descs[i].H * descs[i].W;
+        oc[i] = off; off = align_up(off + px * 4, 256);
+        om[i] = off; off = align_up(off + (size_t)descs[i].N * 16, 256);
+        of[i] = off; off = align_up(off + px * 8, 256);
+    }
+    if (off > hs.cap) {
+        // nothing in flight reads this slot any more
+        if (hs.buf) cudaFree(hs.buf);
+        hs.buf = nullptr;
+        hs.cap = 0;
+        if ((e = cudaMalloc(&hs.buf, off))) return cuda_fail(h, e, "submit_batch_host cudaMalloc");
+        hs.cap = off;
+    }
+    std::vector<epic_pair_desc_t> dev(n);
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)descs[i].H * descs[i].W;
+        if ((e = cudaMemcpyAsync(hs.buf + oc[i], descs[i].cost_map, px * 4,
+                                 cudaMemcpyHostToDevice, h->st_up)) ||
+            (e = cudaMemcpyAsync(hs.buf + om[i], descs[i].matches, (size_t)descs[i].N * 16,
+                                 cudaMemcpyHostToDevice, h->st_up)))
+            return cuda_fail(h, e, "submit_batch_host upload");
+        dev[i] = descs[i];
+        dev[i].cost_map = reinterpret_cast<const float *>(hs.buf + oc[i]);
+        dev[i].matches = reinterpret_cast<const float *>(hs.buf + om[i]);
+        dev[i].flow_out = reinterpret_cast<float *>(hs.buf + of[i]);
+    }
+    if ((e = cudaEventRecord(hs.up, h->st_up)) || (e = cudaStreamWaitEvent(h->st_run, hs.up, 0)))
+        return cuda_fail(h, e, "submit_batch_host upload event");
+    int rc = epic_interp_run_batch(h, dev.data(), n, h->st_run);
+    if (rc) return rc;
+    if ((e = cudaEventRecord(hs.ran, h->st_run)) ||
+        (e = cudaStreamWaitEvent(h->st_down, hs.ran, 0)))
+        return cuda_fail(h, e, "submit_batch_host run event");
+    for (int i = 0; i < n; ++i) {
+        const size_t px = (size_t)descs[i].H * descs[i].W;
+        if ((e = cudaMemcpyAsync(descs[i].flow_out, hs.buf + of[i], px * 8,
+                                 cudaMemcpyDeviceToHost, h->st_down)))
+            return cuda_fail(h, e, "submit_batch_host download");
+    }
+    if ((e = cudaEventRecord(hs.down, h->st_down))) return cuda_fail(h, e, "submit_batch_host");
+    hs.busy = true;
+    return EPIC_OK;
+}
+
 int epic_interp_sync(epic_interp_t *h) {
     if (!h) return EPIC_ERR_INVALID;
+    for (auto &hs : h->hslot) {
+        if (!hs.busy) continue;
+        cudaError_t e = cudaEventSynchronize(hs.down);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+        hs.busy = false;
+    }
     int rc = read_state(h);
     if (rc) return rc;
     int s = h->state_host->status;
@@ -1177,6 +1270,13 @@ void epic_interp_destroy(epic_interp_t *h) {
         if (sl.host) cudaFreeHost(sl.host);
         if (sl.done) cudaEventDestroy(sl.done);
     }
+    for (auto &hs : h->hslot) {
+        if (hs.buf) cudaFree(hs.buf);
+        for (cudaEvent_t x : {hs.up, hs.ran, hs.down})
+            if (x) cudaEventDestroy(x);
+    }
+    for (cudaStream_t x : {h->st_up, h->st_run, h->st_down})
+        if (x) cudaStreamDestroy(x);
     if (h->io_C) cudaFree(h->io_C);
     if (h->io_M) cudaFree(h->io_M);
     if (h->io_F) cudaFree(h->io_F);

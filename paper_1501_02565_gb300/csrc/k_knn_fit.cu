@@ -146,11 +146,14 @@ __device__ void sort_settled(unsigned *rn, float *rd, const unsigned short *bs, 
     __syncwarp();
 }
 
-// HS, FS: this launch's table sizes; retry = 0 for the main pass (small
-// tables, several CTAs per SM; a match that outgrows them is queued), 1 for
-// the pass over the queued matches (large tables, one warp per CTA).
+// HS, FS: this launch's table sizes.  RETRY = false: the main pass (small
+// tables, several CTAs per SM; a match that outgrows them is queued); true:
+// the pass over the queued matches (large tables, one warp per CTA), which
+// returns at once when nothing was queued.
+template <bool RETRY>
 __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
-    knn_fit_kernel(const BatchArgs *__restrict__ ap, int HS, int FS, int retry) {
+    knn_fit_kernel(const BatchArgs *__restrict__ ap, int HS, int FS) {
+    if (RETRY && *(volatile const unsigned *)&ap->state->knn_overflow == 0u) return;
     const BatchArgs a = *ap;
     extern __shared__ __align__(16) unsigned char smem[];
     RunState *st = a.state;
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
     // vary with the neighbourhood, and a static split leaves a long tail
     for (;;) {
         int gm = 0;
-        if (retry) {
+        if (RETRY) {
             const unsigned nq = min(*(volatile unsigned *)&st->knn_overflow, (unsigned)KNN_RETRY_CAP);
             unsigned q = 0;
             if (lane == 0) q = atomicAdd(&st->knn_retry, 1u);
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
             if (overflow) break;
         }
         if (overflow) {
-            if (!retry) {
+            if (!RETRY) {
                 // queued for the pass with large tables
                 if (lane == 0) {
                     const unsigned q = atomicAdd(&st->knn_overflow, 1u);
@@ -638,20 +641,22 @@ cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const Launc
     knn_retry_table_sizes(max_K, lc.smem_optin, &rhs, &rfs);
     const size_t smem = knn_warp_bytes(hs, fs, max_K) * warps;
     const size_t rsmem = knn_warp_bytes(rhs, rfs, max_K);
-    cudaError_t e = cudaFuncSetAttribute(knn_fit_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max(smem, rsmem));
+    cudaError_t e = cudaFuncSetAttribute(knn_fit_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(knn_fit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rsmem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_fit_kernel,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, knn_fit_kernel<false>,
                                                       warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    knn_fit_kernel<<<per_sm * lc.num_sms, warps * 32, smem, lc.stream>>>(dev, hs, fs, 0);
+    knn_fit_kernel<false><<<per_sm * lc.num_sms, warps * 32, smem, lc.stream>>>(dev, hs, fs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the queued matches (usually none: every warp exits at once)
-    knn_fit_kernel<<<lc.num_sms, 32, rsmem, lc.stream>>>(dev, rhs, rfs, 1);
+    // the queued matches (usually none: every CTA returns at once)
+    knn_fit_kernel<true><<<lc.num_sms, 32, rsmem, lc.stream>>>(dev, rhs, rfs);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ STATUS_NAMES = {
 EXPORTED = (
     "epic_config_default", "epic_interp_create", "epic_interp_run",
     "epic_interp_run_batch", "epic_interp_run_host",
-    "epic_interp_run_batch_host", "epic_interp_sync",
+    "epic_interp_run_batch_host", "epic_interp_submit_batch_host", "epic_interp_sync",
     "epic_interp_get_labels", "epic_interp_get_edge_count",
     "epic_interp_get_graph", "epic_interp_get_knn", "epic_interp_get_models",
     "epic_interp_get_pruning", "epic_interp_get_passes",
@@ -121,6 +121,8 @@ def load(path: str | None = None):
     lib.epic_interp_run_host.restype = I
     lib.epic_interp_run_batch_host.argtypes = [P, ctypes.POINTER(epic_pair_desc_t), I, P]
     lib.epic_interp_run_batch_host.restype = I
+    lib.epic_interp_submit_batch_host.argtypes = [P, ctypes.POINTER(epic_pair_desc_t), I]
+    lib.epic_interp_submit_batch_host.restype = I
     lib.epic_interp_sync.argtypes = [P]
     lib.epic_interp_sync.restype = I
     lib.epic_interp_get_labels.argtypes = [P, I, P, P, P]
@@ -198,6 +200,7 @@ class EpicInterp:
         if rc != EPIC_OK:
             raise EpicError(rc, "epic_interp_create failed")
         self.h = h
+        self._inflight = []   # host tensors of submitted batches, until sync()
 
     # -- helpers -------------------------------------------------------------
     def _check(self, rc, what):
@@ -263,11 +266,29 @@ class EpicInterp:
         rc = self.lib.epic_interp_run_batch_host(self.h, arr, n, _stream_handle(stream))
         self._check(rc, "epic_interp_run_batch_host")
 
+    def submit_batch_host(self, items):
+        """Streaming form of run_batch_host: enqueues the batch (uploads, run,
+        downloads) and returns at once; consecutive calls overlap.  The
+        tensors are kept alive here until sync()."""
+        n = len(items)
+        arr = (epic_pair_desc_t * n)()
+        for i, (C, M, K, a, F) in enumerate(items):
+            arr[i] = epic_pair_desc_t(C.data_ptr(), M.data_ptr(), C.shape[0],
+                                      C.shape[1], M.shape[0], int(K), float(a),
+                                      F.data_ptr())
+        self._inflight.append(items)
+        rc = self.lib.epic_interp_submit_batch_host(self.h, arr, n)
+        self._check(rc, "epic_interp_submit_batch_host")
+
     def sync(self):
-        self._check(self.lib.epic_interp_sync(self.h), "device status")
+        rc = self.lib.epic_interp_sync(self.h)
+        self._inflight = []
+        self._check(rc, "device status")
 
     def sync_status(self) -> int:
-        return self.lib.epic_interp_sync(self.h)
+        rc = self.lib.epic_interp_sync(self.h)
+        self._inflight = []
+        return rc
 
     def get_labels(self, pair=0, H=None, W=None, stream=None):
         import torch

@@ -104,3 +104,30 @@ def test_host_buffer_batch_matches_device_batch():
         for d, hh in zip(dev, host):
             assert torch.equal(d[4].cpu(), hh[4])
     eng.close()
+
+
+def test_streamed_host_batches_match_device_batches():
+    import torch
+    # three different batches submitted back to back (two in flight at a
+    # time, the third waits for the first's downloads), one sync at the end
+    pairs = [synth.config_pair(1, i) for i in range(6)]
+    batches = [pairs[0:2], pairs[2:5], pairs[5:6]]
+    eng = EpicInterp(0, max_pairs=4)
+    expect = []
+    for b in batches:
+        dev = [(torch.from_numpy(p.C).cuda(), torch.from_numpy(p.matches).cuda(), p.K, p.a,
+                torch.empty((p.H, p.W, 2), dtype=torch.float32, device="cuda")) for p in b]
+        eng.run_batch(dev)
+        eng.sync()
+        expect.append([d[4].cpu() for d in dev])
+    for _ in range(2):
+        host = [[(torch.from_numpy(p.C).pin_memory(), torch.from_numpy(p.matches).pin_memory(),
+                  p.K, p.a, torch.full((p.H, p.W, 2), float("nan")).pin_memory()) for p in b]
+                for b in batches]
+        for h in host:
+            eng.submit_batch_host(h)
+        eng.sync()
+        for h, ex in zip(host, expect):
+            for hh, e in zip(h, ex):
+                assert torch.equal(hh[4], e)
+    eng.close()
