@@ -395,9 +395,10 @@ def serving_requests(n: int, rate_hz: float, seed: int = 5000):
 
 def region_image(pair: Pair, seed: int = 0, channels: int = 3) -> np.ndarray:
     """A synthetic image float32 [H, W, channels] in [0, 1] of the pair's
-    first frame: a random colour per region, a low-contrast texture (two
-    random plane waves per region) and pixel noise, so that the image
-    gradient is strong at region boundaries and weak inside regions."""
+    first frame: a random colour per region, a texture of three random plane
+    waves per region (so that brightness constancy pins the motion inside a
+    region, as texture does in real frames) and pixel noise; the image
+    gradient is strongest at region boundaries."""
     if pair.regions is None:
         raise ValueError("pair has no region map")
     R = pair.regions
@@ -407,10 +408,10 @@ def region_image(pair: Pair, seed: int = 0, channels: int = 3) -> np.ndarray:
     base = rng.uniform(0.15, 0.85, size=(nreg, channels))
     ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
     img = base[R].astype(np.float64)
-    for _ in range(2):
+    for _ in range(3):
         ang = rng.uniform(0, math.pi, size=nreg)
-        freq = rng.uniform(0.05, 0.3, size=nreg)
-        amp = rng.uniform(0.0, 0.04, size=nreg)
+        freq = rng.uniform(0.1, 0.5, size=nreg)
+        amp = rng.uniform(0.03, 0.08, size=nreg)
         phase = rng.uniform(0, 2 * math.pi, size=nreg)
         wave = amp[R] * np.sin(freq[R] * (np.cos(ang[R]) * xs + np.sin(ang[R]) * ys) + phase[R])
         img += wave[..., None]
@@ -418,21 +419,56 @@ def region_image(pair: Pair, seed: int = 0, channels: int = 3) -> np.ndarray:
     return np.clip(img, 0.0, 1.0).astype(np.float32)
 
 
-def second_frame(image: np.ndarray, flow: np.ndarray) -> np.ndarray:
-    """A second frame for `image` under `flow` [H, W, 2]: I2(q) = I1(q - u(q)),
-    sampled bilinearly with clamped coordinates (a backward approximation of
-    moving every pixel p to p + u(p), exact for translations)."""
-    H, W = image.shape[:2]
-    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
-    X = np.clip(xs - flow[..., 0], 0, W - 1)
-    Y = np.clip(ys - flow[..., 1], 0, H - 1)
+def _bilinear(img: np.ndarray, X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """img [H, W, ...] sampled at (X, Y), coordinates clamped to the image."""
+    H, W = img.shape[:2]
+    X = np.clip(X, 0, W - 1)
+    Y = np.clip(Y, 0, H - 1)
     x0 = np.minimum(np.floor(X).astype(np.int64), max(W - 2, 0))
     y0 = np.minimum(np.floor(Y).astype(np.int64), max(H - 2, 0))
     x1 = np.minimum(x0 + 1, W - 1)
     y1 = np.minimum(y0 + 1, H - 1)
     ax = (X - x0)[..., None]
     ay = (Y - y0)[..., None]
-    I = image.astype(np.float64)
-    out = ((1 - ay) * ((1 - ax) * I[y0, x0] + ax * I[y0, x1]) +
-           ay * ((1 - ax) * I[y1, x0] + ax * I[y1, x1]))
+    I = img.astype(np.float64)
+    return ((1 - ay) * ((1 - ax) * I[y0, x0] + ax * I[y0, x1]) +
+            ay * ((1 - ax) * I[y1, x0] + ax * I[y1, x1]))
+
+
+def second_frame(image: np.ndarray, flow: np.ndarray, iterations: int = 12) -> np.ndarray:
+    """A second frame for `image` under the forward flow `flow` [H, W, 2]
+    (pixel p moves to p + u(p)): I2(q) = I1(q - v(q)), where the backward flow
+    v solves v(q) = u(q - v(q)) by fixed-point iteration (bilinear samples of
+    u).  Then I2(p + u(p)) = I1(p) wherever the motion is smooth and the
+    target is visible; at motion boundaries (occlusions) the iteration takes
+    whichever side it settles on.  For a translation v = u after one step."""
+    H, W = image.shape[:2]
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    u = flow.astype(np.float64)
+    v = u.copy()
+    for _ in range(iterations):
+        v = _bilinear(u, xs - v[..., 0], ys - v[..., 1])
+    out = _bilinear(image, xs - v[..., 0], ys - v[..., 1])
     return out.astype(np.float32)
+
+
+def smooth_perturbation(H: int, W: int, rms: float, seed: int = 0,
+                        scale: int = 32) -> np.ndarray:
+    """A smooth random flow field float32 [H, W, 2] with the given RMS
+    magnitude: Gaussian values on a grid of `scale`-pixel spacing,
+    interpolated bilinearly."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gh, gw = H // scale + 2, W // scale + 2
+    g = rng.normal(size=(gh, gw, 2))
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    f = _bilinear(g, xs / scale, ys / scale)
+    f *= rms / np.sqrt((f ** 2).sum(-1).mean())
+    return f.astype(np.float32)
+
+
+def in_frame(flow: np.ndarray) -> np.ndarray:
+    """bool [H, W]: pixels whose target p + u(p) lies inside the frame."""
+    H, W = flow.shape[:2]
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    tx, ty = xs + flow[..., 0], ys + flow[..., 1]
+    return (tx >= 0) & (tx <= W - 1) & (ty >= 0) & (ty <= H - 1)
