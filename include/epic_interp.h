@@ -25,7 +25,7 @@
  *   - Images are row-major, x = column, y = row; pixel centres are integer.
  *   - cost_map: float32 [H*W], every value finite and in [0, 2) (edge
  *     strengths).  The relaxation adds exact fixed-point step costs (units
- *     of 2^-32), so geodesic distances must stay below 512; a value outside
+ *     of 2^-31), so geodesic distances must stay below 1024; a value outside
  *     the range, or a pixel left unreached, is reported as EPIC_ERR_INVALID.
  *   - matches:  float32 [N*4], rows (x, y, x', y').  The source pixel of match
  *     m is (floor(x+0.5), floor(y+0.5)) and must lie inside the image; two

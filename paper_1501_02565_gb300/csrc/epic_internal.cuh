@@ -19,7 +19,7 @@ namespace epic {
 
 // Packed (distance, label) key of the geodesic relaxation.
 //   bit 63       : unreached flag
-//   bits 62..22  : D in fixed point, units of 2^-32 (D < 2^41 units = 512)
+//   bits 62..22  : D in fixed point, units of 2^-31 (D < 2^41 units = 1024)
 //   bits 21..0   : match index (label), 0x3FFFFF = none
 // Comparing keys as uint64 compares (D, L) lexicographically, which realises
 // "nearest match, ties to the smallest index" (Sec. 3.4), and a 64-bit access
@@ -36,8 +36,8 @@ constexpr pkey_t KEY_INF = 0x8000000000000000ull | LABEL_NONE;
 constexpr unsigned EMPTY32 = 0xFFFFFFFFu;
 constexpr pkey_t EMPTY64 = 0xFFFFFFFFFFFFFFFFull;
 constexpr int MAX_LABELS = (1 << LABEL_BITS) - 2;    // largest N
-constexpr float UNITS_PER_ONE = 4294967296.0f;        // 2^32
-constexpr float ONE_PER_UNIT = 2.3283064365386963e-10f;  // 2^-32
+constexpr float UNITS_PER_ONE = 2147483648.0f;        // 2^31
+constexpr float ONE_PER_UNIT = 4.6566128730773926e-10f;  // 2^-31
 
 __device__ __forceinline__ pkey_t make_key(unsigned long long d_units, unsigned label) {
     return (d_units << LABEL_BITS) | label;
@@ -52,25 +52,25 @@ __device__ __forceinline__ unsigned key_label(pkey_t k) { return (unsigned)k & L
 
 // Step cost of Eq. 3 between 8-neighbours p, q in fixed-point units:
 // |p-q| (C(p)+C(q))/2 = |p-q| (h(p)+h(q)) with half-costs h = C/2 held as
-// integers h = rint(C 2^31) (units of 2^-32; 0 <= C < 2).  An axis step is
+// integers h = rint(C 2^30) (units of 2^-31; 0 <= C < 2).  An axis step is
 // the exact sum of the two halves; a diagonal step multiplies that sum by
 // sqrt 2 in 2.30 fixed point, rounded to the nearest unit.  Both are
 // symmetric in p, q and every kernel forms the identical integer.
 constexpr float C_MAX = 2.0f;  // costs are edge strengths in [0, 2)
 constexpr unsigned long long SQRT2_Q30 = 1518500250ull;  // rint(sqrt(2) 2^30)
-__device__ __forceinline__ unsigned long long step_axis(unsigned hp, unsigned hq) {
-    return (unsigned long long)hp + hq;
+__device__ __forceinline__ unsigned step_axis(unsigned hp, unsigned hq) {
+    return hp + hq;   // < 2^32: half-costs are below 2^31
 }
 __device__ __forceinline__ unsigned long long step_diag(unsigned hp, unsigned hq) {
-    return (((unsigned long long)hp + hq) * SQRT2_Q30 + (1ull << 29)) >> 30;
+    return ((unsigned long long)(hp + hq) * SQRT2_Q30 + (1ull << 29)) >> 30;
 }
-// h = rint(C 2^31) for 0 <= C < C_MAX, else 0 and *bad set.
+// h = rint(C 2^30) for 0 <= C < C_MAX, else 0 and *bad set.
 __device__ __forceinline__ unsigned half_cost(float c, bool *bad) {
     if (!(c >= 0.f && c < C_MAX)) {
         *bad = true;
         return 0u;
     }
-    return __float2uint_rn(__fmul_rn(c, 2147483648.0f));
+    return __float2uint_rn(__fmul_rn(c, 1073741824.0f));
 }
 // Candidate key at p from neighbour key kq over a step of w units; an
 // unreached neighbour offers nothing (its flag bit makes the sum >= KEY_INF).

@@ -3,7 +3,7 @@
 //
 // Each pixel's packed key (D, L) is the minimum over all matches m and all
 // grid paths from p_m of (path cost, m), with path costs summed exactly in
-// fixed point (units of 2^-32) from the steps |p-q| (C(p)+C(q))/2.  Any
+// fixed point (units of 2^-31) from the steps |p-q| (C(p)+C(q))/2.  Any
 // order of relaxation steps that ends when no step improves any key reaches
 // these keys bit for bit: with exact sums every prefix of an optimal path is
 // optimal, so a state that no single step improves is the minimum.  The
