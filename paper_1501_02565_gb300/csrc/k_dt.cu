@@ -310,17 +310,36 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
                             unsigned *h, RunState *st, float *stage, Tma &tma) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, P.apron);
+    // seeds: the region lies within the 3x3 tiles around (tx, ty)
+    const int ctx0 = max(0, g.x0) / P.tile_w;
+    const int ctx1 = min(P.W - 1, g.x0 + g.RW - 1) / P.tile_w;
+    const int cty0 = max(0, g.y0) / P.tile_h;
+    const int cty1 = min(P.H - 1, g.y0 + g.RH - 1) / P.tile_h;
+    int nseeds = 0;
+    for (int cy = cty0; cy <= cty1; ++cy)
+        for (int cx = ctx0; cx <= ctx1; ++cx) {
+            const int t = cy * P.tiles_x + cx;
+            nseeds += P.tile_start[t + 1] - P.tile_start[t];
+        }
+    if (nseeds == 0) {
+        // no seed near the tile (the single-source runs of the exact variant
+        // have one in the whole image): it stays unreached until the
+        // verification passes bring distances in from its neighbours
+        if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = 0;
+        for (int i = threadIdx.x; i < P.tile_w * P.tile_h; i += blockDim.x) {
+            const int ly = i / P.tile_w, lx = i - ly * P.tile_w;
+            const int gx = gx0 + lx, gy = gy0 + ly;
+            if (gx < P.W && gy < P.H) P.keys[(size_t)gy * P.W + gx] = KEY_INF;
+        }
+        __syncthreads();
+        return;
+    }
     load_costs(P, g, h, st, true, stage, tma);
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         K[r * g.P + c] = KEY_INF;
     }
     __syncthreads();
-    // seeds: the region lies within the 3x3 tiles around (tx, ty)
-    const int ctx0 = max(0, g.x0) / P.tile_w;
-    const int ctx1 = min(P.W - 1, g.x0 + g.RW - 1) / P.tile_w;
-    const int cty0 = max(0, g.y0) / P.tile_h;
-    const int cty1 = min(P.H - 1, g.y0 + g.RH - 1) / P.tile_h;
     for (int cy = cty0; cy <= cty1; ++cy) {
         for (int cx = ctx0; cx <= ctx1; ++cx) {
             int t = cy * P.tiles_x + cx;

@@ -30,8 +30,8 @@
 // kept, and every batch of the finished list is sorted before the fit.  All
 // edges of all batch nodes are relaxed in one pass: lanes take (node, edge)
 // pairs found from a warp prefix sum of the batch nodes' degrees (CSR row
-// lengths).  A newly pushed node's row offsets are prefetched into L1 for
-// when it is settled; its lightest edge comes with the adjacency entry,
+// lengths).  A newly pushed node's lightest edge comes with the adjacency
+// entry,
 // since the step's bound is kept as a running minimum over the entries
 // pushed and kept (no separate pass over the frontier).  The step's smallest
 // key and bound are then two 32-bit warp reductions (redux.sync).
@@ -118,10 +118,6 @@ __device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.l
 
 __host__ __device__ __forceinline__ size_t knn_warp_bytes(int hs, int fs, int km) {
     return (size_t)fs * 16 + (size_t)hs * 8 + (size_t)km * 8 + (((size_t)km * 2 + 7) & ~(size_t)7);
-}
-
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 // Sort the settled list (node, distance) by key (distance, node) in place.
@@ -439,7 +435,6 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                         fw[p] = tw;
                         rk = nk < rk ? nk : rk;
                         rb = fminf(rb, tw);
-                        prefetch_l1(P.row + u);
                     }
                     fn += np;
                     overflow = __any_sync(0xffffffffu, overflow);
