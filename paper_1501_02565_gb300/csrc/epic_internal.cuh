@@ -204,9 +204,11 @@ struct LaunchCfg {
 // kernels' only parameter, so a captured launch sequence can be replayed for
 // any batch whose table has been uploaded to the same address).
 cudaError_t launch_prepare(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
+// chunked_passes: the verification passes hand out tiles in chunks (for
+// single-source runs, which need dozens of passes); see dt_kernel.
 cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                       int max_tile_w, int max_tile_h, int max_apron, bool fixed_grid,
-                      int *grid_used);
+                      int *grid_used, bool chunked_passes = false);
 cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
 cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
 cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,

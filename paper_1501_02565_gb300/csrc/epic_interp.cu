@@ -1140,7 +1140,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
             const BatchArgs *dev_a = reinterpret_cast<const BatchArgs *>(tdev);
             if ((e = cudaMemcpyAsync(tdev, thost.data(), t_bytes, cudaMemcpyHostToDevice, stream)) ||
                 (e = epic::launch_prepare(ba, dev_a, lc)) ||
-                (e = epic::launch_dt(ba, dev_a, lc, tw, th, ap, false, nullptr)) ||
+                (e = epic::launch_dt(ba, dev_a, lc, tw, th, ap, false, nullptr, true)) ||
                 (e = epic::launch_keys_to_dist(keys, (long long)n * P, D + m0 * P, stream)) ||
                 (e = cudaStreamSynchronize(stream)))
                 return cuda_fail(h, e, "exact-variant relaxation");

@@ -33,6 +33,7 @@ namespace epic {
 namespace {
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 2000000000ull;  // 2 s
+constexpr int PASS_CHUNK = 8;  // tiles per dispenser step in chunked verification passes
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
@@ -452,6 +453,15 @@ __device__ __forceinline__ bool neighbour_changed(const PairDev &P, int tx, int 
     return false;
 }
 
+// CHUNKED: how the verification passes hand out tiles.  false (the
+// interpolator's runs: a handful of passes, about half of the tiles
+// re-solved in the first): one tile at a time.  true (the single-source runs
+// of the exact variant: dozens of passes while distances cross the image
+// tile by tile, each re-solving a thin front): chunks of tiles whose
+// neighbour stamps are read in parallel.  The chunked loop keeps more state
+// and, at the four-CTA register budget, costs the interpolator's sweeps a
+// spill (2.21 -> 2.33 ms); the single-source runs go 3.1 -> 2.1 s per pair.
+template <bool CHUNKED>
 __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restrict__ ap) {
     const BatchArgs a = *ap;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -503,20 +513,79 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
         }
         unsigned *cnt = &st->changed[pass % 3];
         unsigned *disp = &st->work[pass % 3];
-        for (int t = next_tile(disp); t < a.total_tiles; t = next_tile(disp)) {
-            const PairDev &P = a.pairs[s_pair];
-            const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
-            __shared__ int s_check;
-            if (threadIdx.x == 0) s_check = neighbour_changed(P, tx, ty, pass);
-            __syncthreads();
-            if (s_check && border_dirty(P, tx, ty)) {
-                const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
-                pkey_t *K = reinterpret_cast<pkey_t *>(smem);
-                unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-                solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
-                if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+        if constexpr (!CHUNKED) {
+            for (int t = next_tile(disp); t < a.total_tiles; t = next_tile(disp)) {
+                const PairDev &P = a.pairs[s_pair];
+                const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
+                __shared__ int s_check;
+                if (threadIdx.x == 0) s_check = neighbour_changed(P, tx, ty, pass);
+                __syncthreads();
+                if (s_check && border_dirty(P, tx, ty)) {
+                    const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
+                    pkey_t *K = reinterpret_cast<pkey_t *>(smem);
+                    unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
+                    solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
+                    if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+                }
+                __syncthreads();
             }
-            __syncthreads();
+        } else {
+            // Tiles are handed out in chunks (one at a time in pass 0, which
+            // follows phase 1 and re-solves about half of them; PASS_CHUNK in
+            // later passes, which re-solve a few tiles in a thousand).  The first
+            // 8 x chunk threads read the chunk's neighbour stamps in parallel and
+            // flag the tiles with a neighbour written since the last pass; only
+            // those go on to the border test.  The loop state lives in shared
+            // memory, so nothing extra stays in registers across a re-solve.
+            __shared__ int s_t0, s_bits;
+            for (;;) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    s_t0 = (int)atomicAdd(disp, pass == 0 ? 1u : (unsigned)PASS_CHUNK);
+                    s_bits = 0;
+                }
+                __syncthreads();
+                if (s_t0 >= a.total_tiles) break;
+                if (threadIdx.x < 8 * (pass == 0 ? 1 : PASS_CHUNK)) {
+                    const int t = s_t0 + (threadIdx.x >> 3), k = threadIdx.x & 7;
+                    if (t < a.total_tiles) {
+                        const int pi = find_pair(a.tile_base, a.npairs, t);
+                        const PairDev &P = a.pairs[pi];
+                        const int lt = t - a.tile_base[pi];
+                        const int x = lt % P.tiles_x + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
+                        const int y = lt / P.tiles_x + (k < 3 ? -1 : k < 5 ? 0 : 1);
+                        if (x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
+                            __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass)
+                            atomicOr(&s_bits, 1 << (threadIdx.x >> 3));
+                    }
+                }
+                for (;;) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        const int b = s_bits;
+                        if (b) {
+                            const int t = s_t0 + __ffs(b) - 1;
+                            s_bits = b & (b - 1);
+                            s_tile = t;
+                            s_pair = find_pair(a.tile_base, a.npairs, t);
+                            s_local = t - a.tile_base[s_pair];
+                        } else {
+                            s_tile = -1;
+                        }
+                    }
+                    __syncthreads();
+                    if (s_tile < 0) break;
+                    const PairDev &P = a.pairs[s_pair];
+                    const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
+                    if (border_dirty(P, tx, ty)) {
+                        const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
+                        pkey_t *K = reinterpret_cast<pkey_t *>(smem);
+                        unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
+                        solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
+                        if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+                    }
+                }
+            }
         }
         if (!grid_sync(st, nblocks)) return;
         const unsigned dirty = ld_acquire(cnt);
@@ -567,13 +636,14 @@ size_t dt_smem_bytes(int tile_w, int tile_h, int apron) {
 
 cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                       int max_tile_w, int max_tile_h, int max_apron, bool fixed_grid,
-                      int *grid_used) {
+                      int *grid_used, bool chunked_passes) {
     size_t smem = dt_smem_bytes(max_tile_w, max_tile_h, max_apron);
+    void (*kernel)(const BatchArgs *) = chunked_passes ? dt_kernel<true> : dt_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(
-        dt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dt_kernel,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel,
                                                       DT_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -591,7 +661,7 @@ cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (grid_used) *grid_used = grid;
-    return cudaLaunchKernelEx(&cfg, dt_kernel, dev);
+    return cudaLaunchKernelEx(&cfg, kernel, dev);
 }
 
 }  // namespace epic

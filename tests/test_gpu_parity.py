@@ -79,6 +79,18 @@ def test_image_smaller_than_one_tile_and_single_match():
     np.testing.assert_allclose(g["flow"][..., 1], -0.75, atol=1e-6)
 
 
+def test_sparse_seeds_leave_most_tiles_empty():
+    # three matches in a 300 x 700 image: most relaxation tiles have no seed
+    # near them, skip their first solve and are reached only through the
+    # verification passes, which must carry the distances across many tiles
+    rng = np.random.default_rng(21)
+    C = rng.uniform(0.05, 0.6, (300, 700)).astype(np.float32)
+    M = np.array([[10, 12, 12.5, 11.0], [650, 280, 648.0, 281.5], [350, 150, 351.0, 149.0]],
+                 np.float32)
+    g, ref, rep = full_parity((C, M), K=3, a=0.02, tile_w=32, tile_h=32, apron=4)
+    _print("sparse", rep)
+
+
 def test_single_pixel_image():
     C = np.array([[1.0]], np.float32)
     M = np.array([[0, 0, 2, 3]], np.float32)
