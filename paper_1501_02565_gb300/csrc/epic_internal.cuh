@@ -209,7 +209,8 @@ cudaError_t launch_prepare(const BatchArgs &a, const BatchArgs *dev, const Launc
 cudaError_t launch_dt(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                       int max_tile_w, int max_tile_h, int max_apron, bool fixed_grid,
                       int *grid_used, bool chunked_passes = false);
-cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
+cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                         int max_tile_w, int max_tile_h);
 cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc);
 cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                            int max_K);

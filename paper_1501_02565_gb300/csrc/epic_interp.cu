@@ -617,7 +617,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
             // the compaction that rewrites the device tables for the second
             if ((r = epic::launch_prepare(a, dev_a, lc))) return r;
             if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
-            if ((r = epic::launch_edges(a, dev_a, lc))) return r;
+            if ((r = epic::launch_edges(a, dev_a, lc, dt_tw, dt_th))) return r;
             if ((r = epic::launch_scatter(a, dev_a, lc))) return r;
             if ((r = epic::launch_knn_fit(a, dev_a, lc, knn_K))) return r;
             if ((r = epic::launch_compact(a, dev_rw, lc))) return r;
@@ -630,7 +630,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
         mark(3);
         mark(4);
-        if ((r = epic::launch_edges(a, dev_a, lc))) return r;
+        if ((r = epic::launch_edges(a, dev_a, lc, dt_tw, dt_th))) return r;
         mark(5);
         mark(6);
         if ((r = epic::launch_scatter(a, dev_a, lc))) return r;

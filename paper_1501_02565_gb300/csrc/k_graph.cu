@@ -25,6 +25,8 @@
 //                lightest-edge weight.
 // offsets_kernel one CTA per pair: exclusive scan of the degrees into the
 //                CSR row offsets; the degree array becomes the fill cursor.
+//                The pair's edge count is half the degree total (no shared
+//                counter for the edges kernel to contend on).
 // scatter_kernel every occupied slot appends (n, w, w_min(n)) to row m and
 //                (m, w, w_min(m)) to row n of the CSR adjacency (order within
 //                a row unspecified; the K-NN search does not depend on it).
@@ -52,7 +54,6 @@ __device__ __forceinline__ void table_insert(const PairDev &P, pkey_t k,
             if (prev == EMPTY64) {       // a new edge
                 atomicAdd(P.deg + m, 1);
                 atomicAdd(P.deg + n, 1);
-                atomicAdd(P.info + 0, 1);
             }
             atomicMin(P.wmin + m, wbits);
             atomicMin(P.wmin + n, wbits);
@@ -106,6 +107,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
     __shared__ int s_tile, s_pair, s_local;
     __shared__ pkey_t sk[TILE_TABLE];
     __shared__ unsigned sw[TILE_TABLE];
+    // the tile's keys and half-costs plus the column on each side and the
+    // row below (every forward neighbour), staged with coalesced loads that
+    // are all in flight at once; cells outside the image hold KEY_INF
+    extern __shared__ __align__(16) unsigned char edge_smem[];
     // tiles are handed out from a counter: their cost varies with the number
     // of cell boundaries they hold
     for (;;) {
@@ -123,11 +128,26 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
             sk[i] = EMPTY64;
             sw[i] = 0xFFFFFFFFu;
         }
-        __syncthreads();
         const PairDev &P = a.pairs[s_pair];
         const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
         const int npx = P.tile_w * P.tile_h;
         const int W = P.W, H = P.H;
+        const int SC = P.tile_w + 2, SR = P.tile_h + 1;   // staged columns x0-1 .. x0+tw
+        pkey_t *skey = reinterpret_cast<pkey_t *>(edge_smem);
+        unsigned *sh = reinterpret_cast<unsigned *>(skey + SC * SR);
+        {
+            const int x0 = tx * P.tile_w - 1, y0 = ty * P.tile_h;
+            bool bad = false;
+            for (int j = threadIdx.x; j < SC * SR; j += blockDim.x) {
+                const int r = j / SC, c = j - r * SC;
+                const int gx = x0 + c, gy = y0 + r;
+                const bool in = gx >= 0 && gx < W && gy < H;
+                const size_t q = (size_t)gy * W + gx;
+                skey[j] = in ? __ldg(P.keys + q) : KEY_INF;
+                sh[j] = in ? half_cost(__ldg(P.C + q), &bad) : 0u;
+            }
+        }
+        __syncthreads();
         for (int i0 = 0; i0 < npx; i0 += blockDim.x) {  // warp-uniform trip count
             const int i = i0 + threadIdx.x;
             const int ly = i / P.tile_w, lx = i - ly * P.tile_w;
@@ -135,10 +155,9 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
             const bool act = i < npx && x < W && y < H;
             pkey_t kp = 0;
             unsigned hp = 0;
-            bool bad = false;
             if (act) {
-                kp = __ldg(P.keys + (size_t)y * W + x);
-                hp = half_cost(__ldg(P.C + (size_t)y * W + x), &bad);
+                kp = skey[ly * SC + lx + 1];
+                hp = sh[ly * SC + lx + 1];
             }
             // the four forward candidates of this pixel; a label pair seen in
             // an earlier direction is folded into that one (min weight), so
@@ -154,9 +173,9 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                 bool have = act && qx >= 0 && qx < W && qy < H;
                 pkey_t k = 0;
                 unsigned wb = 0;
+                const int sq = (ly + dy) * SC + lx + 1 + dx;   // staged cell of q
                 if (have) {
-                    const size_t q = (size_t)qy * W + qx;
-                    const pkey_t kq = __ldg(P.keys + q);
+                    const pkey_t kq = skey[sq];
                     const unsigned lp = key_label(kp), lq = key_label(kq);
                     have = lp != lq;
                     if (have && (lp >= (unsigned)P.N || lq >= (unsigned)P.N ||
@@ -167,7 +186,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                         have = false;
                     }
                     if (have) {
-                        const unsigned hq = half_cost(__ldg(P.C + q), &bad);
+                        const unsigned hq = sh[sq];
                         const unsigned long long stp = (dx != 0 && dy != 0)
                                                            ? step_diag(hp, hq)
                                                            : step_axis(hp, hq);
@@ -267,7 +286,10 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const BatchArgs *__restri
     for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {
         const PairDev &P = a.pairs[p];
         const int mx = block_offsets(P.deg, P.row, P.N);
-        if (threadIdx.x == 0) P.info[1] = mx;
+        if (threadIdx.x == 0) {
+            P.info[0] = P.row[P.N] / 2;   // edges: every edge is in two rows
+            P.info[1] = mx;
+        }
         __syncthreads();
     }
 }
@@ -319,17 +341,23 @@ __global__ void collect_kernel(const pkey_t *hkeys, const unsigned *hw, int cap_
 
 }  // namespace
 
-cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
+size_t edges_smem_bytes(int max_tile_w, int max_tile_h) {
+    return (size_t)(max_tile_w + 2) * (max_tile_h + 1) * (sizeof(pkey_t) + sizeof(unsigned));
+}
+
+cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                         int max_tile_w, int max_tile_h) {
     (void)a;
+    const size_t smem = edges_smem_bytes(max_tile_w, max_tile_h);
+    cudaError_t e = cudaFuncSetAttribute(edges_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     // one resident wave: every CTA keeps taking tiles until none are left
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_kernel,
-                                                                      EDGE_THREADS, 0);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-    }
-    edges_kernel<<<lc.num_sms * per_sm, EDGE_THREADS, 0, lc.stream>>>(dev);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, edges_kernel, EDGE_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    edges_kernel<<<lc.num_sms * per_sm, EDGE_THREADS, smem, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 
