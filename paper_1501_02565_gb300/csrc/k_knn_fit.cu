@@ -38,8 +38,9 @@
 //
 // The fit uses centred coordinates x~ = p_n - p_m and fits the flow
 // u = p' - p (the same least-squares problem as fitting p', Eq. 2, with
-// A = I + B): 12 weighted sums, warp-reduced, then the 3x3 normal equations
-// solved in float64 by cofactors, spread over the lanes of the warp.  The
+// A = I + B): 12 weighted sums, warp-reduced by a transposed reduction that
+// leaves each sum on two lanes, then the 3x3 normal equations solved in
+// float64 by cofactors, spread over the lanes of the warp.  The
 // sums stay in float32 registers but are carried as unevaluated pairs hi + lo: every product w * t is split exactly with an FMA
 // (TwoProduct) and every addition with TwoSum, so the accumulated sums keep
 // about twice float32's precision.  Kernel weights span many decades when a
@@ -99,19 +100,6 @@ __device__ __forceinline__ void acc_add(F2 &acc, float v) {
     two_sum(acc.hi, v, s, e);
     acc.hi = s;
     acc.lo = __fadd_rn(acc.lo, e);
-}
-
-__device__ __forceinline__ F2 warp_sum(F2 v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
-        const float ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
-        float s, e;
-        two_sum(v.hi, oh, s, e);
-        v.hi = s;
-        v.lo = __fadd_rn(v.lo, __fadd_rn(ol, e));
-    }
-    return v;
 }
 
 __device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.lo; }
@@ -510,16 +498,42 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
         // warp instruction costs the same however few lanes are active, so
         // each conversion, cofactor, quotient and coefficient goes to its own
         // lane and the operands travel by shuffles.
-        F2 mine = F2{0.f, 0.f};
+        // Transposed warp reduction of the 15 sums (a 16th is zero): at each
+        // of four levels a lane keeps half of its items, sends the other half
+        // to its partner and adds what it receives, so lanes 2i and 2i + 1
+        // end with the partial sums of item i over 16 lanes each; one last
+        // exchange completes them.  About 40 exchanges instead of 150.
+        F2 mine;
+        {
+            F2 r[16];
 #pragma unroll
-        for (int i = 0; i < 15; ++i) {
-            const F2 t = warp_sum(s[i]);
-            if (lane == i) mine = t;
+            for (int i = 0; i < 15; ++i) r[i] = s[i];
+            r[15] = F2{0.f, 0.f};
+#pragma unroll
+            for (int lvl = 0; lvl < 4; ++lvl) {
+                const int m = 16 >> lvl, half = 8 >> lvl;
+                const bool up = (lane & m) != 0;
+#pragma unroll
+                for (int j = 0; j < half; ++j) {
+                    const F2 keep = up ? r[j + half] : r[j];
+                    const F2 send = up ? r[j] : r[j + half];
+                    const float oh = __shfl_xor_sync(0xffffffffu, send.hi, m);
+                    const float ol = __shfl_xor_sync(0xffffffffu, send.lo, m);
+                    float sh, eh;
+                    two_sum(keep.hi, oh, sh, eh);
+                    r[j] = F2{sh, __fadd_rn(keep.lo, __fadd_rn(ol, eh))};
+                }
+            }
+            const float oh = __shfl_xor_sync(0xffffffffu, r[0].hi, 1);
+            const float ol = __shfl_xor_sync(0xffffffffu, r[0].lo, 1);
+            float sh, eh;
+            two_sum(r[0].hi, oh, sh, eh);
+            mine = F2{sh, __fadd_rn(r[0].lo, __fadd_rn(ol, eh))};
         }
-        // lane i < 15 holds sum i: M00 M01 M02 M11 M12 M22 (0-5), the
+        // lanes 2i and 2i + 1 hold sum i: M00 M01 M02 M11 M12 M22 (0-5), the
         // right-hand sides ru (6-8), rv (9-11), and the NW sums (12-14)
         const double Sl = to_d(mine);
-        auto S = [&](int src) { return __shfl_sync(0xffffffffu, Sl, src); };
+        auto S = [&](int i) { return __shfl_sync(0xffffffffu, Sl, 2 * i); };
         // cofactors of the symmetric matrix M, c00 c01 c02 c11 c12 c22 on
         // lanes 0-5, each c = x y - z w with the operands' sum indices packed
         // in nibbles
