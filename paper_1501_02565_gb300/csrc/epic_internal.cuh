@@ -99,6 +99,8 @@ struct PairDev {
     unsigned *hw;           // [hash_cap] float bits of the edge weight
     int *deg;               // [N] node degree in G, then the CSR fill cursor
     unsigned *wmin;         // [N] float bits of the lightest edge at each node
+    unsigned *wmin2;        // [N] float bits of the second-lightest edge (+inf if none)
+    int *wnear;             // [N] other end of the lightest edge (-1 if none)
     int *row;               // [N + 1] CSR row offsets into adj
     uint4 *adj;              // [2 * hash_cap] CSR rows: (neighbour, w bits, the
                              // neighbour's lightest-edge bits, 0)

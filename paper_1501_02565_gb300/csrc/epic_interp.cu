@@ -138,7 +138,8 @@ void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &r
 }
 
 struct Layout {
-    size_t keys, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, row, adj, models,
+    size_t keys, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, wmin2, wnear,
+        row, adj, models,
         fallback, knn_idx, knn_dist, knn_count, info, keep, pruned, kept_index, end;
 };
 
@@ -164,6 +165,8 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep, boo
     L.hw = take((size_t)P.hash_cap * sizeof(unsigned));
     L.deg = take((size_t)P.N * sizeof(int));
     L.wmin = take((size_t)P.N * sizeof(unsigned));
+    L.wmin2 = take((size_t)P.N * sizeof(unsigned));
+    L.wnear = take((size_t)P.N * sizeof(int));
     L.row = take(((size_t)P.N + 1) * sizeof(int));
     // CSR adjacency: at most one entry per direction of every table slot
     L.adj = take((size_t)P.hash_cap * 2 * sizeof(uint4));
@@ -488,6 +491,8 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         P[i].hw = reinterpret_cast<unsigned *>(b + L[i].hw);
         P[i].deg = reinterpret_cast<int *>(b + L[i].deg);
         P[i].wmin = reinterpret_cast<unsigned *>(b + L[i].wmin);
+        P[i].wmin2 = reinterpret_cast<unsigned *>(b + L[i].wmin2);
+        P[i].wnear = reinterpret_cast<int *>(b + L[i].wnear);
         P[i].row = reinterpret_cast<int *>(b + L[i].row);
         P[i].adj = reinterpret_cast<uint4 *>(b + L[i].adj);
         P[i].models = reinterpret_cast<float4 *>(b + L[i].models);
@@ -1246,10 +1251,10 @@ int epic_gradient_cost(const float *image, int frames, int H, int W, int channel
 
 int epic_interp_launches_per_run(epic_interp_t *h, int n) {
     (void)n;
-    // prepare, relaxation, edges, CSR offsets, scatter, K-NN + fit and its
-    // retry pass, write-out; pruning adds the first pass's seven and the
-    // compaction
-    return h && h->cfg.prune ? 16 : 8;
+    // prepare, relaxation, edges, CSR offsets, scatter, the two lightest
+    // edges per node, the per-entry bound edge, K-NN + fit and its retry
+    // pass, write-out; pruning adds the first pass's nine and the compaction
+    return h && h->cfg.prune ? 20 : 10;
 }
 
 const char *epic_interp_last_error(epic_interp_t *h) {

@@ -27,11 +27,14 @@
 //                CSR row offsets; the degree array becomes the fill cursor.
 //                The pair's edge count is half the degree total (no shared
 //                counter for the edges kernel to contend on).
-// scatter_kernel every occupied slot appends (n, w, w_min(n)) to row m and
-//                (m, w, w_min(m)) to row n of the CSR adjacency (order within
-//                a row unspecified; the K-NN search does not depend on it).
-//                Carrying the neighbour's lightest edge in the entry saves
-//                the search a dependent load per pushed node.
+// scatter_kernel every occupied slot appends (n, w) to row m and (m, w) to
+//                row n of the CSR adjacency (order within a row unspecified;
+//                the K-NN search does not depend on it).
+// rowmin_kernel, bound_edge_kernel
+//                per node the two lightest edges; then in every entry
+//                (m -> n) the lightest edge at n other than (n, m).  The
+//                K-NN search reads it with the entry (no dependent load)
+//                for its step bound.
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -311,8 +314,53 @@ __global__ void __launch_bounds__(256) scatter_kernel(const BatchArgs *__restric
             continue;
         }
         const unsigned wb = P.hw[s];
-        P.adj[atomicAdd(P.deg + m, 1)] = make_uint4(n, wb, P.wmin[n], 0u);
-        P.adj[atomicAdd(P.deg + n, 1)] = make_uint4(m, wb, P.wmin[m], 0u);
+        P.adj[atomicAdd(P.deg + m, 1)] = make_uint4(n, wb, 0u, 0u);
+        P.adj[atomicAdd(P.deg + n, 1)] = make_uint4(m, wb, 0u, 0u);
+    }
+}
+
+// Per node: the two lightest edge weights (the second is +inf below two
+// edges) and the other end of the lightest.
+__global__ void __launch_bounds__(256) rowmin_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
+    if (get_status(a.state) != 0) return;
+    for (int gm = blockIdx.x * blockDim.x + threadIdx.x; gm < a.total_matches;
+         gm += gridDim.x * blockDim.x) {
+        const int pi = find_pair(a.match_base, a.npairs, gm);
+        const PairDev &P = a.pairs[pi];
+        const int m = gm - a.match_base[pi];
+        unsigned w1 = 0x7F800000u, w2 = 0x7F800000u;
+        int n1 = -1;
+        for (int j = P.row[m], e = P.row[m + 1]; j < e; ++j) {
+            const uint4 ed = P.adj[j];
+            if (ed.y < w1) {
+                w2 = w1;
+                w1 = ed.y;
+                n1 = (int)ed.x;
+            } else if (ed.y < w2) {
+                w2 = ed.y;
+            }
+        }
+        P.wmin2[m] = w2;
+        P.wnear[m] = n1;
+    }
+}
+
+// Per CSR entry (m -> n): the lightest edge at n other than the one back to
+// m, which is what a K-NN search that reaches n from m adds to n's distance
+// for its step bound (see k_knn_fit.cu).
+__global__ void __launch_bounds__(256) bound_edge_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
+    if (get_status(a.state) != 0) return;
+    for (int gm = blockIdx.x * blockDim.x + threadIdx.x; gm < a.total_matches;
+         gm += gridDim.x * blockDim.x) {
+        const int pi = find_pair(a.match_base, a.npairs, gm);
+        const PairDev &P = a.pairs[pi];
+        const int m = gm - a.match_base[pi];
+        for (int j = P.row[m], e = P.row[m + 1]; j < e; ++j) {
+            const int n = (int)P.adj[j].x;
+            P.adj[j].z = P.wnear[n] == m ? P.wmin2[n] : P.wmin[n];
+        }
     }
 }
 
@@ -367,6 +415,10 @@ cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const Launc
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     scatter_kernel<<<lc.num_sms * 4, 256, 0, lc.stream>>>(dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    rowmin_kernel<<<lc.num_sms * 4, 256, 0, lc.stream>>>(dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bound_edge_kernel<<<lc.num_sms * 4, 256, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

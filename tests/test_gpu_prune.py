@@ -156,5 +156,5 @@ def test_pruned_batch_and_graph_replay_match_single_runs():
         eng.sync()
         for i in range(3):
             assert np.array_equal(dev[i][4].cpu().numpy(), singles[i]), (rep, i)
-        assert eng.launches_per_run(3) == 16
+        assert eng.launches_per_run(3) == 20
     eng.close()
