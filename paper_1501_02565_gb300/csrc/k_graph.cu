@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(const BatchArgs *__restric
             continue;
         }
         const unsigned wb = P.hw[s];
-        P.adj[atomicAdd(P.deg + m, 1)] = make_uint4(n, wb, 0u, 0u);
-        P.adj[atomicAdd(P.deg + n, 1)] = make_uint4(m, wb, 0u, 0u);
+        P.adj[atomicAdd(P.deg + m, 1)] = make_uint4(n, wb, 0u, m);
+        P.adj[atomicAdd(P.deg + n, 1)] = make_uint4(m, wb, 0u, n);
     }
 }
 
@@ -348,19 +348,21 @@ __global__ void __launch_bounds__(256) rowmin_kernel(const BatchArgs *__restrict
 
 // Per CSR entry (m -> n): the lightest edge at n other than the one back to
 // m, which is what a K-NN search that reaches n from m adds to n's distance
-// for its step bound (see k_knn_fit.cu).
+// for its step bound (see k_knn_fit.cu).  A thread per entry slot of the
+// pairs' adjacency arrays (2 x hash_cap each, the used ones first); the
+// entry carries its row node m.
 __global__ void __launch_bounds__(256) bound_edge_kernel(const BatchArgs *__restrict__ ap) {
     const BatchArgs a = *ap;
     if (get_status(a.state) != 0) return;
-    for (int gm = blockIdx.x * blockDim.x + threadIdx.x; gm < a.total_matches;
-         gm += gridDim.x * blockDim.x) {
-        const int pi = find_pair(a.match_base, a.npairs, gm);
+    for (long long gs = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+         gs < 2LL * a.total_hash; gs += (long long)gridDim.x * blockDim.x) {
+        const int pi = find_pair(a.hash_base, a.npairs, (int)(gs >> 1));
         const PairDev &P = a.pairs[pi];
-        const int m = gm - a.match_base[pi];
-        for (int j = P.row[m], e = P.row[m + 1]; j < e; ++j) {
-            const int n = (int)P.adj[j].x;
-            P.adj[j].z = P.wnear[n] == m ? P.wmin2[n] : P.wmin[n];
-        }
+        const int j = (int)(gs - 2LL * a.hash_base[pi]);
+        if (j >= P.row[P.N]) continue;
+        const uint4 ed = P.adj[j];
+        const int n = (int)ed.x, m = (int)ed.w;
+        P.adj[j].z = P.wnear[n] == m ? P.wmin2[n] : P.wmin[n];
     }
 }
 
