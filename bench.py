@@ -23,7 +23,8 @@ Prints one JSON line (rank 0).  Keys beyond the common ones:
   pruned        the batched path with the NW consistency pruning of Sec. 4.1
                 (two passes per run)
   exact         the exact per-pixel variant of Sec. 5.2 (geodesic and
-                Euclidean) on one pair, against the one-pair path
+                Euclidean) on one pair, against the one-pair path: times,
+                and the endpoint errors of both against the ground truth
   gradient_cost the image-gradient cost map (Table 2) of the step's frames
                 (synthetic region images), one launch, vs the HBM peak
   refine        the variational refinement (Sec. 4) of one pair's
@@ -527,15 +528,25 @@ def run_ours(args, rank, world, local_rank):
             xeng.set_tile_rules(tile_rules)
         exact = {"pair": f"{p0.W}x{p0.H}, N={p0.N}, K={p0.K}"}
         C0, M0 = items[0][0], items[0][1]
+        flows = {}
         for metric in ("geodesic", "euclidean"):
             xeng.exact(C0, M0, p0.K, p0.a, metric=metric)      # warm-up, allocation
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            xeng.exact(C0, M0, p0.K, p0.a, metric=metric)
+            flows[metric] = xeng.exact(C0, M0, p0.K, p0.a, metric=metric)
             torch.cuda.synchronize()
             exact[f"{metric}_ms"] = 1e3 * (time.perf_counter() - t0)
         exact["approx_ms"] = float(np.median(lat))
         exact["geodesic_over_approx"] = exact["geodesic_ms"] / exact["approx_ms"]
+        # accuracy (Table 2 compares the approximation with the exact method):
+        # average endpoint error against the ground-truth flow, and the mean
+        # distance between the approximate and the exact geodesic flows
+        gt = torch.from_numpy(p0.gt_flow).to(dev)
+        approx = items[0][4]
+        exact["aee_approx"] = float((approx - gt).norm(dim=2).mean())
+        exact["aee_exact_geodesic"] = float((flows["geodesic"] - gt).norm(dim=2).mean())
+        exact["aee_exact_euclidean"] = float((flows["euclidean"] - gt).norm(dim=2).mean())
+        exact["mean_approx_to_exact_px"] = float((approx - flows["geodesic"]).norm(dim=2).mean())
         xeng.close()
 
     # ---- served: continuous batching vs one request at a time ------------

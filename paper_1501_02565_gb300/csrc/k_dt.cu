@@ -436,23 +436,6 @@ __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
     __syncthreads();
 }
 
-// Was any of the eight neighbours of tile (tx, ty) written in pass
-// `since` or later?  (Stamps of other tiles change during the launch, so
-// they are read through L2.)
-__device__ __forceinline__ bool neighbour_changed(const PairDev &P, int tx, int ty,
-                                                  int since) {
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int y = ty + dy;
-        if (y < 0 || y >= P.tiles_y) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int x = tx + dx;
-            if ((dx == 0 && dy == 0) || x < 0 || x >= P.tiles_x) continue;
-            if (__ldcg(P.tile_stamp + y * P.tiles_x + x) >= since) return true;
-        }
-    }
-    return false;
-}
-
 // CHUNKED: how the verification passes hand out tiles.  false (the
 // interpolator's runs: a handful of passes, about half of the tiles
 // re-solved in the first): one tile at a time.  true (the single-source runs
@@ -517,10 +500,16 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
             for (int t = next_tile(disp); t < a.total_tiles; t = next_tile(disp)) {
                 const PairDev &P = a.pairs[s_pair];
                 const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
-                __shared__ int s_check;
-                if (threadIdx.x == 0) s_check = neighbour_changed(P, tx, ty, pass);
-                __syncthreads();
-                if (s_check && border_dirty(P, tx, ty)) {
+                // threads 0-7 read the eight neighbour stamps at once
+                bool nb = false;
+                if (threadIdx.x < 8) {
+                    const int k = threadIdx.x;
+                    const int x = tx + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
+                    const int y = ty + (k < 3 ? -1 : k < 5 ? 0 : 1);
+                    nb = x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
+                         __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass;
+                }
+                if (__syncthreads_or(nb) && border_dirty(P, tx, ty)) {
                     const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                     pkey_t *K = reinterpret_cast<pkey_t *>(smem);
                     unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
