@@ -253,7 +253,13 @@ int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages,
  * degenerate fit falls back to NW as in the main path).  The flow at p is
  * the model's value at p.  metric 0: the geodesic distance D_G of Eq. 3,
  * computed by one single-source relaxation per match (the paper's "exact"
- * geodesic row); metric 1: the Euclidean distance between pixel centres and
+ * geodesic row).  Each relaxation is capped where its match cannot be among
+ * a pixel's K nearest: an approximate run on the same handle (its K-NN
+ * lists; it replaces the handle's last-run state) bounds every match's K-th
+ * nearest distance, and a relaxation seeded with those bounds gives a
+ * 1-Lipschitz upper bound of every pixel's K-th nearest distance; distances
+ * beyond it are not needed and not computed.  metric 1: the Euclidean
+ * distance between pixel centres and
  * match pixels (the paper's "Euclidean" row).  Device pointers; cost_map,
  * matches and flow_out as for epic_interp_run; knn_idx_out [H*W*K] int32 and
  * knn_dist_out [H*W*K] float32 receive every pixel's list in key order (both

@@ -91,6 +91,11 @@ struct PairDev {
     int hash_cap;           // power of two
     int flow_vec_ok;        // flow pointer is 16-byte aligned
     pkey_t *keys;            // [H*W] packed (D, L)
+    // exact variant only (null elsewhere): a distance offset per seed (units),
+    // and a key map whose distances cap the keys written back (a pixel whose
+    // distance exceeds its cap is left unreached)
+    const unsigned long long *seed_init;   // [N]
+    const pkey_t *cap;                     // [H*W]
     int *tile_start;        // [tiles+1] seed bins (prefix offsets)
     int *tile_fill;         // [tiles] scatter cursors
     int *tile_seeds;        // [N] match indices grouped by tile
@@ -233,6 +238,8 @@ struct ExactArgs {
     int weight_squared, estimator;
 };
 size_t exact_smem_bytes(int K);
+cudaError_t launch_cap_seed(const float *knn_dist, const int *knn_count, int N, int K, int ld,
+                            unsigned long long *init, cudaStream_t stream);
 cudaError_t launch_keys_to_dist(const pkey_t *keys, long long n, float *D, cudaStream_t stream);
 cudaError_t launch_exact_fit(const ExactArgs &x, cudaStream_t stream);
 

@@ -72,6 +72,9 @@ struct epic_interp {
     size_t ex_cap = 0;
     // scratch of the variational refinement
     void *rf_buf = nullptr;
+    // set by the exact variant around its internal approximate run: keep the
+    // K-NN lists, plain launches, no pruning
+    bool force_keep = false;
     size_t rf_cap = 0;
     // stage timing: NSTAGE+1 events per timed run, reused across enablements
     std::vector<epic_tile_rule_t> rules;  // relaxation tile by frame size
@@ -453,7 +456,12 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     if (!h) return EPIC_ERR_INVALID;
     if (!descs || n < 1) return fail(h, EPIC_ERR_INVALID, "empty batch");
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    const epic_config_t &c = h->cfg;
+    epic_config_t c = h->cfg;
+    if (h->force_keep) {
+        c.keep_intermediates = 1;
+        c.use_graphs = 0;
+        c.prune = 0;
+    }
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     for (int i = 0; i < n; ++i) {
@@ -1063,12 +1071,18 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
         const size_t pd_bytes = align_up(sizeof(PairDev) * Cm, 256);
         const size_t pre_stride = align_up(sizeof(int) * (Cm + 1), 256);
         const size_t t_bytes = args_bytes + pd_bytes + 5 * pre_stride;
-        const size_t need = d_bytes + k_bytes + s_bytes + t_bytes;
+        // cap map: its keys, the bins and per-match scratch of its
+        // relaxation, the seed offsets, and the approximate run's flow
+        const size_t v_ints = (size_t)(T + 1) + T + N + T + N + N + 4;
+        const size_t c_bytes = align_up((size_t)P * sizeof(pkey_t), 256) +
+                               align_up(v_ints * sizeof(int), 256) +
+                               align_up((size_t)N * sizeof(unsigned long long), 256) +
+                               align_up((size_t)P * 2 * sizeof(float), 256);
+        const size_t need = d_bytes + k_bytes + s_bytes + align_up(t_bytes, 256) + c_bytes;
         if (need > h->ex_cap) {
             if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
                 return cuda_fail(h, e, "cudaStreamSynchronize");
             if (h->ex_buf) cudaFree(h->ex_buf);
-    if (h->rf_buf) cudaFree(h->rf_buf);
             h->ex_buf = nullptr;
             h->ex_cap = 0;
             e = cudaMalloc(&h->ex_buf, need);
@@ -1083,8 +1097,88 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
         pkey_t *keys = reinterpret_cast<pkey_t *>(b + d_bytes);
         int *small = reinterpret_cast<int *>(b + d_bytes + k_bytes);
         char *tdev = b + d_bytes + k_bytes + s_bytes;
+        char *cb = tdev + align_up(t_bytes, 256);
+        pkey_t *vkeys = reinterpret_cast<pkey_t *>(cb);
+        int *vs = reinterpret_cast<int *>(cb + align_up((size_t)P * sizeof(pkey_t), 256));
+        unsigned long long *vinit = reinterpret_cast<unsigned long long *>(
+            reinterpret_cast<char *>(vs) + align_up(v_ints * sizeof(int), 256));
+        float *aflow = reinterpret_cast<float *>(
+            reinterpret_cast<char *>(vinit) + align_up((size_t)N * sizeof(unsigned long long), 256));
         std::vector<char> thost(t_bytes);
         epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
+
+        // Cap map.  An approximate run keeps its K-NN lists: each match's
+        // K-th nearest graph distance bounds its K-th nearest geodesic
+        // distance.  A multi-source relaxation seeded with those bounds gives
+        // V(p) = min over m of (d(p, m) + bound(m)) >= the K-th nearest
+        // distance of p, and V is 1-Lipschitz in the relaxation's metric.
+        // The single-source runs below write back only distances within V,
+        // so each stops spreading about where its seed stops mattering.
+        {
+            h->force_keep = true;
+            epic_pair_desc_t ad{cost_map, matches, H, W, N, K, a, aflow};
+            const int rca = epic_interp_run_batch(h, &ad, 1, stream_);
+            h->force_keep = false;
+            if (rca) return rca;
+            const PairDev &Pa = h->pairs[0];
+            if ((e = epic::launch_cap_seed(Pa.knn_dist, Pa.knn_count, N, K, Pa.K, vinit, stream)))
+                return cuda_fail(h, e, "exact-variant cap seeds");
+            PairDev v{};
+            v.C = cost_map;
+            v.matches = reinterpret_cast<const float4 *>(matches);
+            v.H = H;
+            v.W = W;
+            v.N = N;
+            v.K = 1;
+            v.a = 1.f;
+            v.tile_w = tw;
+            v.tile_h = th;
+            v.apron = ap;
+            v.sweep = sw;
+            v.tiles_x = tx;
+            v.tiles_y = ty;
+            v.keys = vkeys;
+            v.tile_start = vs;
+            v.tile_fill = vs + T + 1;
+            v.tile_seeds = vs + 2 * T + 1;
+            v.tile_stamp = vs + 2 * T + 1 + N;
+            v.deg = vs + 3 * T + 1 + N;
+            v.wmin = reinterpret_cast<unsigned *>(vs + 3 * T + 1 + 2 * N);
+            v.info = vs + 3 * T + 1 + 3 * N;
+            v.seed_init = vinit;
+            std::vector<int> pre(5 * 2, 0);
+            pre[1] = T;          // tiles
+            pre[2 + 1] = N;      // matches
+            BatchArgs vb{};
+            vb.pairs = reinterpret_cast<const PairDev *>(tdev + args_bytes);
+            vb.npairs = 1;
+            auto vpre = [&](int k) {
+                return reinterpret_cast<const int *>(tdev + args_bytes + pd_bytes + k * pre_stride);
+            };
+            vb.tile_base = vpre(0);
+            vb.match_base = vpre(1);
+            vb.chunk_base = vpre(2);
+            vb.hash_base = vpre(3);
+            vb.clear_base = vpre(4);
+            vb.total_tiles = T;
+            vb.total_matches = N;
+            vb.max_degree = 1;
+            vb.max_passes = c.max_passes;
+            vb.weight_squared = 1;
+            vb.fallback_eps = c.fallback_eps;
+            vb.state = h->state;
+            memcpy(thost.data(), &vb, sizeof vb);
+            memcpy(thost.data() + args_bytes, &v, sizeof(PairDev));
+            for (int k = 0; k < 5; ++k)
+                memcpy(thost.data() + args_bytes + pd_bytes + k * pre_stride, pre.data() + k * 2,
+                       sizeof(int) * 2);
+            const BatchArgs *dev_v = reinterpret_cast<const BatchArgs *>(tdev);
+            if ((e = cudaMemcpyAsync(tdev, thost.data(), t_bytes, cudaMemcpyHostToDevice, stream)) ||
+                (e = epic::launch_prepare(vb, dev_v, lc)) ||
+                (e = epic::launch_dt(vb, dev_v, lc, tw, th, ap, false, nullptr)) ||
+                (e = cudaStreamSynchronize(stream)))
+                return cuda_fail(h, e, "exact-variant cap map");
+        }
         for (long long m0 = 0; m0 < N; m0 += Cm) {
             const int n = (int)std::min(Cm, (long long)N - m0);
             std::vector<PairDev> pd(n);
@@ -1113,6 +1207,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
                 q.deg = sp + 3 * T + 2;
                 q.wmin = reinterpret_cast<unsigned *>(sp + 3 * T + 3);
                 q.info = sp + 3 * T + 4;
+                q.cap = vkeys;
             }
             std::vector<int> pre(5 * (n + 1), 0);
             for (int j = 0; j <= n; ++j) {

@@ -306,6 +306,15 @@ __device__ __forceinline__ float *stage_area(unsigned char *smem) {
     return reinterpret_cast<float *>(((uintptr_t)smem + 127) & ~(uintptr_t)127);
 }
 
+// A key as written back: with a cap map (the exact variant's single-source
+// runs), a distance beyond the pixel's cap is left unreached, so the run
+// stops spreading where it can no longer matter.  The cap is 1-Lipschitz in
+// the same fixed-point metric, so every pixel on a shortest path to a
+// pixel within its cap is within its own cap: capped runs are exact there.
+__device__ __forceinline__ pkey_t capped(const PairDev &P, size_t p, pkey_t k) {
+    return P.cap && key_dunits(k) > key_dunits(P.cap[p]) ? KEY_INF : k;
+}
+
 // Phase 1: solve tile (tx, ty) on its region from its seeds alone.
 __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
                             unsigned *h, RunState *st, float *stage, Tma &tma) {
@@ -351,7 +360,8 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
                 int px = (int)floorf(mt.x + 0.5f) - g.x0;
                 int py = (int)floorf(mt.y + 0.5f) - g.y0;
                 if (px >= 0 && px < g.RW && py >= 0 && py < g.RH)
-                    atomicMin(&K[py * g.P + px], make_key(0ull, (unsigned)m));
+                    atomicMin(&K[py * g.P + px],
+                              make_key(P.seed_init ? P.seed_init[m] : 0ull, (unsigned)m));
             }
         }
     }
@@ -364,7 +374,8 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
         int ly = i / P.tile_w, lx = i - ly * P.tile_w;
         int gx = gx0 + lx, gy = gy0 + ly;
         if (gx < P.W && gy < P.H)
-            P.keys[(size_t)gy * P.W + gx] = K[(ly + off) * g.P + lx + off];
+            P.keys[(size_t)gy * P.W + gx] =
+                capped(P, (size_t)gy * P.W + gx, K[(ly + off) * g.P + lx + off]);
     }
     __syncthreads();
 }
@@ -405,7 +416,9 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
             const pkey_t kq = ld_key(P.keys + q);
             const unsigned hq = half_cost(__ldg(P.C + q), &bad);
             const unsigned long long w = (dx != 0 && dy != 0) ? step_diag(hp, hq) : step_axis(hp, hq);
-            dirty |= step_key(kq, w) < kp;
+            // an improvement beyond the pixel's cap would be written back
+            // unreached, so it does not make the tile dirty
+            dirty |= capped(P, p, step_key(kq, w)) < kp;
         }
     }
     return __syncthreads_or(dirty) != 0;
@@ -429,7 +442,8 @@ __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
             int ly = i / P.tile_w, lx = i - ly * P.tile_w;
             int gx = gx0 + lx, gy = gy0 + ly;
             if (gx < P.W && gy < P.H)
-                P.keys[(size_t)gy * P.W + gx] = K[(ly + 1) * g.P + lx + 1];
+                P.keys[(size_t)gy * P.W + gx] =
+                    capped(P, (size_t)gy * P.W + gx, K[(ly + 1) * g.P + lx + 1]);
         }
     }
     if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = pass;

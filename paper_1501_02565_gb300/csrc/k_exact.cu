@@ -26,6 +26,26 @@ __global__ void keys_to_dist_kernel(const pkey_t *keys, long long n, float *D) {
         D[i] = key_dist(keys[i]);
 }
 
+// Seed offsets of the cap map (in key units): an upper bound of each
+// match's K-th nearest graph distance, from the K-NN lists of an
+// approximate run.  A graph distance is the cost of a real path (each edge
+// weight is one), but summed in float from float-rounded weights, hence the
+// relative and absolute margins.  Fewer than K neighbours: no bound.
+__global__ void cap_seed_kernel(const float *knn_dist, const int *knn_count, int N, int K,
+                                int ld, unsigned long long *init) {
+    constexpr unsigned long long UNBOUNDED = 1ull << 40;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
+        unsigned long long u = UNBOUNDED;
+        if (knn_count[m] >= K) {
+            const double d = (double)knn_dist[(size_t)m * ld + K - 1];
+            if (d >= 0.0 && d < 256.0)
+                u = min((unsigned long long)ceil(d * 2147483648.0 * (1.0 + 1.0 / 65536.0)) + 256ull,
+                        UNBOUNDED);
+        }
+        init[m] = u;
+    }
+}
+
 __device__ __forceinline__ unsigned long long dist_key(float d, unsigned m) {
     return ((unsigned long long)__float_as_uint(d) << 32) | m;
 }
@@ -126,6 +146,13 @@ __global__ void __launch_bounds__(EXACT_THREADS) exact_fit_kernel(ExactArgs x) {
 }  // namespace
 
 size_t exact_smem_bytes(int K) { return (size_t)K * EXACT_THREADS * sizeof(unsigned long long); }
+
+cudaError_t launch_cap_seed(const float *knn_dist, const int *knn_count, int N, int K, int ld,
+                            unsigned long long *init, cudaStream_t stream) {
+    const int blocks = (N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024;
+    cap_seed_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, stream>>>(knn_dist, knn_count, N, K, ld, init);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_keys_to_dist(const pkey_t *keys, long long n, float *D, cudaStream_t stream) {
     long long blocks = (n + 255) / 256;

@@ -79,3 +79,26 @@ def test_refines_the_interpolated_flow_of_a_pair():
     print(f"\n[refine config1] max |gpu - oracle| = {err:.3g} px; AEE to ground truth "
           f"{aee(flow0):.3f} interpolated -> {aee(g):.3f} refined")
     assert err <= REF_TOL
+
+
+def test_refine_before_and_after_the_exact_variant_on_one_handle():
+    # the refinement's scratch and the exact variant's scratch belong to the
+    # same handle; growing the exact variant's leaves the refinement intact
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    p = synth.config_pair(1, 0)
+    I1 = torch.from_numpy(synth.region_image(p, seed=1)).cuda()
+    I2 = torch.from_numpy(synth.second_frame(synth.region_image(p, seed=1), p.gt_flow)).cuda()
+    eng = EpicInterp(0)
+    C, M = torch.from_numpy(p.C).cuda(), torch.from_numpy(p.matches).cuda()
+    f0 = eng.run(C, M, p.K, p.a)
+    eng.sync()
+    f1 = f0.clone()
+    eng.refine(I1, I2, f1)
+    eng.sync()
+    eng.exact(C, M, p.K, p.a)
+    f2 = f0.clone()
+    eng.refine(I1, I2, f2)
+    eng.sync()
+    assert torch.equal(f1, f2)
+    eng.close()
