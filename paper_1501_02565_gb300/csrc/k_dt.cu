@@ -334,8 +334,10 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
     if (nseeds == 0) {
         // no seed near the tile (the single-source runs of the exact variant
         // have one in the whole image): it stays unreached until the
-        // verification passes bring distances in from its neighbours
-        if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = 0;
+        // verification passes bring distances in from its neighbours.  Its
+        // stamp says "never written", so its neighbours (unreached too, if
+        // also seedless) skip the border test in the first pass
+        if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = -1;
         for (int i = threadIdx.x; i < P.tile_w * P.tile_h; i += blockDim.x) {
             const int ly = i / P.tile_w, lx = i - ly * P.tile_w;
             const int gx = gx0 + lx, gy = gy0 + ly;
@@ -533,23 +535,23 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                 __syncthreads();
             }
         } else {
-            // Tiles are handed out in chunks (one at a time in pass 0, which
-            // follows phase 1 and re-solves about half of them; PASS_CHUNK in
-            // later passes, which re-solve a few tiles in a thousand).  The first
-            // 8 x chunk threads read the chunk's neighbour stamps in parallel and
-            // flag the tiles with a neighbour written since the last pass; only
-            // those go on to the border test.  The loop state lives in shared
-            // memory, so nothing extra stays in registers across a re-solve.
+            // Tiles are handed out PASS_CHUNK at a time: a single-source run
+            // re-solves only a thin front in every pass.  The first
+            // 8 x PASS_CHUNK threads read the chunk's neighbour stamps in
+            // parallel and flag the tiles with a neighbour written since the
+            // last pass; only those go on to the border test.  The loop state
+            // lives in shared memory, so nothing extra stays in registers
+            // across a re-solve.
             __shared__ int s_t0, s_bits;
             for (;;) {
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    s_t0 = (int)atomicAdd(disp, pass == 0 ? 1u : (unsigned)PASS_CHUNK);
+                    s_t0 = (int)atomicAdd(disp, (unsigned)PASS_CHUNK);
                     s_bits = 0;
                 }
                 __syncthreads();
                 if (s_t0 >= a.total_tiles) break;
-                if (threadIdx.x < 8 * (pass == 0 ? 1 : PASS_CHUNK)) {
+                if (threadIdx.x < 8 * PASS_CHUNK) {
                     const int t = s_t0 + (threadIdx.x >> 3), k = threadIdx.x & 7;
                     if (t < a.total_tiles) {
                         const int pi = find_pair(a.tile_base, a.npairs, t);

@@ -115,3 +115,11 @@ def test_nw_estimator_and_single_neighbour():
     flow, idx, _ = _gpu_exact(C, M, 1, 1.0, "geodesic")
     np.testing.assert_allclose(flow.reshape(-1, 2), M[idx[:, 0], 2:] - M[idx[:, 0], :2],
                                rtol=1e-6, atol=1e-6)
+
+
+def test_config1_pair_small_k_caps_most_runs():
+    # K = 4 of 500 matches: the cap of every single-source relaxation closes
+    # in a few cells from its seed; lists, distances and flow must still be
+    # the oracle's
+    p = synth.config_pair(1, 0)
+    _check(p.C, p.matches, 4, p.a, "geodesic")
