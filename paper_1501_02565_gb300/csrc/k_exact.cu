@@ -71,6 +71,9 @@ __global__ void __launch_bounds__(EXACT_THREADS) exact_fit_kernel(ExactArgs x) {
             const float dy = __fsub_rn((float)py, floorf(q.y + 0.5f));
             d = __fsqrt_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
         }
+        // an unreached distance (beyond the single-source run's cap) cannot
+        // be among the K nearest: every pixel has K matches within its cap
+        if (!(d < __int_as_float(0x7f800000))) continue;
         const unsigned long long key = dist_key(d, (unsigned)m);
         int j;
         if (cnt < K) {
