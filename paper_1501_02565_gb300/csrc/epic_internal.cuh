@@ -162,6 +162,7 @@ struct BatchArgs {
     const int *hash_base;    // [npairs+1] prefix of hash slots
     const int *clear_base;   // [npairs+1] prefix of clear chunks
     int total_tiles, total_matches, total_chunks, total_hash, total_clear;
+    int uniform_tiles;       // > 0: every pair has this many tiles (pair = tile / uniform_tiles)
     int max_degree;
     int knn_hs, knn_fs, knn_kmax;  // main-pass K-NN table sizes per warp, and K bound
     int *knn_retry_list;   // [KNN_RETRY_CAP] global match indices to search again

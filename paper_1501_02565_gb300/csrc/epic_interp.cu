@@ -1227,6 +1227,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
             ba.clear_base = pre_dev(4);
             ba.total_tiles = n * T;
             ba.total_matches = n;
+            ba.uniform_tiles = T;
             ba.max_degree = 1;
             ba.max_passes = c.max_passes;
             ba.weight_squared = 1;

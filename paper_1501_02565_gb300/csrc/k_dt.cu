@@ -315,6 +315,12 @@ __device__ __forceinline__ pkey_t capped(const PairDev &P, size_t p, pkey_t k) {
     return P.cap && key_dunits(k) > key_dunits(P.cap[p]) ? KEY_INF : k;
 }
 
+// The pair a flat tile index belongs to (a division when all pairs have the
+// same tile count, as the exact variant's single-source pseudo-pairs do).
+__device__ __forceinline__ int tile_pair(const BatchArgs &a, int t) {
+    return a.uniform_tiles > 0 ? t / a.uniform_tiles : find_pair(a.tile_base, a.npairs, t);
+}
+
 // Phase 1: solve tile (tx, ty) on its region from its seeds alone.
 __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
                             unsigned *h, RunState *st, float *stage, Tma &tma) {
@@ -483,7 +489,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
             const int t = (int)atomicAdd(dispenser, 1u);
             s_tile = t;
             if (t < a.total_tiles) {
-                s_pair = find_pair(a.tile_base, a.npairs, t);
+                s_pair = tile_pair(a, t);
                 s_local = t - a.tile_base[s_pair];
             }
         }
@@ -554,7 +560,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                 if (threadIdx.x < 8 * PASS_CHUNK) {
                     const int t = s_t0 + (threadIdx.x >> 3), k = threadIdx.x & 7;
                     if (t < a.total_tiles) {
-                        const int pi = find_pair(a.tile_base, a.npairs, t);
+                        const int pi = tile_pair(a, t);
                         const PairDev &P = a.pairs[pi];
                         const int lt = t - a.tile_base[pi];
                         const int x = lt % P.tiles_x + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
@@ -572,7 +578,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                             const int t = s_t0 + __ffs(b) - 1;
                             s_bits = b & (b - 1);
                             s_tile = t;
-                            s_pair = find_pair(a.tile_base, a.npairs, t);
+                            s_pair = tile_pair(a, t);
                             s_local = t - a.tile_base[s_pair];
                         } else {
                             s_tile = -1;

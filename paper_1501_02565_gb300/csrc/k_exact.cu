@@ -20,6 +20,8 @@ namespace epic {
 
 namespace {
 
+constexpr int EXACT_GROUP = 8;   // candidate distances loaded per group
+
 __global__ void keys_to_dist_kernel(const pkey_t *keys, long long n, float *D) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -61,35 +63,50 @@ __global__ void __launch_bounds__(EXACT_THREADS) exact_fit_kernel(ExactArgs x) {
     const int py = (int)(p / x.W), px = (int)(p - (long long)py * x.W);
     const int K = x.K;
     int cnt = 0;
-    for (int m = 0; m < x.N; ++m) {
-        float d;
-        if (x.D) {
-            d = __ldcs(x.D + (long long)m * P + p);
-        } else {
-            const float4 q = __ldg(x.matches + m);
-            const float dx = __fsub_rn((float)px, floorf(q.x + 0.5f));
-            const float dy = __fsub_rn((float)py, floorf(q.y + 0.5f));
-            d = __fsqrt_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
+    // candidates in groups of EXACT_GROUP: the group's distance loads are
+    // all issued before any is used, so that many are in flight per thread
+    for (int m0 = 0; m0 < x.N; m0 += EXACT_GROUP) {
+        float dg[EXACT_GROUP];
+#pragma unroll
+        for (int u = 0; u < EXACT_GROUP; ++u) {
+            const int m = m0 + u;
+            float d = __int_as_float(0x7f800000);
+            if (m < x.N) {
+                if (x.D) {
+                    d = __ldcs(x.D + (long long)m * P + p);
+                } else {
+                    const float4 q = __ldg(x.matches + m);
+                    const float dx = __fsub_rn((float)px, floorf(q.x + 0.5f));
+                    const float dy = __fsub_rn((float)py, floorf(q.y + 0.5f));
+                    d = __fsqrt_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
+                }
+            }
+            dg[u] = d;
         }
-        // an unreached distance (beyond the single-source run's cap) cannot
-        // be among the K nearest: every pixel has K matches within its cap
-        if (!(d < __int_as_float(0x7f800000))) continue;
-        const unsigned long long key = dist_key(d, (unsigned)m);
-        int j;
-        if (cnt < K) {
-            j = cnt - 1;
-            ++cnt;
-        } else if (key < list[(K - 1) * T + t]) {
-            j = K - 2;
-        } else {
-            continue;
+#pragma unroll
+        for (int u = 0; u < EXACT_GROUP; ++u) {
+            const float d = dg[u];
+            // an unreached distance (beyond the single-source run's cap, or
+            // past the last match) cannot be among the K nearest: every pixel
+            // has K matches within its cap
+            if (!(d < __int_as_float(0x7f800000))) continue;
+            const unsigned long long key = dist_key(d, (unsigned)(m0 + u));
+            int j;
+            if (cnt < K) {
+                j = cnt - 1;
+                ++cnt;
+            } else if (key < list[(K - 1) * T + t]) {
+                j = K - 2;
+            } else {
+                continue;
+            }
+            // insertion into the sorted list (ascending keys)
+            while (j >= 0 && list[j * T + t] > key) {
+                list[(j + 1) * T + t] = list[j * T + t];
+                --j;
+            }
+            list[(j + 1) * T + t] = key;
         }
-        // insertion into the sorted list (ascending keys)
-        while (j >= 0 && list[j * T + t] > key) {
-            list[(j + 1) * T + t] = list[j * T + t];
-            --j;
-        }
-        list[(j + 1) * T + t] = key;
     }
     // fit centred at the pixel: rows (x~, y~, 1), x~ = x_n - x_p
     double M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
