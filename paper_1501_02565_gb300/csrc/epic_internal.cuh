@@ -148,6 +148,7 @@ struct RunState {
     unsigned knn_overflow; // matches whose search outgrew the small tables
     unsigned knn_retry;    // dispenser of the retry pass over those matches
     unsigned edge_next;    // boundary-edge tile dispenser
+    unsigned wl_count[3];  // worklist lengths of the chunked relaxation passes (rotating)
     unsigned compact_done; // CTAs finished in the pruning compaction
     GridBarrier barrier;
 };
@@ -163,6 +164,8 @@ struct BatchArgs {
     const int *clear_base;   // [npairs+1] prefix of clear chunks
     int total_tiles, total_matches, total_chunks, total_hash, total_clear;
     int uniform_tiles;       // > 0: every pair has this many tiles (pair = tile / uniform_tiles)
+    int *wl;                 // chunked relaxation only: 3 worklists of total_tiles flat tile indices
+    int *wl_queued;          // [total_tiles] last pass + 1 a tile was queued for (0 = never)
     int max_degree;
     int knn_hs, knn_fs, knn_kmax;  // main-pass K-NN table sizes per warp, and K bound
     int *knn_retry_list;   // [KNN_RETRY_CAP] global match indices to search again

@@ -1078,7 +1078,9 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
                                align_up(v_ints * sizeof(int), 256) +
                                align_up((size_t)N * sizeof(unsigned long long), 256) +
                                align_up((size_t)P * 2 * sizeof(float), 256);
-        const size_t need = d_bytes + k_bytes + s_bytes + align_up(t_bytes, 256) + c_bytes;
+        // worklists of the chunked passes: three lists and the queued marks
+        const size_t w_bytes = align_up((size_t)4 * Cm * T * sizeof(int), 256);
+        const size_t need = d_bytes + k_bytes + s_bytes + align_up(t_bytes, 256) + c_bytes + w_bytes;
         if (need > h->ex_cap) {
             if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
                 return cuda_fail(h, e, "cudaStreamSynchronize");
@@ -1104,6 +1106,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
             reinterpret_cast<char *>(vs) + align_up(v_ints * sizeof(int), 256));
         float *aflow = reinterpret_cast<float *>(
             reinterpret_cast<char *>(vinit) + align_up((size_t)N * sizeof(unsigned long long), 256));
+        int *wl = reinterpret_cast<int *>(cb + c_bytes);   // [3][Cm * T], then [Cm * T] marks
         std::vector<char> thost(t_bytes);
         epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
 
@@ -1228,6 +1231,8 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
             ba.total_tiles = n * T;
             ba.total_matches = n;
             ba.uniform_tiles = T;
+            ba.wl = wl;
+            ba.wl_queued = wl + (size_t)3 * n * T;
             ba.max_degree = 1;
             ba.max_passes = c.max_passes;
             ba.weight_squared = 1;
@@ -1240,6 +1245,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
                        sizeof(int) * (n + 1));
             const BatchArgs *dev_a = reinterpret_cast<const BatchArgs *>(tdev);
             if ((e = cudaMemcpyAsync(tdev, thost.data(), t_bytes, cudaMemcpyHostToDevice, stream)) ||
+                (e = cudaMemsetAsync(ba.wl_queued, 0, sizeof(int) * (size_t)n * T, stream)) ||
                 (e = epic::launch_prepare(ba, dev_a, lc)) ||
                 (e = epic::launch_dt(ba, dev_a, lc, tw, th, ap, false, nullptr, true)) ||
                 (e = epic::launch_keys_to_dist(keys, (long long)n * P, D + m0 * P, stream)) ||

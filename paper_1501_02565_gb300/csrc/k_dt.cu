@@ -433,7 +433,8 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
 }
 
 // Phase 2 re-solve of tile (tx, ty) from the current keys (tile + ring).
-__device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
+// Returns whether any key of the region changed (the same in every thread).
+__device__ bool solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
                             unsigned *h, RunState *st, int pass, float *stage, Tma &tma) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, 0);
@@ -445,7 +446,8 @@ __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
         K[r * g.P + c] = in ? ld_key(P.keys + (size_t)gy * P.W + gx) : KEY_INF;
     }
     __syncthreads();
-    if (local_solve(K, h, g, st, P.sweep)) {
+    const bool changed = local_solve(K, h, g, st, P.sweep) != 0;
+    if (changed) {
         for (int i = threadIdx.x; i < P.tile_w * P.tile_h; i += blockDim.x) {
             int ly = i / P.tile_w, lx = i - ly * P.tile_w;
             int gx = gx0 + lx, gy = gy0 + ly;
@@ -456,6 +458,24 @@ __device__ void solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
     }
     if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = pass;
     __syncthreads();
+    return changed;
+}
+
+// Chunked passes: queue the eight neighbours of tile t (flat index; local
+// (tx, ty) in pair pi) for pass `next`, each at most once (threads 0-7).
+__device__ __forceinline__ void queue_neighbours(const BatchArgs &a, RunState *st, int pi,
+                                                 int tx, int ty, int next) {
+    if (threadIdx.x >= 8) return;
+    const PairDev &P = a.pairs[pi];
+    const int k = threadIdx.x;
+    const int x = tx + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
+    const int y = ty + (k < 3 ? -1 : k < 5 ? 0 : 1);
+    if (x < 0 || x >= P.tiles_x || y < 0 || y >= P.tiles_y) return;
+    const int nt = a.tile_base[pi] + y * P.tiles_x + x;
+    if (atomicMax(a.wl_queued + nt, next + 1) < next + 1) {
+        const unsigned q = atomicAdd(&st->wl_count[next % 3], 1u);
+        a.wl[(size_t)(next % 3) * a.total_tiles + q] = nt;
+    }
 }
 
 // CHUNKED: how the verification passes hand out tiles.  false (the
@@ -541,47 +561,79 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                 __syncthreads();
             }
         } else {
-            // Tiles are handed out PASS_CHUNK at a time: a single-source run
-            // re-solves only a thin front in every pass.  The first
+            // Pass 0 scans every tile, PASS_CHUNK at a time: the first
             // 8 x PASS_CHUNK threads read the chunk's neighbour stamps in
-            // parallel and flag the tiles with a neighbour written since the
-            // last pass; only those go on to the border test.  The loop state
+            // parallel and flag the tiles with a neighbour written since phase
+            // 1; only those go on to the border test.  A tile that changes
+            // queues its eight neighbours for the next pass, and every later
+            // pass works through that list alone (a single-source run
+            // re-solves a thin front, and scanning every tile in each of its
+            // dozen passes cost more than the re-solves).  The loop state
             // lives in shared memory, so nothing extra stays in registers
             // across a re-solve.
             __shared__ int s_t0, s_bits;
-            for (;;) {
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    s_t0 = (int)atomicAdd(disp, (unsigned)PASS_CHUNK);
-                    s_bits = 0;
-                }
-                __syncthreads();
-                if (s_t0 >= a.total_tiles) break;
-                if (threadIdx.x < 8 * PASS_CHUNK) {
-                    const int t = s_t0 + (threadIdx.x >> 3), k = threadIdx.x & 7;
-                    if (t < a.total_tiles) {
-                        const int pi = tile_pair(a, t);
-                        const PairDev &P = a.pairs[pi];
-                        const int lt = t - a.tile_base[pi];
-                        const int x = lt % P.tiles_x + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
-                        const int y = lt / P.tiles_x + (k < 3 ? -1 : k < 5 ? 0 : 1);
-                        if (x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
-                            __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass)
-                            atomicOr(&s_bits, 1 << (threadIdx.x >> 3));
-                    }
-                }
+            if (pass == 0) {
                 for (;;) {
                     __syncthreads();
                     if (threadIdx.x == 0) {
-                        const int b = s_bits;
-                        if (b) {
-                            const int t = s_t0 + __ffs(b) - 1;
-                            s_bits = b & (b - 1);
-                            s_tile = t;
-                            s_pair = tile_pair(a, t);
-                            s_local = t - a.tile_base[s_pair];
-                        } else {
-                            s_tile = -1;
+                        s_t0 = (int)atomicAdd(disp, (unsigned)PASS_CHUNK);
+                        s_bits = 0;
+                    }
+                    __syncthreads();
+                    if (s_t0 >= a.total_tiles) break;
+                    if (threadIdx.x < 8 * PASS_CHUNK) {
+                        const int t = s_t0 + (threadIdx.x >> 3), k = threadIdx.x & 7;
+                        if (t < a.total_tiles) {
+                            const int pi = tile_pair(a, t);
+                            const PairDev &P = a.pairs[pi];
+                            const int lt = t - a.tile_base[pi];
+                            const int x = lt % P.tiles_x + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
+                            const int y = lt / P.tiles_x + (k < 3 ? -1 : k < 5 ? 0 : 1);
+                            if (x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
+                                __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass)
+                                atomicOr(&s_bits, 1 << (threadIdx.x >> 3));
+                        }
+                    }
+                    for (;;) {
+                        __syncthreads();
+                        if (threadIdx.x == 0) {
+                            const int b = s_bits;
+                            if (b) {
+                                const int t = s_t0 + __ffs(b) - 1;
+                                s_bits = b & (b - 1);
+                                s_tile = t;
+                                s_pair = tile_pair(a, t);
+                                s_local = t - a.tile_base[s_pair];
+                            } else {
+                                s_tile = -1;
+                            }
+                        }
+                        __syncthreads();
+                        if (s_tile < 0) break;
+                        const PairDev &P = a.pairs[s_pair];
+                        const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
+                        if (border_dirty(P, tx, ty)) {
+                            const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
+                            pkey_t *K = reinterpret_cast<pkey_t *>(smem);
+                            unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
+                            if (solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma))
+                                queue_neighbours(a, st, s_pair, tx, ty, pass + 1);
+                            if (threadIdx.x == 0) atomicAdd(cnt, 1u);
+                        }
+                    }
+                }
+            } else {
+                // the list of this pass was complete before the last barrier
+                const unsigned n = ld_acquire(&st->wl_count[pass % 3]);
+                const int *list = a.wl + (size_t)(pass % 3) * a.total_tiles;
+                for (;;) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        const unsigned q = atomicAdd(disp, 1u);
+                        s_tile = q < n ? list[q] : -1;
+                        if (s_tile >= 0) {
+                            s_pair = tile_pair(a, s_tile);
+                            s_local = s_tile - a.tile_base[s_pair];
                         }
                     }
                     __syncthreads();
@@ -592,7 +644,8 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                         const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                         pkey_t *K = reinterpret_cast<pkey_t *>(smem);
                         unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-                        solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
+                        if (solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma))
+                            queue_neighbours(a, st, s_pair, tx, ty, pass + 1);
                         if (threadIdx.x == 0) atomicAdd(cnt, 1u);
                     }
                 }
@@ -605,6 +658,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->changed[(pass + 2) % 3] = 0;
             st->work[(pass + 2) % 3] = 0;
+            st->wl_count[(pass + 2) % 3] = 0;
         }
         if (dirty == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) st->passes = pass + 1;

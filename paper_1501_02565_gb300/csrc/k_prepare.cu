@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
         st->knn_overflow = 0;
         st->knn_retry = 0;
         st->edge_next = 0;
+        st->wl_count[0] = st->wl_count[1] = st->wl_count[2] = 0;
         st->barrier.count = 0;
         st->compact_done = 0;
     }
