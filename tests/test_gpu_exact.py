@@ -123,3 +123,23 @@ def test_config1_pair_small_k_caps_most_runs():
     # the oracle's
     p = synth.config_pair(1, 0)
     _check(p.C, p.matches, 4, p.a, "geodesic")
+
+
+def test_exact_on_a_pruning_handle():
+    # the exact variant's internal approximate run turns pruning off for its
+    # bounds; on a handle configured to prune it must still give the oracle's
+    # exact lists and flow
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    C, M = random_small_case(950, H=37, W=70, N=30, c_lo=0.01, c_hi=1.0)
+    eng = EpicInterp(0, prune=1)
+    Ct = torch.from_numpy(C).cuda()
+    Mt = torch.from_numpy(M).cuda()
+    flow_p, idx_p, dist_p = eng.exact(Ct, Mt, 8, 1.0, with_knn=True)
+    eng.close()
+    eng = EpicInterp(0)
+    flow, idx, dist = eng.exact(Ct, Mt, 8, 1.0, with_knn=True)
+    eng.close()
+    assert torch.equal(flow_p, flow)
+    assert torch.equal(idx_p, idx)
+    assert torch.equal(dist_p, dist)
