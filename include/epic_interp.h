@@ -235,7 +235,8 @@ int epic_interp_set_tile_rules(epic_interp_t *h, const epic_tile_rule_t *rules,
                                int n);
 
 /* Stage timing.  While enabled, every run records CUDA events on its
- * stream around its stages: 0 prepare, 1 relaxation, 2 edges, 3 scatter,
+ * stream around its stages: 0 prepare, 1 relaxation, 2 edges, 3 scatter (CSR
+ * offsets and rows, the lightest edges per node, the K-NN bound edges),
  * 4 K-NN + fit, 5 write-out, 6 pruning (the whole first pass and the
  * compaction; zero when prune = 0).  Enabling (again) clears the
  * accumulated times. */
