@@ -85,6 +85,41 @@ def test_approximate_distance_upper_bounds_geodesic(seed):
     np.testing.assert_allclose(Dtilde[Lf, np.arange(len(Lf))], Df, atol=0)
 
 
+def test_approximate_distance_is_exact_along_a_chain_of_cells():
+    # Eq. 4 on a one-row strip: the cells are consecutive intervals, G is the
+    # chain of neighbouring matches, and each edge weight is the geodesic
+    # between the two seeds.  For a pixel whose own seed lies between it and
+    # p_n, the shortest path passes through that seed, so D~ equals D_G
+    # exactly; for a pixel strictly between its seed and p_n it is longer.
+    rng = np.random.default_rng(31)
+    W = 48
+    C = rng.uniform(0.05, 2.0, (1, W)).astype(np.float32)
+    xs = np.array([2, 9, 17, 18, 26, 35, 44])
+    N = len(xs)
+    m = np.zeros((N, 4), np.float32)
+    m[:, 0] = xs
+    m[:, 2] = xs + 1.0
+    D, L = oracle.geodesic(C, m)
+    em, en, ew = oracle.graph(C, D, L, m)
+    pairs = sorted(zip(np.minimum(em, en).tolist(), np.maximum(em, en).tolist()))
+    assert pairs == [(i, i + 1) for i in range(N - 1)]
+    _, _, _, Dg = knn_by_scipy(N, em, en, ew, N)
+    Dexact = per_seed_distances(C, m)            # [N, W]
+    Lf, Df = L.ravel(), D.ravel()
+    Dtilde = Df[None, :] + Dg[Lf].T              # [N, W]
+    seed_x = xs[Lf]                              # x of each pixel's own seed
+    px = np.arange(W)
+    n_eq = n_gt = 0
+    for n in range(N):
+        through = (seed_x - px) * (xs[n] - seed_x) >= 0
+        np.testing.assert_allclose(Dtilde[n, through], Dexact[n, through], rtol=1e-12)
+        n_eq += through.sum()
+        beyond = ~through
+        assert (Dtilde[n, beyond] > Dexact[n, beyond] + 1e-3).all()
+        n_gt += beyond.sum()
+    assert n_eq > 0 and n_gt > 0
+
+
 def test_piecewise_property_same_knn_set_for_whole_cell():
     # Sec. 3.4 "Piecewise field": under D~, every pixel of a cell has the same
     # K nearest matches as the cell's match, and weights differ by a common
