@@ -70,11 +70,21 @@ typedef enum {
                                     (edge table, node degree, K-NN frontier) */
 } epic_status_t;
 
+/* Largest neighbourhood size K of the interpolator, after K is clamped to N
+ * (the paper uses K = 100).  A K-NN search keeps its node table (~3.84 K
+ * slots), frontier (~1.92 K entries) and settled list in the shared memory
+ * of one warp; a search that outgrows them is re-run with tables of 8192
+ * node slots, which stay larger than the first tables up to this K.  A run
+ * with a larger K returns EPIC_ERR_INVALID; a config max_K above it is
+ * treated as EPIC_MAX_K. */
+enum { EPIC_MAX_K = 2048 };
+
 typedef struct epic_interp epic_interp_t;
 
 typedef struct {
     int max_H, max_W;     /* largest frame the arena is first sized for */
-    int max_N, max_K;     /* largest match count / neighbourhood size */
+    int max_N, max_K;     /* largest match count / neighbourhood size
+                             (max_K at most EPIC_MAX_K) */
     int max_pairs;        /* largest batch the arena is first sized for */
     int max_passes;       /* cap on relaxation verification passes */
     int weight_squared;   /* 1: Eq. 2 rows scaled by k, i.e. minimise
@@ -139,7 +149,8 @@ void epic_config_default(epic_config_t *cfg);
 int epic_interp_create(epic_interp_t **h, int device, const epic_config_t *cfg);
 
 /* Interpolate one pair (Algorithm 1, LA form).  Device pointers; K is
- * clamped to N; requires H, W, N >= 1, K >= 1, a > 0.  Enqueues the whole
+ * clamped to N; requires H, W, N >= 1, 1 <= K and min(K, N) <= EPIC_MAX_K,
+ * a > 0.  Enqueues the whole
  * path on `stream` and returns without waiting. */
 int epic_interp_run(epic_interp_t *h, const float *cost_map,
                     const float *matches, int H, int W, int N, int K, float a,

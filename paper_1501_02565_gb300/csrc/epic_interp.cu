@@ -399,6 +399,7 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     if (!(c.fallback_eps > 0.f)) c.fallback_eps = 1e-10f;
     if (c.max_pairs <= 0) c.max_pairs = 1;
     if (c.prune_K <= 0) c.prune_K = 25;
+    c.max_K = std::min(c.max_K, (int)EPIC_MAX_K);
     if (c.sweep != 0 && c.sweep != 1) c.sweep = 0;
     if ((c.estimator != 0 && c.estimator != 1) || !(c.prune_threshold >= 0.f) ||
         !std::isfinite(c.prune_threshold)) {
@@ -485,6 +486,8 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         max_ap = std::max(max_ap, P[i].apron);
         max_K = std::max(max_K, knn_cap(P[i]));
     }
+    if (max_K > EPIC_MAX_K)
+        return fail(h, EPIC_ERR_INVALID, "K (clamped to N) above EPIC_MAX_K");
     int rc = ensure_arena(h, off);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
@@ -559,7 +562,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         cfg_th = std::max(cfg_th, r.tile_h);
         cfg_ap = std::max(cfg_ap, r.apron);
     }
-    const int cfg_K = std::max(c.max_K, c.prune ? c.prune_K : 1);
+    const int cfg_K = std::min((int)EPIC_MAX_K, std::max(c.max_K, c.prune ? c.prune_K : 1));
     const bool graph = c.use_graphs && stream != nullptr && !h->timing && max_K <= cfg_K &&
                        max_tw <= cfg_tw && max_th <= cfg_th && max_ap <= cfg_ap;
     const int knn_K = graph ? cfg_K : max_K;

@@ -21,6 +21,7 @@ EPIC_ERR_CUDA = 3
 EPIC_ERR_NOT_CONVERGED = 4
 EPIC_ERR_TIMEOUT = 5
 EPIC_ERR_CAPACITY = 6
+EPIC_MAX_K = 2048
 
 STATUS_NAMES = {
     0: "EPIC_OK", 1: "EPIC_ERR_INVALID", 2: "EPIC_ERR_OOM", 3: "EPIC_ERR_CUDA",

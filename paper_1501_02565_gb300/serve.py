@@ -29,7 +29,7 @@ import time
 
 import numpy as np
 
-from .native import EpicInterp
+from .native import EPIC_MAX_K, EpicInterp
 
 # bytes of library scratch per pixel and per match (keys, bins, edge table,
 # adjacency, models; see the arena layout in csrc/epic_interp.cu)
@@ -151,6 +151,8 @@ class Server:
             raise ValueError("a match's source pixel lies outside the frame")
         if req.K < 1 or not req.a > 0:
             raise ValueError("need K >= 1 and a > 0")
+        if min(req.K, m.shape[0]) > EPIC_MAX_K:
+            raise ValueError(f"K (clamped to N) must be at most {EPIC_MAX_K}")
 
     def submit(self, req: Request) -> Request:
         self.validate(req)

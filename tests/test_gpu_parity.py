@@ -91,6 +91,24 @@ def test_sparse_seeds_leave_most_tiles_empty():
     _print("sparse", rep)
 
 
+def test_largest_neighbourhood_size():
+    # K = EPIC_MAX_K: the K-NN tables of one warp take most of an SM's shared
+    # memory (one warp per CTA) and every search settles 2048 of 2400 nodes;
+    # one above the limit is refused before any launch
+    import torch
+    from paper_1501_02565_gb300.native import EPIC_MAX_K, EpicError, EpicInterp, EPIC_ERR_INVALID
+    C, M = random_small_case(950, H=150, W=200, N=2400, c_lo=0.01, c_hi=0.2)
+    g, ref, rep = full_parity((C, M), K=EPIC_MAX_K, a=0.1)
+    _print(f"K={EPIC_MAX_K}", rep)
+    assert (g["count"] == EPIC_MAX_K).all()
+    eng = EpicInterp(0)
+    with pytest.raises(EpicError) as e:
+        eng.run(torch.from_numpy(C).cuda(), torch.from_numpy(M).cuda(), EPIC_MAX_K + 1, 0.1)
+    assert e.value.code == EPIC_ERR_INVALID
+    eng.sync()
+    eng.close()
+
+
 def test_single_pixel_image():
     C = np.array([[1.0]], np.float32)
     M = np.array([[0, 0, 2, 3]], np.float32)
@@ -144,6 +162,44 @@ def test_full_size_workloads_full_parity(config, index):
     g, ref, rep = full_parity(p)
     _print(f"config{config}.{index} {p.W}x{p.H} N={p.N} K={p.K}", rep)
     assert rep["flow_excluded_px"] < 0.02 * p.P
+
+
+def test_timed_batch_configuration_matches_parity_checked_runs():
+    # the configuration of the throughput line: 32 Sintel-shaped pairs
+    # (1024x436, ~5000 matches, K = 100) in one batched run, with the tile
+    # rules the autotuner picks for them.  Repeated runs are bit-identical,
+    # every pair's flow equals its single-pair run bit for bit, and three
+    # pairs of the batch (first, middle, last) get the full element-by-element
+    # parity against the oracle.
+    import torch
+    from paper_1501_02565_gb300 import tune
+    from paper_1501_02565_gb300.native import EpicInterp
+    pairs = [synth.config_pair(2, i) for i in range(32)]
+    rules, _ = tune.autotune(pairs, device=0, reps=1)
+    eng = EpicInterp(0, max_pairs=len(pairs))
+    eng.set_tile_rules(rules)
+    items = [(torch.from_numpy(p.C).cuda(), torch.from_numpy(p.matches).cuda(), p.K, p.a,
+              torch.empty((p.H, p.W, 2), dtype=torch.float32, device="cuda")) for p in pairs]
+    eng.run_batch(items)
+    eng.sync()
+    batched = [it[4].cpu().numpy() for it in items]
+    for _ in range(2):
+        eng.run_batch(items)
+    eng.sync()
+    for it, fb in zip(items, batched):
+        assert np.array_equal(it[4].cpu().numpy(), fb)
+    eng.close()
+    single = EpicInterp(0)
+    for p, it, fb in zip(pairs, items, batched):
+        f = single.run(it[0], it[1], p.K, p.a)
+        single.sync()
+        assert np.array_equal(f.cpu().numpy(), fb)
+    single.close()
+    for s in (0, 16, 31):
+        g, ref, rep = full_parity(pairs[s])
+        _print(f"batch32 pair {s}", rep)
+        assert np.array_equal(g["flow"], batched[s])
+        assert rep["flow_excluded_px"] < 0.02 * pairs[s].P
 
 
 def test_graph_replay_matches_plain_launches():
