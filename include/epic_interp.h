@@ -237,6 +237,13 @@ int epic_interp_get_pruning(epic_interp_t *h, int pair, int *keep,
  * whole batch (waits for the stream). */
 int epic_interp_get_passes(epic_interp_t *h, int *passes);
 
+/* Number of matches of the last run whose K-NN search outgrew the per-warp
+ * tables of the main pass and was run again with large tables (the final
+ * interpolation pass when pruning; waits for the stream).  Diagnostic only:
+ * the results do not depend on it, and the retry list holds every match of
+ * the batch, so any number of retries succeeds. */
+int epic_interp_get_knn_retries(epic_interp_t *h, int *retries);
+
 /* Install relaxation tile rules (replacing any earlier ones; n = 0 clears
  * them).  A pair uses the first rule whose max_pixels >= H*W, else the
  * configured tile.  Tile sides must be in [8, 256], apron < min(side) and

@@ -168,7 +168,8 @@ struct BatchArgs {
     int *wl_queued;          // [total_tiles] last pass + 1 a tile was queued for (0 = never)
     int max_degree;
     int knn_hs, knn_fs, knn_kmax;  // main-pass K-NN table sizes per warp, and K bound
-    int *knn_retry_list;   // [KNN_RETRY_CAP] global match indices to search again
+    int *knn_retry_list;   // [knn_retry_cap] global match indices to search again
+    int knn_retry_cap;     // = total_matches: a match is queued at most once per pass
     int max_passes;
     int weight_squared;
     float fallback_eps;
@@ -201,7 +202,6 @@ constexpr int WRITEOUT_CHUNK = 1024;  // pixels per write-out work item
 constexpr int CLEAR_CHUNK = 4096;     // 8-byte words per clear work item
 constexpr int DT_THREADS = 256;
 constexpr int KNN_WARPS = 8;          // warps (= matches in flight) per CTA
-constexpr int KNN_RETRY_CAP = 4096;   // matches the large-table retry pass can take
 constexpr int EDGE_THREADS = 256;
 
 // Host-side launchers (one per kernel file).

@@ -421,8 +421,8 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     if (e != cudaSuccess) { delete h; return EPIC_ERR_CUDA; }
     h->num_sms = prop.multiProcessorCount;
     h->smem_optin = (int)prop.sharedMemPerBlockOptin;
-    // the run state, a scratch counter, then the K-NN retry list
-    e = cudaMalloc(&h->state, sizeof(RunState) + 64 + sizeof(int) * epic::KNN_RETRY_CAP);
+    // the run state, then a scratch counter
+    e = cudaMalloc(&h->state, sizeof(RunState) + 64);
     if (e != cudaSuccess) { delete h; return EPIC_ERR_OOM; }
     h->scratch_count = reinterpret_cast<int *>(reinterpret_cast<char *>(h->state) + sizeof(RunState) + 32);
     cudaMemset(h->state, 0, sizeof(RunState) + 64);
@@ -444,7 +444,9 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     d.a = 1.f;
     PairDev P = make_pair_desc(c, h->rules, d);
     size_t per = layout_pair(0, P, c.max_degree, c.keep_intermediates != 0, c.prune != 0).end;
-    int rc = ensure_arena(h, per * (size_t)c.max_pairs);
+    // pairs, then the K-NN retry list of the batch (one int per match)
+    int rc = ensure_arena(h, per * (size_t)c.max_pairs + 256 +
+                                 sizeof(int) * (size_t)d.N * (size_t)c.max_pairs);
     if (rc) { epic_interp_destroy(h); return rc; }
     rc = ensure_table(h, 4096);
     if (rc) { epic_interp_destroy(h); return rc; }
@@ -474,6 +476,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     std::vector<Layout> L(n);
     size_t off = 0;
     int max_tw = 8, max_th = 8, max_ap = 0, max_K = 1;
+    size_t total_N = 0;
     for (int i = 0; i < n; ++i) {
         P[i] = make_pair_desc(c, h->rules, descs[i]);
         if (P[i].apron + 1 > std::min(P[i].tile_w, P[i].tile_h) || P[i].apron > 64)
@@ -485,7 +488,12 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         max_th = std::max(max_th, P[i].tile_h);
         max_ap = std::max(max_ap, P[i].apron);
         max_K = std::max(max_K, knn_cap(P[i]));
+        total_N += (size_t)P[i].N;
     }
+    // the K-NN retry list: every match of the batch fits, since a match is
+    // queued at most once per pass
+    const size_t retry_off = align_up(off, 256);
+    off = retry_off + sizeof(int) * total_N;
     if (max_K > EPIC_MAX_K)
         return fail(h, EPIC_ERR_INVALID, "K (clamped to N) above EPIC_MAX_K");
     int rc = ensure_arena(h, off);
@@ -595,7 +603,8 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     a.max_degree = c.max_degree;
     epic::knn_table_sizes(knn_K, &a.knn_hs, &a.knn_fs);
     a.knn_kmax = knn_K;
-    a.knn_retry_list = reinterpret_cast<int *>(reinterpret_cast<char *>(h->state) + sizeof(RunState) + 64);
+    a.knn_retry_list = reinterpret_cast<int *>(h->arena + retry_off);
+    a.knn_retry_cap = (int)tm;
     a.max_passes = c.max_passes;
     a.weight_squared = c.weight_squared ? 1 : 0;
     a.fallback_eps = c.fallback_eps;
@@ -986,6 +995,14 @@ int epic_interp_get_passes(epic_interp_t *h, int *passes) {
     int rc = read_state(h);
     if (rc) return rc;
     *passes = h->state_host->passes;
+    return EPIC_OK;
+}
+
+int epic_interp_get_knn_retries(epic_interp_t *h, int *retries) {
+    if (!h || !retries) return EPIC_ERR_INVALID;
+    int rc = read_state(h);
+    if (rc) return rc;
+    *retries = (int)h->state_host->knn_overflow;
     return EPIC_OK;
 }
 

@@ -35,7 +35,7 @@ EXPORTED = (
     "epic_interp_run_batch_host", "epic_interp_submit_batch_host", "epic_interp_sync",
     "epic_interp_get_labels", "epic_interp_get_edge_count",
     "epic_interp_get_graph", "epic_interp_get_knn", "epic_interp_get_models",
-    "epic_interp_get_pruning", "epic_interp_get_passes",
+    "epic_interp_get_pruning", "epic_interp_get_passes", "epic_interp_get_knn_retries",
     "epic_interp_set_tile_rules",
     "epic_interp_enable_stage_timing",
     "epic_interp_get_stage_times", "epic_interp_launches_per_run",
@@ -140,6 +140,8 @@ def load(path: str | None = None):
     lib.epic_interp_get_pruning.restype = I
     lib.epic_interp_get_passes.argtypes = [P, pi]
     lib.epic_interp_get_passes.restype = I
+    lib.epic_interp_get_knn_retries.argtypes = [P, pi]
+    lib.epic_interp_get_knn_retries.restype = I
     lib.epic_interp_set_tile_rules.argtypes = [P, ctypes.POINTER(epic_tile_rule_t), I]
     lib.epic_interp_set_tile_rules.restype = I
     lib.epic_interp_enable_stage_timing.argtypes = [P, I]
@@ -411,6 +413,13 @@ class EpicInterp:
     def get_passes(self):
         n = ctypes.c_int()
         self._check(self.lib.epic_interp_get_passes(self.h, ctypes.byref(n)), "get_passes")
+        return n.value
+
+    def get_knn_retries(self):
+        """Matches of the last run whose K-NN search ran again with large tables."""
+        n = ctypes.c_int()
+        self._check(self.lib.epic_interp_get_knn_retries(self.h, ctypes.byref(n)),
+                    "get_knn_retries")
         return n.value
 
     STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout", "prune")

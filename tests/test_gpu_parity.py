@@ -70,6 +70,48 @@ def test_hub_graph_searches_outgrow_the_small_tables():
     _print("hub", rep)
 
 
+def _hub_grid(seed, H=1024, W=2048, unit=96, ring=80, R=40.0):
+    # a grid of hubs: each is a match ringed by 80 others at radius 40, with a
+    # cheap disk (C / 10) out to 0.8 R so that the hub's cell touches all 80
+    # ring cells.  A search that settles a hub pushes ~80 nodes at once
+    rng = np.random.default_rng(seed)
+    C = 0.5 + rng.uniform(-0.01, 0.01, size=(H, W))
+    ang = np.linspace(0.0, 2.0 * np.pi, ring, endpoint=False)
+    cxs = np.arange(unit // 2, W - unit // 2 + 1, unit)
+    cys = np.arange(unit // 2, H - unit // 2 + 1, unit)
+    ys, xs = np.mgrid[0:H, 0:W]
+    dx = np.min(np.abs(xs[..., None] - cxs), -1)
+    dy = np.min(np.abs(ys[..., None] - cys), -1)
+    C[dx * dx + dy * dy < (0.8 * R) ** 2] *= 0.1
+    pts = []
+    for cy in cys:
+        for cx in cxs:
+            pts.append((cx, cy))
+            pts += list(zip(np.round(cx + R * np.cos(ang)), np.round(cy + R * np.sin(ang))))
+    p = np.array(pts, np.float64)
+    M = np.stack([p[:, 0], p[:, 1], p[:, 0] + 1.5 + 0.003 * p[:, 1],
+                  p[:, 1] - 0.5 + 0.002 * p[:, 0]], 1).astype(np.float32)
+    return C.astype(np.float32), M
+
+
+def test_every_search_outgrowing_the_small_tables():
+    # 210 hubs on a 2048 x 1024 frame (17,010 matches, K = 30): the hubs have
+    # degree 80, above the 64 frontier entries of the main pass, and a ring
+    # match settles its hub after ~8 neighbours, so nearly every search is
+    # queued for the large-table pass.  The queue holds every match of the
+    # batch; the result must agree with the oracle.
+    from paper_1501_02565_gb300.native import EpicInterp
+    C, M = _hub_grid(5)
+    eng = EpicInterp(0, keep_intermediates=1, max_H=1024, max_W=2048, max_N=len(M), max_K=30)
+    g, ref, rep = full_parity((C, M), K=30, a=0.05, eng=eng)
+    retries = eng.get_knn_retries()
+    eng.close()
+    _print(f"hub grid N={len(M)} retries={retries}", rep)
+    deg = np.bincount(np.r_[g["em"], g["en"]], minlength=len(M))
+    assert (deg > 64).sum() >= 200
+    assert retries > 4096
+
+
 def test_image_smaller_than_one_tile_and_single_match():
     C = np.full((5, 7), 0.3, np.float32)
     M = np.array([[3, 2, 5.5, 1.25]], np.float32)
