@@ -168,8 +168,8 @@ struct BatchArgs {
     int *wl_queued;          // [total_tiles] last pass + 1 a tile was queued for (0 = never)
     int max_degree;
     int knn_hs, knn_fs, knn_kmax;  // main-pass K-NN table sizes per warp, and K bound
-    int *knn_retry_list;   // [knn_retry_cap] global match indices to search again
-    int knn_retry_cap;     // = total_matches: a match is queued at most once per pass
+    int *knn_retry_list;   // global match indices to search again; holds every match of
+                           // the batch (a match is queued at most once per pass)
     int max_passes;
     int weight_squared;
     float fallback_eps;

@@ -604,7 +604,6 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     epic::knn_table_sizes(knn_K, &a.knn_hs, &a.knn_fs);
     a.knn_kmax = knn_K;
     a.knn_retry_list = reinterpret_cast<int *>(h->arena + retry_off);
-    a.knn_retry_cap = (int)tm;
     a.max_passes = c.max_passes;
     a.weight_squared = c.weight_squared ? 1 : 0;
     a.fallback_eps = c.fallback_eps;

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
     for (;;) {
         int gm = 0;
         if (RETRY) {
-            const unsigned nq = min(*(volatile unsigned *)&st->knn_overflow, (unsigned)a.knn_retry_cap);
+            const unsigned nq = min(*(volatile unsigned *)&st->knn_overflow, (unsigned)a.total_matches);
             unsigned q = 0;
             if (lane == 0) q = atomicAdd(&st->knn_retry, 1u);
             q = __shfl_sync(0xffffffffu, q, 0);
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                 // queued for the pass with large tables
                 if (lane == 0) {
                     const unsigned q = atomicAdd(&st->knn_overflow, 1u);
-                    if (q < (unsigned)a.knn_retry_cap)
+                    if (q < (unsigned)a.total_matches)
                         a.knn_retry_list[q] = gm;
                     else
                         set_status(st, EPIC_ERR_CAPACITY);
