@@ -149,9 +149,9 @@ void epic_config_default(epic_config_t *cfg);
 int epic_interp_create(epic_interp_t **h, int device, const epic_config_t *cfg);
 
 /* Interpolate one pair (Algorithm 1, LA form).  Device pointers; K is
- * clamped to N; requires H, W, N >= 1, 1 <= K and min(K, N) <= EPIC_MAX_K,
- * a > 0.  Enqueues the whole
- * path on `stream` and returns without waiting. */
+ * clamped to N; requires H, W, N >= 1, K >= 1, min(K, N) <= EPIC_MAX_K and
+ * a > 0 (else EPIC_ERR_INVALID, nothing enqueued).  Enqueues the whole path
+ * on `stream` and returns without waiting. */
 int epic_interp_run(epic_interp_t *h, const float *cost_map,
                     const float *matches, int H, int W, int N, int K, float a,
                     float *flow_out, void *stream);
