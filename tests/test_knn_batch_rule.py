@@ -16,7 +16,9 @@ import pytest
 import oracle
 
 
-def batched_knn(adj, src, K, lane_cut=32):
+def batched_knn(adj, src, K, lane_cut=32, steps=None):
+    """First K settled (distance, node) pairs under the batch rule; appends
+    the number of steps taken to `steps` if given."""
     def w_x(v, parent):
         return min((w for x, w in adj[v] if x != parent), default=np.inf)
 
@@ -24,13 +26,16 @@ def batched_knn(adj, src, K, lane_cut=32):
     settled = set()
     front = {src: (0.0, w_x(src, None))}      # node -> (t, t + w_x)
     out = []
+    k = 0
     while len(out) < K and front:
+        k += 1
         kmin = min((tv, v) for v, (tv, _) in front.items())
         bound = min(b for _, b in front.values())
         batch = sorted((tv, v) for v, (tv, _) in front.items() if tv < bound or (tv, v) == kmin)
         if len(out) + len(batch) >= K:
             if len(batch) <= lane_cut:
-                return out + batch[:K - len(out)]
+                out += batch[:K - len(out)]
+                break
             batch = [kmin]
         for _, v in batch:
             settled.add(v)
@@ -42,6 +47,8 @@ def batched_knn(adj, src, K, lane_cut=32):
                 if u not in settled and (u not in t or nd < t[u]):
                     t[u] = nd
                     front[u] = (nd, nd + w_x(u, v))
+    if steps is not None:
+        steps.append(k)
     return out
 
 
@@ -100,26 +107,6 @@ def test_batches_settle_several_nodes_per_step():
                     adj[b].append((a, w))
     K = 100
     steps = []
-    for s in rng.choice(n * n, 20, replace=False):
-        out, k = [], 0
-        # count steps with the same rule
-        t, settled = {int(s): 0.0}, set()
-        front = {int(s): (0.0, min(w for _, w in adj[int(s)]))}
-        while len(out) < K:
-            k += 1
-            kmin = min((tv, v) for v, (tv, _) in front.items())
-            bound = min(b for _, b in front.values())
-            batch = [(tv, v) for v, (tv, _) in front.items() if tv < bound or (tv, v) == kmin]
-            for _, v in batch:
-                settled.add(v)
-                del front[v]
-            out += batch
-            for tv, v in batch:
-                for u, w in adj[v]:
-                    nd = tv + w
-                    if u not in settled and (u not in t or nd < t[u]):
-                        t[u] = nd
-                        front[u] = (nd, nd + min((ww for x, ww in adj[u] if x != v),
-                                                 default=np.inf))
-        steps.append(k)
+    for src in rng.choice(n * n, 20, replace=False):
+        assert len(batched_knn(adj, int(src), K, steps=steps)) == K
     assert np.mean(steps) < K / 3
