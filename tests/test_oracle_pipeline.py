@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import knn_by_scipy, per_seed_distances, random_small_case
+from helpers import knn_by_scipy, load_golden, per_seed_distances, random_small_case
 
 
 def test_global_affine_flow_recovered_everywhere():
@@ -144,3 +144,22 @@ def test_piecewise_property_same_knn_set_for_whole_cell():
         flow = ref[:2] + np.array([[ref[2], ref[3]], [ref[4], ref[5]]]) @ (
             np.array([x, y], float) - m[l, :2])
         np.testing.assert_allclose(r["flow"][y, x], flow, rtol=1e-7, atol=1e-7)
+
+
+@pytest.mark.parametrize("K", [3, 2])
+def test_hand_derived_strip_through_every_stage(K):
+    # tests/golden/pipeline_strip.txt: labels, distances, graph, K-NN lists
+    # (with an index tie), the NW fallback of a degenerate fit and the
+    # dense flow, all worked out by hand
+    g = load_golden("pipeline_strip.txt")
+    a = float(g["a"][0])
+    r = oracle.interp(g["C"], g["matches"], K, a)
+    np.testing.assert_allclose(r["D"], g["D"], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(r["L"], g["L"])
+    edges = sorted(zip(np.minimum(r["em"], r["en"]), np.maximum(r["em"], r["en"]), r["ew"]))
+    np.testing.assert_allclose(np.array(edges, float).ravel(), g["edges"], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(r["idx"][:, :K].ravel(), g[f"K{K}_idx"])
+    np.testing.assert_allclose(r["dist"][:, :K].ravel(), g[f"K{K}_dist"], rtol=0, atol=1e-12)
+    assert r["fallback"].all()
+    per_match = np.stack([g[f"K{K}_flow_u"], g[f"K{K}_flow_v"]], -1)
+    np.testing.assert_allclose(r["flow"][0], per_match[g["L"][0]], rtol=0, atol=1e-12)
