@@ -51,6 +51,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -149,7 +150,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: $EPIC_CLOCKS_DIR if set (to keep them), else the temp dir
+        out_dir = os.environ.get("EPIC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"epic_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
