@@ -163,3 +163,19 @@ def test_hand_derived_strip_through_every_stage(K):
     assert r["fallback"].all()
     per_match = np.stack([g[f"K{K}_flow_u"], g[f"K{K}_flow_v"]], -1)
     np.testing.assert_allclose(r["flow"][0], per_match[g["L"][0]], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("a", [0.05, 0.5, 1.0])
+def test_hand_derived_affine_triangle(a):
+    # tests/golden/affine_triangle.txt: three correspondences fix one affine
+    # map, which the LA fit must return for every match and every pixel
+    g = load_golden("affine_triangle.txt")
+    r = oracle.interp(g["C"], g["matches"], 3, a)
+    assert not r["fallback"].any()
+    model = r["model"]                           # (c_u, c_v, b11, b12, b21, b22)
+    np.testing.assert_allclose(model[:, :2].ravel(), g["c"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(model[:, 2:], np.tile(g["B"], (3, 1)), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["flow"][..., 0], np.repeat(g["flow_u_by_row"][:, None], 5, 1),
+                               rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["flow"][..., 1], np.repeat(g["flow_v_by_col"][None, :], 5, 0),
+                               rtol=0, atol=1e-12)
