@@ -368,9 +368,15 @@ int epic_interp_launches_per_run(epic_interp_t *h, int n);
  *     are limited to 524288 pixels, 32768 matches and 16384 relaxation tiles
  *     of 64 x 32 pixels.  Larger inputs return EPIC_ERR_CAPACITY without
  *     doing any work.
- *   - Runs on the current device.  The first call on each device looks up
- *     the array's device address (cudaGetSymbolAddress); make that first
- *     call before any stream capture.
+ *   - Runs on the current device.  Every call looks up the array's device
+ *     address in the current CUDA context (cudaGetSymbolAddress, a host-side
+ *     query), so a context reset between calls is harmless.  The first call
+ *     in a context may load the library's device code; make that first call
+ *     before any stream capture.
+ *   - The small argument blocks (one pair descriptor, its prefix sums, the
+ *     launch arguments) are copied into the array by cudaMemcpyAsync from
+ *     the call's own stack; a copy from pageable host memory has read its
+ *     source by the time cudaMemcpyAsync returns.
  *   - Every call shares the array: calls that overlap on the GPU race.  Each
  *     call clears its run state, waits for its own work on `stream` and
  *     returns the device status (EPIC_OK, or e.g. EPIC_ERR_INVALID for a

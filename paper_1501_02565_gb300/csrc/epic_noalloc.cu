@@ -10,14 +10,15 @@
 // the call allocates nothing; the caller provides only inputs and outputs.
 //
 // The array is part of the library image: every GPU that loads the library
-// holds it (about 5 MB) until the process exits.  Its address is looked up
-// once per device with cudaGetSymbolAddress, by the first call made on that
-// device.  All calls share the array, so calls that overlap on the GPU (from
-// several host threads or streams) race; each call clears what must start at
-// zero and waits for its own work before returning.
+// holds it (about 5 MB) until the process exits.  Its device address belongs
+// to the CUDA context that loaded the library's device code, so every call
+// looks it up again (cudaGetSymbolAddress, a host-side query) in the context
+// current at the call: an address kept from an earlier call would be stale
+// after cudaDeviceReset or in another context on the same device.  All
+// calls share the array, so calls that overlap on the GPU (from several
+// host threads or streams) race; each call clears what must start at zero
+// and waits for its own work before returning.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "epic_internal.cuh"
 
@@ -29,7 +30,6 @@ constexpr int NA_MAX_PIXELS = 1 << 19;   // e.g. 1024 x 512
 constexpr int NA_MAX_MATCHES = 1 << 15;
 constexpr int NA_MAX_TILES = 1 << 14;
 constexpr int NA_TILE_W = 64, NA_TILE_H = 32, NA_APRON = 4;
-constexpr int NA_MAX_DEVICES = 64;
 
 // byte offsets inside the scratch array (each 256-byte aligned)
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -49,23 +49,13 @@ constexpr size_t NA_SCRATCH_BYTES = align256(OFF_ARGS + sizeof(epic::BatchArgs))
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
 
-std::mutex g_setup_mu;
-unsigned char *g_scratch_ptr[NA_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).
+// Device address of the scratch array in the current context, looked up on
+// every call (the context may have been reset or replaced since the last).
 int scratch_address(unsigned char **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return EPIC_ERR_CUDA;
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return EPIC_ERR_INVALID;
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return EPIC_ERR_CUDA;
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return EPIC_ERR_CUDA;
+    *out = static_cast<unsigned char *>(p);
     return EPIC_OK;
 }
 

@@ -242,11 +242,13 @@ __device__ __forceinline__ void tma_load_2d(const Tma &t, const CUtensorMap *map
 }
 
 // All threads wait for the copy, at most TMA_LIMIT_NS; on time-out the run
-// reports EPIC_ERR_TIMEOUT.
+// reports EPIC_ERR_TIMEOUT.  Returns, in every thread of the CTA, whether
+// the copy completed for all of them (false if any thread gave up).
 constexpr unsigned long long TMA_LIMIT_NS = 1000000000ull;
-__device__ __forceinline__ void tma_wait(Tma &t, RunState *st,
+__device__ __forceinline__ bool tma_wait(Tma &t, RunState *st,
                                          unsigned long long limit_ns = TMA_LIMIT_NS) {
     const unsigned long long t0 = global_ns();
+    int gave_up = 0;
     for (;;) {
         unsigned done;
         asm volatile(
@@ -258,10 +260,12 @@ __device__ __forceinline__ void tma_wait(Tma &t, RunState *st,
         if (done) break;
         if (global_ns() - t0 > limit_ns) {
             set_status(st, EPIC_ERR_TIMEOUT);
+            gave_up = 1;
             break;
         }
     }
     t.phase ^= 1u;
+    return __syncthreads_or(gave_up) == 0;
 }
 
 // Half-costs of the region in fixed-point units; a cost outside [0, C_MAX)
@@ -269,8 +273,11 @@ __device__ __forceinline__ void tma_wait(Tma &t, RunState *st,
 // first copied as one box into `stage` (free shared memory, 128-byte
 // aligned), from the region's x origin rounded down to a multiple of 4;
 // cells outside the image are filled with zeros by the copy and get h = 0
-// here, as on the plain path.
-__device__ __forceinline__ void load_costs(const PairDev &P, const Region &g,
+// here, as on the plain path.  Returns false (in every thread) when the
+// copy's wait timed out: the stage is then not read, and the caller leaves
+// the kernel (the run has recorded EPIC_ERR_TIMEOUT; the copy may still land
+// in this CTA's shared memory after it has left).
+__device__ __forceinline__ bool load_costs(const PairDev &P, const Region &g,
                                            unsigned *h, RunState *st, bool fresh,
                                            float *stage, Tma &tma) {
     bool bad = false;
@@ -279,7 +286,7 @@ __device__ __forceinline__ void load_costs(const PairDev &P, const Region &g,
         const int xa = g.x0 - (((g.x0 % 4) + 4) % 4);
         tma_load_2d(tma, fresh ? &P.tm_cost_fresh : &P.tm_cost_again, stage, xa, g.y0,
                     (unsigned)(bw * g.RH * 4));
-        tma_wait(tma, st);
+        if (!tma_wait(tma, st)) return false;
         const int off = g.x0 - xa;
         for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
             int r = i / g.RW, c = i - r * g.RW;
@@ -297,6 +304,7 @@ __device__ __forceinline__ void load_costs(const PairDev &P, const Region &g,
         }
     }
     if (bad) set_status(st, EPIC_ERR_INVALID);
+    return true;
 }
 
 // The relaxation's shared memory: keys (RH x P), half-costs (RH x P); the
@@ -321,8 +329,9 @@ __device__ __forceinline__ int tile_pair(const BatchArgs &a, int t) {
     return a.uniform_tiles > 0 ? t / a.uniform_tiles : find_pair(a.tile_base, a.npairs, t);
 }
 
-// Phase 1: solve tile (tx, ty) on its region from its seeds alone.
-__device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
+// Phase 1: solve tile (tx, ty) on its region from its seeds alone.  Returns
+// false when the cost staging timed out (the CTA must leave the kernel).
+__device__ bool solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
                             unsigned *h, RunState *st, float *stage, Tma &tma) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, P.apron);
@@ -350,9 +359,9 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
             if (gx < P.W && gy < P.H) P.keys[(size_t)gy * P.W + gx] = KEY_INF;
         }
         __syncthreads();
-        return;
+        return true;
     }
-    load_costs(P, g, h, st, true, stage, tma);
+    if (!load_costs(P, g, h, st, true, stage, tma)) return false;
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         K[r * g.P + c] = KEY_INF;
@@ -386,6 +395,7 @@ __device__ void solve_fresh(const PairDev &P, int tx, int ty, pkey_t *K,
                 capped(P, (size_t)gy * P.W + gx, K[(ly + off) * g.P + lx + off]);
     }
     __syncthreads();
+    return true;
 }
 
 __device__ __forceinline__ pkey_t ld_key(const pkey_t *p) { return __ldcg(p); }
@@ -433,12 +443,14 @@ __device__ bool border_dirty(const PairDev &P, int tx, int ty) {
 }
 
 // Phase 2 re-solve of tile (tx, ty) from the current keys (tile + ring).
-// Returns whether any key of the region changed (the same in every thread).
-__device__ bool solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
+// Returns 1 if any key of the region changed, 0 if none did, -1 if the cost
+// staging timed out (the CTA must leave the kernel); the same in every
+// thread.
+__device__ int solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
                             unsigned *h, RunState *st, int pass, float *stage, Tma &tma) {
     const int gx0 = tx * P.tile_w, gy0 = ty * P.tile_h;
     const Region g = make_region(P, gx0, gy0, P.tile_w, P.tile_h, 0);
-    load_costs(P, g, h, st, false, stage, tma);
+    if (!load_costs(P, g, h, st, false, stage, tma)) return -1;
     for (int i = threadIdx.x; i < g.RW * g.RH; i += blockDim.x) {
         int r = i / g.RW, c = i - r * g.RW;
         int gx = g.x0 + c, gy = g.y0 + r;
@@ -458,7 +470,7 @@ __device__ bool solve_again(const PairDev &P, int tx, int ty, pkey_t *K,
     }
     if (threadIdx.x == 0) P.tile_stamp[ty * P.tiles_x + tx] = pass;
     __syncthreads();
-    return changed;
+    return changed ? 1 : 0;
 }
 
 // Chunked passes: queue the eight neighbours of tile t (flat index; local
@@ -523,7 +535,8 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
         const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, P.apron);
         pkey_t *K = reinterpret_cast<pkey_t *>(smem);
         unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-        solve_fresh(P, s_local % P.tiles_x, s_local / P.tiles_x, K, h, st, stage, tma);
+        if (!solve_fresh(P, s_local % P.tiles_x, s_local / P.tiles_x, K, h, st, stage, tma))
+            return;
     }
     if (!grid_sync(st, nblocks)) return;
 
@@ -555,7 +568,7 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                     const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                     pkey_t *K = reinterpret_cast<pkey_t *>(smem);
                     unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-                    solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
+                    if (solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma) < 0) return;
                     if (threadIdx.x == 0) atomicAdd(cnt, 1u);
                 }
                 __syncthreads();
@@ -616,8 +629,9 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                             const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                             pkey_t *K = reinterpret_cast<pkey_t *>(smem);
                             unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-                            if (solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma))
-                                queue_neighbours(a, st, s_pair, tx, ty, pass + 1);
+                            const int r = solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
+                            if (r < 0) return;
+                            if (r > 0) queue_neighbours(a, st, s_pair, tx, ty, pass + 1);
                             if (threadIdx.x == 0) atomicAdd(cnt, 1u);
                         }
                     }
@@ -644,8 +658,9 @@ __global__ void __launch_bounds__(DT_THREADS) dt_kernel(const BatchArgs *__restr
                         const Region g = make_region(P, 0, 0, P.tile_w, P.tile_h, 0);
                         pkey_t *K = reinterpret_cast<pkey_t *>(smem);
                         unsigned *h = reinterpret_cast<unsigned *>(smem + sizeof(pkey_t) * g.RH * g.P);
-                        if (solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma))
-                            queue_neighbours(a, st, s_pair, tx, ty, pass + 1);
+                        const int r = solve_again(P, tx, ty, K, h, st, pass + 1, stage, tma);
+                        if (r < 0) return;
+                        if (r > 0) queue_neighbours(a, st, s_pair, tx, ty, pass + 1);
                         if (threadIdx.x == 0) atomicAdd(cnt, 1u);
                     }
                 }

@@ -5,16 +5,19 @@ where cudaMalloc's implicit synchronisation is not acceptable.  Its scratch is
 a fixed device array inside the library.
 
 Checked through the C ABI against the regular entry point
-(epic_interp_run + epic_interp_get_labels) on two calls in a row, with the
-parity tolerances of tests/parity.py (labels equal, distances within
-1e-4 * D + 1e-6)."""
+(epic_interp_run + epic_interp_get_labels) on two calls in a row (labels
+equal, distances within 1e-4 * D + 1e-6), and against the FP64 oracle with
+the parity rule of tests/parity.py (labels equal or verified near ties,
+distances within 1e-4 * D + 1e-6)."""
 
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1501_02565_gb300 import native, synth
+from parity import check_labels_and_distances
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +64,10 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
         assert rc == native.EPIC_OK, native.STATUS_NAMES.get(rc, rc)
         Lr, Dr = _regular(p, C, M)
         _check(Ln, Dn, Lr, Dr)
+        D_ref, L_ref = oracle.geodesic(p.C, p.matches)
+        report = {}
+        check_labels_and_distances(p.C, p.matches, {"L": Ln, "D": Dn},
+                                   {"L": L_ref, "D": D_ref}, report)
 
 
 def test_noalloc_rejects_frames_beyond_its_scratch():
