@@ -118,6 +118,13 @@ typedef struct {
     int prune_K;          /* neighbours of the NW pass (default 25) */
     int sweep;            /* relaxation sweep schedule when no tile rule
                              applies (see epic_tile_rule_t; default 0) */
+    long long exact_chunk_bytes; /* epic_exact_interp with metric 0: device
+                             bytes of packed keys its single-source
+                             relaxations may hold at once (8 bytes per pixel
+                             per match); the matches run in chunks of
+                             max(1, min(N, exact_chunk_bytes / (8 H W))).
+                             0 = 1 GiB (default).  Only speed and memory
+                             depend on it, never the results. */
 } epic_config_t;
 
 /* One frame pair of a batch; pointers are device pointers. */
@@ -284,8 +291,9 @@ int epic_interp_get_stage_times(epic_interp_t *h, float *ms_out, int n_stages,
  * knn_dist_out [H*W*K] float32 receive every pixel's list in key order (both
  * NULL, or both set).  K is clamped to N and limited by shared memory
  * (K * 512 bytes per 64 pixels; K <= 448 on GB300).  With metric 0 the
- * handle holds N * H * W * 4 bytes of distances plus up to 1 GiB of
- * relaxation scratch (grown on demand, EPIC_ERR_OOM if it cannot be).  Runs
+ * handle holds N * H * W * 4 bytes of distances plus up to
+ * exact_chunk_bytes (1 GiB by default) of relaxation keys (grown on demand,
+ * EPIC_ERR_OOM if it cannot be).  Runs
  * on `stream` and waits for completion; returns the device status. */
 int epic_exact_interp(epic_interp_t *h, const float *cost_map,
                       const float *matches, int H, int W, int N, int K,
@@ -350,6 +358,18 @@ int epic_refine(epic_interp_t *h, const float *I1, const float *I2, int H,
  * recorded (EPIC_ERR_TIMEOUT when the bound works) and leaves the handle and
  * the context usable.  Waits for completion. */
 int epic_selftest_wait_timeout(epic_interp_t *h, int which, int limit_ms);
+
+/* Device scratch one pair of H x W pixels, N matches and neighbourhood size
+ * K takes in the handle's arena when it runs in a batch (its packed keys,
+ * seed bins, edge table, CSR rows, models, optional K-NN lists and pruning
+ * buffers, and its K-NN retry-list slots), in *bytes; a batch needs the sum
+ * over its pairs plus 256 bytes.  The caller's own buffers (cost map,
+ * matches, flow) are not included.  Uses the configuration and tile rules of
+ * `h`; with h = NULL, those of *cfg and no tile rules (cfg = NULL: the
+ * defaults).  A host computation: needs no device and enqueues nothing.
+ * EPIC_ERR_INVALID for sizes that epic_interp_run would refuse. */
+int epic_interp_request_bytes(const epic_interp_t *h, const epic_config_t *cfg, int H,
+                              int W, int N, int K, long long *bytes);
 
 /* Number of kernel launches one run of `n` pairs enqueues. */
 int epic_interp_launches_per_run(epic_interp_t *h, int n);

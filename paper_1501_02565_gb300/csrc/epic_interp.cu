@@ -1081,7 +1081,8 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
         int tw, th, ap, sw;
         choose_tiles(c, h->rules, H, W, &tw, &th, &ap, &sw);
         const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th, T = tx * ty;
-        const long long Cm = std::max(1LL, std::min((long long)N, (1LL << 30) / (P * 8)));
+        const long long chunk_bytes = c.exact_chunk_bytes > 0 ? c.exact_chunk_bytes : (1LL << 30);
+        const long long Cm = std::max(1LL, std::min((long long)N, chunk_bytes / (P * 8)));
         const size_t small_ints = (size_t)(T + 1) + T + 1 + T + 1 + 1 + 4;  // per pseudo-pair
         const size_t d_bytes = align_up((size_t)N * P * sizeof(float), 256);
         const size_t k_bytes = align_up((size_t)Cm * P * sizeof(pkey_t), 256);
@@ -1368,6 +1369,34 @@ int epic_gradient_cost(const float *image, int frames, int H, int W, int channel
     cudaError_t e = epic::launch_gradcost(image, frames, H, W, channels, floor_, cost_out, sms,
                                           reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+int epic_interp_request_bytes(const epic_interp_t *h, const epic_config_t *cfg, int H, int W,
+                              int N, int K, long long *bytes) {
+    if (!bytes || H < 1 || W < 1 || N < 1 || K < 1 || N > epic::MAX_LABELS ||
+        (long long)H * W > (1LL << 30))
+        return EPIC_ERR_INVALID;
+    epic_config_t c;
+    if (h) c = h->cfg;
+    else if (cfg) c = *cfg;
+    else epic_config_default(&c);
+    static const std::vector<epic_tile_rule_t> no_rules;
+    epic_pair_desc_t d{};
+    d.cost_map = reinterpret_cast<const float *>(16);
+    d.matches = reinterpret_cast<const float *>(16);
+    d.flow_out = reinterpret_cast<float *>(16);
+    d.H = H;
+    d.W = W;
+    d.N = N;
+    d.K = K;
+    d.a = 1.f;
+    const PairDev P = make_pair_desc(c, h ? h->rules : no_rules, d);
+    // the pair's arena regions (each 256-byte aligned, so a pair placed after
+    // any other needs at most its aligned size) and its K-NN retry-list slots
+    const size_t per = layout_pair(0, P, c.max_degree, c.keep_intermediates != 0,
+                                   c.prune != 0).end;
+    *bytes = (long long)(per + sizeof(int) * (size_t)N);
+    return EPIC_OK;
 }
 
 int epic_interp_launches_per_run(epic_interp_t *h, int n) {

@@ -38,7 +38,8 @@ EXPORTED = (
     "epic_interp_get_pruning", "epic_interp_get_passes", "epic_interp_get_knn_retries",
     "epic_interp_set_tile_rules",
     "epic_interp_enable_stage_timing",
-    "epic_interp_get_stage_times", "epic_interp_launches_per_run",
+    "epic_interp_get_stage_times", "epic_interp_request_bytes",
+    "epic_interp_launches_per_run",
     "epic_interp_last_error", "epic_interp_destroy",
     "epic_geodesic_labels_noalloc", "epic_exact_interp", "epic_gradient_cost",
     "epic_refine_params_default", "epic_refine", "epic_selftest_wait_timeout",
@@ -56,7 +57,7 @@ class epic_config_t(ctypes.Structure):
         ("max_degree", ctypes.c_int), ("use_graphs", ctypes.c_int),
         ("estimator", ctypes.c_int), ("prune", ctypes.c_int),
         ("prune_threshold", ctypes.c_float), ("prune_K", ctypes.c_int),
-        ("sweep", ctypes.c_int),
+        ("sweep", ctypes.c_int), ("exact_chunk_bytes", ctypes.c_longlong),
     ]
 
 
@@ -148,6 +149,9 @@ def load(path: str | None = None):
     lib.epic_interp_enable_stage_timing.restype = I
     lib.epic_interp_get_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), I, pi]
     lib.epic_interp_get_stage_times.restype = I
+    lib.epic_interp_request_bytes.argtypes = [P, ctypes.POINTER(epic_config_t), I, I, I, I,
+                                              ctypes.POINTER(ctypes.c_longlong)]
+    lib.epic_interp_request_bytes.restype = I
     lib.epic_interp_launches_per_run.argtypes = [P, I]
     lib.epic_interp_launches_per_run.restype = I
     lib.epic_interp_last_error.argtypes = [P]
@@ -448,8 +452,26 @@ class EpicInterp:
                     "get_stage_times")
         return dict(zip(self.STAGES, list(arr))), n.value
 
+    def request_bytes(self, H, W, N, K):
+        """Arena bytes one H x W pair with N matches and K neighbours takes
+        in a batch on this handle (epic_interp_request_bytes)."""
+        return request_bytes(H, W, N, K, handle=self.h)
+
     def launches_per_run(self, n=1):
         return self.lib.epic_interp_launches_per_run(self.h, n)
+
+
+def request_bytes(H, W, N, K, cfg=None, handle=None):
+    """epic_interp_request_bytes: the arena bytes of one pair, from the
+    handle's configuration and tile rules, else from `cfg` (an epic_config_t,
+    None = defaults) without tile rules.  Needs no device."""
+    lib = load()
+    out = ctypes.c_longlong()
+    rc = lib.epic_interp_request_bytes(handle, None if cfg is None else ctypes.byref(cfg),
+                                       int(H), int(W), int(N), int(K), ctypes.byref(out))
+    if rc != EPIC_OK:
+        raise EpicError(rc, "epic_interp_request_bytes")
+    return out.value
 
 
 def gradient_cost(image, floor=0.0, out=None, stream=None):

@@ -29,12 +29,7 @@ import time
 
 import numpy as np
 
-from .native import EPIC_MAX_K, EpicInterp
-
-# bytes of library scratch per pixel and per match (keys, bins, edge table,
-# adjacency, models; see the arena layout in csrc/epic_interp.cu)
-_SCRATCH_PER_PIXEL = 8.2
-_SCRATCH_PER_MATCH = 16 * 12 + 16 * 2 * 16 + 96   # edge table, CSR adjacency, per-node
+from .native import EPIC_MAX_K, EpicInterp, request_bytes
 
 
 @dataclasses.dataclass
@@ -50,6 +45,7 @@ class Request:
     flow: object = None        # pinned torch tensor [H, W, 2] once done
     out: object = None         # optional caller-owned pinned [H, W, 2] output
     error: str | None = None
+    _bytes: int = 0            # device bytes, set by the server at submission
     _done: threading.Event = dataclasses.field(default_factory=threading.Event)
 
     @property
@@ -64,9 +60,15 @@ class Request:
     def P(self):
         return self.C.shape[0] * self.C.shape[1]
 
-    def device_bytes(self):
+    def device_bytes(self, engine=None):
+        """Device bytes the request holds while admitted: its cost map,
+        matches and flow, plus the library's scratch for the pair as the
+        library computes it (epic_interp_request_bytes) for `engine`'s
+        configuration, or for the default configuration."""
         N = int(self.matches.shape[0])
-        return int(self.P * (4 + 8 + _SCRATCH_PER_PIXEL) + N * (16 + _SCRATCH_PER_MATCH))
+        scratch = (engine.request_bytes(self.H, self.W, N, self.K) if engine is not None
+                   else request_bytes(self.H, self.W, N, self.K))
+        return int(self.P * (4 + 8) + N * 16 + scratch)
 
     def wait(self, timeout=None):
         if not self._done.wait(timeout):
@@ -143,7 +145,9 @@ class Server:
         m = m.numpy() if hasattr(m, "numpy") else m
         if C.ndim != 2 or m.ndim != 2 or m.shape[1] != 4 or m.shape[0] < 1:
             raise ValueError("C must be [H, W] and matches [N, 4] with N >= 1")
-        if not (np.isfinite(C).all() and (C >= 0).all()):
+        # two reductions: a NaN makes both comparisons false, +inf the second
+        lo, hi = C.min(), C.max()
+        if not (lo >= 0 and hi < np.inf):
             raise ValueError("cost map must be finite and >= 0")
         x = np.floor(m[:, 0].astype(np.float64) + 0.5)
         y = np.floor(m[:, 1].astype(np.float64) + 0.5)
@@ -154,9 +158,13 @@ class Server:
         if min(req.K, m.shape[0]) > EPIC_MAX_K:
             raise ValueError(f"K (clamped to N) must be at most {EPIC_MAX_K}")
 
-    def submit(self, req: Request) -> Request:
-        self.validate(req)
-        if req.device_bytes() > self.budget:
+    def submit(self, req: Request, validate: bool = True) -> Request:
+        """Queue a request.  validate=False skips the host checks, for inputs
+        the caller has already passed through Server.validate."""
+        if validate:
+            self.validate(req)
+        req._bytes = req.device_bytes(self.engine)
+        if req._bytes > self.budget:
             raise ValueError(f"request {req.rid} needs more device memory than the budget")
         req.arrival = time.monotonic() if req.arrival == 0.0 else req.arrival
         with self.lock:
@@ -171,7 +179,7 @@ class Server:
         with self.lock:
             while self.pending and len(self.uploading) + len(admitted) < self.max_batch:
                 r = self.pending[0]
-                need = r.device_bytes()
+                need = r._bytes
                 if self.in_use + need > self.budget:
                     break
                 self.pending.popleft()
@@ -256,7 +264,7 @@ class Server:
                     r.flow = r._hF
                     for k in ("_dC", "_dM", "_dF", "_hold"):
                         setattr(r, k, None)
-                    self.in_use -= r.device_bytes()
+                    self.in_use -= r._bytes
                     self.completed.append(r)
                     r._done.set()
         return True
@@ -295,15 +303,17 @@ class Server:
         }
 
 
-def replay(server: Server, requests, arrivals):
-    """Submit `requests` at the given offsets (seconds from now) and wait."""
+def replay(server: Server, requests, arrivals, validate: bool = True):
+    """Submit `requests` at the given offsets (seconds from now) and wait.
+    A request's latency counts from its scheduled arrival, so a submitter
+    that falls behind the schedule adds to the measured latency."""
     t0 = time.monotonic()
     for r, t in zip(requests, arrivals):
         delay = t0 + t - time.monotonic()
         if delay > 0:
             time.sleep(delay)
-        r.arrival = time.monotonic()
-        server.submit(r)
+        r.arrival = t0 + t
+        server.submit(r, validate=validate)
     for r in requests:
         r.wait(timeout=120)
     return server.stats()

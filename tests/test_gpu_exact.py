@@ -60,9 +60,9 @@ def _ill_conditioned(C, M, ref, a, estimator):
     return (worst > FLOW_TOL / 2) | near_det
 
 
-def _check(C, M, K, a, metric, estimator="la"):
+def _check(C, M, K, a, metric, estimator="la", **extra_cfg):
     K = min(K, M.shape[0])
-    cfg = {"estimator": 1 if estimator == "nw" else 0}
+    cfg = {"estimator": 1 if estimator == "nw" else 0, **extra_cfg}
     flow, idx, dist = _gpu_exact(C, M, K, a, metric, **cfg)
     ref, nxt = _reference_with_next(C, M, K, a, metric, estimator)
     kth = ref["dist"][:, -1]
@@ -106,6 +106,29 @@ def test_config1_pair(metric):
         aee = lambda f: float(np.hypot(*(f - p.gt_flow).transpose(2, 0, 1)).mean())
         print(f"[exact vs approx] AEE to ground truth: exact {aee(flow):.3f}, "
               f"approx {aee(approx):.3f}")
+
+
+@pytest.mark.parametrize("metric", ["geodesic", "euclidean"])
+def test_config1_pair_in_several_chunks(metric):
+    # a key budget of 137 single-source runs splits config 1's 500 matches
+    # into chunks of 137, 137, 137 and a ragged 89: the chunk offsets and the
+    # rows of D across chunk boundaries must give the oracle's lists and
+    # flow, and the same bits as one chunk
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    p = synth.config_pair(1, 0)
+    budget = 8 * p.H * p.W * 137
+    flow, _ = _check(p.C, p.matches, p.K, p.a, metric, exact_chunk_bytes=budget)
+    Ct = torch.from_numpy(p.C).cuda()
+    Mt = torch.from_numpy(p.matches).cuda()
+    outs = []
+    for b in (budget, 0):
+        eng = EpicInterp(0, exact_chunk_bytes=b)
+        outs.append([t.cpu() for t in eng.exact(Ct, Mt, p.K, p.a, metric=metric,
+                                                with_knn=True)])
+        eng.close()
+    for x, y in zip(*outs):
+        assert torch.equal(x, y)
 
 
 def test_nw_estimator_and_single_neighbour():

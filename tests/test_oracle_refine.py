@@ -112,3 +112,40 @@ def test_refinement_recovers_a_translation():
     e0 = np.hypot(f0[..., 0] - 2, f0[..., 1] - 1)[inner].mean()
     e1 = np.hypot(out[..., 0] - 2, out[..., 1] - 1)[inner].mean()
     assert e1 < 0.2 * e0, (e0, e1)
+
+
+def _load_fixture(name):
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, *vals = line.split()
+                out[k] = [float(v) for v in vals]
+    return out
+
+
+def test_coefficients_match_the_hand_derived_fixture():
+    # tests/golden/refine_coeffs.txt: two-channel quadratic frames on 7x7,
+    # where central differences are exact, with every term of the data and
+    # smoothness coefficients derived by hand at two pixels.  Dropping the
+    # normalisation theta or gamma, weighting by exp(-kappa ||grad I||^2),
+    # sharing one Psi between the two constancies, or taking Psi' at another
+    # residual changes these values.
+    g = _load_fixture("refine_coeffs.txt")
+    ys, xs = np.mgrid[0:7, 0:7].astype(np.float64)
+    X, Y = xs - 3, ys - 3
+    I1 = np.stack([0.5 + 0.4 * X + 0.2 * Y + 0.1 * X * X + 0.05 * X * Y - 0.05 * Y * Y,
+                   0.3 - 0.2 * X + 0.1 * Y + 0.1 * X * Y], -1)
+    I2w = I1 + np.stack([0.1 + 0.02 * X - 0.04 * Y + 0.1 * Y * Y,
+                         -0.05 + 0.06 * X + 0.02 * X * X], -1)
+    u = 0.2 * X + 0.1 * Y
+    v = -0.1 * X + 0.3 * Y
+    out = dict(zip(("A11", "A12", "A22", "b1", "b2", "phi"),
+                   R.coefficients(I1, I2w, u, v, R.RefineParams())))
+    for tag in ("3_3", "4_2"):
+        x, y = (int(t) for t in g["at_" + tag])
+        for k, arr in out.items():
+            np.testing.assert_allclose(arr[y, x], g[f"{k}_{tag}"][0], rtol=1e-12, atol=1e-15,
+                                       err_msg=f"{k} at ({x},{y})")
