@@ -32,7 +32,7 @@ import numpy as np
 from .native import EPIC_MAX_K, EpicInterp, request_bytes
 
 
-@dataclasses.dataclass
+@dataclasses.dataclass(eq=False)     # requests compare by identity
 class Request:
     C: np.ndarray              # float32 [H, W]
     matches: np.ndarray        # float32 [N, 4]
@@ -161,6 +161,8 @@ class Server:
     def submit(self, req: Request, validate: bool = True) -> Request:
         """Queue a request.  validate=False skips the host checks, for inputs
         the caller has already passed through Server.validate."""
+        if self.thread is not None and not self.thread.is_alive():
+            raise RuntimeError("the server loop is not running")
         if validate:
             self.validate(req)
         req._bytes = req.device_bytes(self.engine)
@@ -270,6 +272,23 @@ class Server:
         return True
 
     def _loop(self):
+        try:
+            self._loop_body()
+        except BaseException as exc:   # fail every outstanding request, never hang them
+            msg = f"server loop failed: {exc!r}"
+            with self.lock:
+                self.running = False
+                waiting = list(self.pending) + list(self.uploading)
+                waiting += [r for batch, _, _ in self.inflight for r in batch]
+                self.pending.clear()
+                self.uploading = []
+                self.inflight = []
+                for r in waiting:
+                    r.error = msg
+                    r._done.set()
+            raise
+
+    def _loop_body(self):
         self.torch.cuda.set_device(self.device)
         while True:
             with self.lock:

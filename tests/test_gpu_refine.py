@@ -1,9 +1,16 @@
 """Variational refinement on the GPU (epic_refine) vs the FP64 oracle
 (Sec. 4).  The GPU runs the same discretisation in float32; after 5
 fixed-point iterations x 30 red-black SOR iterations its flow is compared
-with the oracle's from the same inputs, at every pixel, within the flow
-tolerance of the interpolator (REF_TOL = 1e-3 px), on small frames and on a
-full Sintel-shaped 1024x436 frame."""
+with the oracle's from the same inputs, within the flow tolerance of the
+interpolator (REF_TOL = 1e-3 px), on small frames (every pixel) and on a
+full Sintel-shaped 1024x436 frame.
+
+On the full frame a few pixels are ill-conditioned: there the FP64 result
+itself moves by up to ~0.08 px when the starting flow is moved by 1e-5 px,
+the size of float32's rounding of ~100 px flows, so no float32 computation
+can hold them to 1e-3 px.  Those pixels -- where the FP64 result moves by
+more than half the tolerance under such a perturbation (two random draws) --
+are excluded and counted; every other pixel is held to REF_TOL."""
 
 import numpy as np
 import pytest
@@ -15,6 +22,7 @@ from parity import FLOW_TOL
 pytestmark = pytest.mark.gpu
 
 REF_TOL = FLOW_TOL
+SENS_PX_IN = 1e-5      # perturbation of the starting flow, px (float32 ulp of 128 is 1.5e-5)
 
 
 def _gpu_refine(I1, I2, flow, **prm):
@@ -104,10 +112,20 @@ def test_full_size_sintel_frame(start):
         eng.close()
     g = _gpu_refine(I1, I2, flow0)
     ref = R.refine(I1, I2, flow0)
-    err = np.abs(g - ref).max()
-    print(f"\n[refine 1024x436 from {start}] max |gpu - oracle| = {err:.3g} px, "
-          f"mean update {np.abs(ref - flow0).mean():.3g} px")
-    assert err <= REF_TOL
+    ill = np.zeros(ref.shape[:2], bool)
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        moved = R.refine(I1, I2, flow0.astype(np.float64) +
+                         SENS_PX_IN * rng.uniform(-1, 1, flow0.shape))
+        ill |= np.abs(moved - ref).max(-1) > REF_TOL / 2
+    err = np.abs(g - ref).max(-1)
+    e_in = err[~ill]
+    print(f"\n[refine 1024x436 from {start}] max |gpu - oracle| = {e_in.max():.3g} px over "
+          f"{e_in.size} pixels; {ill.sum()} ill-conditioned pixels excluded (max there "
+          f"{err[ill].max() if ill.any() else 0:.3g} px); mean update "
+          f"{np.abs(ref - flow0).mean():.3g} px")
+    assert ill.sum() <= 1e-3 * ill.size
+    assert e_in.max() <= REF_TOL
 
 
 def test_refine_before_and_after_the_exact_variant_on_one_handle():
