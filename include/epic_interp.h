@@ -92,9 +92,10 @@ typedef struct {
     float fallback_eps;   /* fit is degenerate when det M <= eps (tr M/3)^3
                              or fewer than 3 neighbours; then the NW estimate
                              of Eq. 1 at p_m is used as a constant flow */
-    int tile_w, tile_h;   /* relaxation tile (0 = chosen per frame size) */
-    int apron;            /* extra context around a tile in the first
-                             relaxation pass (-1 = chosen per frame size) */
+    int tile_w, tile_h;   /* relaxation tile (0 = 64 x 32); with sweep 2 the
+                             width is always 64 and tile_h at most 32 */
+    int apron;            /* sweep 0 / 1: extra context around a tile in the
+                             first relaxation pass (-1 = 4); sweep 2: none */
     int keep_intermediates; /* 1: keep K-NN lists for epic_interp_get_knn */
     int max_degree;       /* ignored: the match graph is stored as CSR rows
                              with no degree limit */
@@ -116,8 +117,14 @@ typedef struct {
                              passes, the pair keeps all its matches. */
     float prune_threshold; /* px (default 5) */
     int prune_K;          /* neighbours of the NW pass (default 25) */
-    int sweep;            /* relaxation sweep schedule when no tile rule
-                             applies (see epic_tile_rule_t; default 0) */
+    int sweep;            /* relaxation schedule when no tile rule applies
+                             (see epic_tile_rule_t; default 2).  The warp
+                             tiles of schedule 2 are used only when this and
+                             every installed rule ask for them; otherwise a
+                             frame whose rule says 2 gets 64 x 32 tiles with
+                             apron 4 and schedule 0.  The exact variant's
+                             single-source runs always use schedule 0 or 1.
+                             Every schedule gives the same result. */
     long long exact_chunk_bytes; /* epic_exact_interp with metric 0: device
                              bytes of packed keys its single-source
                              relaxations may hold at once (8 bytes per pixel
@@ -137,9 +144,13 @@ typedef struct {
 } epic_pair_desc_t;
 
 /* A relaxation tile rule: frames of at most max_pixels pixels use tiles of
- * tile_w x tile_h with the given first-pass apron and sweep schedule
- * (0: lines cut into segments so every thread of the CTA has one; 1: a
- * thread sweeps whole lines). */
+ * tile_w x tile_h with the given first-pass apron and schedule:
+ *   0: a CTA solves a tile with its apron by directional sweeps, lines cut
+ *      into segments so every thread of the CTA has one;
+ *   1: the same, a thread sweeping whole lines;
+ *   2: a warp solves a tile of 64 x tile_h (tile_h 1..32, apron 0) by down
+ *      and up passes over its rows, each row taking the three candidates of
+ *      the row before it and then closed along itself (the default). */
 typedef struct {
     long long max_pixels;
     int tile_w, tile_h, apron;

@@ -86,7 +86,8 @@ struct PairDev {
     int H, W, N, K;
     float a;
     int tile_w, tile_h, apron;
-    int sweep;              // relaxation sweep schedule (0 segmented lines, 1 whole lines)
+    int sweep;              // relaxation schedule: 0 segmented lines, 1 whole lines
+                            // (k_dt.cu); 2 row-closure passes on warp tiles (k_relax.cu)
     int tiles_x, tiles_y;
     int hash_cap;           // power of two
     int flow_vec_ok;        // flow pointer is 16-byte aligned
@@ -198,6 +199,62 @@ __device__ __forceinline__ int get_status(const RunState *s) {
     return *(volatile const int *)&s->status;
 }
 
+// ---------------------------------------------------------------------------
+// Bounded grid barrier of the cooperative relaxation launches.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long BARRIER_LIMIT_NS = 2000000000ull;  // 2 s
+constexpr int PASS_CHUNK = 8;  // tiles per dispenser step in chunked verification passes
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-free generation barrier over all CTAs of a cooperative launch.  The
+// wait gives up after BARRIER_LIMIT_NS (or as soon as another CTA has given
+// up) and reports EPIC_ERR_TIMEOUT instead of spinning forever.
+static __device__ __noinline__ bool grid_sync(RunState *st, unsigned nblocks,
+                          unsigned long long limit_ns = BARRIER_LIMIT_NS) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        GridBarrier *b = &st->barrier;
+        int ok = 1;
+        unsigned g = ld_acquire(&b->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&b->count, 1u);
+        if (arrived == nblocks - 1) {
+            b->count = 0;
+            __threadfence();
+            st_release(&b->gen, g + 1);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (ld_acquire(&b->gen) == g) {
+                if (get_status(st) == EPIC_ERR_TIMEOUT) { ok = 0; break; }
+                if (global_ns() - t0 > limit_ns) {
+                    set_status(st, EPIC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 constexpr int WRITEOUT_CHUNK = 1024;  // pixels per write-out work item
 constexpr int CLEAR_CHUNK = 4096;     // 8-byte words per clear work item
 constexpr int DT_THREADS = 256;
@@ -269,6 +326,13 @@ cudaError_t launch_collect_edges(const PairDev *pair_host_copy, int *em,
                                  int *en, float *ew, int cap, int *count,
                                  cudaStream_t stream);
 size_t dt_smem_bytes(int tile_w, int tile_h, int apron);
+// The interpolator's relaxation on warp-owned tiles of 64 x tile_h pixels
+// (k_relax.cu); max_rows = the largest tile_h of the batch (<= 32).
+constexpr int RELAX_TILE_W = 64;
+constexpr int RELAX_MAX_ROWS = 32;
+size_t relax_smem_bytes(int max_rows);
+cudaError_t launch_relax(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                         int max_rows, bool fixed_grid, int *grid_used);
 void knn_table_sizes(int max_K, int *hs, int *fs);
 void knn_retry_table_sizes(int max_K, int smem_limit, int *hs, int *fs);
 size_t knn_smem_per_warp(int max_K);

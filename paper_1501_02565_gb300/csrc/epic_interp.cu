@@ -121,23 +121,59 @@ int next_pow2(long long x) {
 }
 
 // Tile shape for the relaxation of an H x W frame: the first installed rule
-// covering the frame, else the configured tile (64 x 32, apron 4 by default).
+// covering the frame, else the configured tile (64 x 32 by default; apron 4
+// for the sweep schedules of k_dt.cu, none for the warp tiles of
+// k_relax.cu).  With warp_tiles_ok = false (the exact variant's runs, which
+// need the capped relaxation of k_dt.cu), a warp-tile choice becomes the
+// default k_dt.cu tile.
+constexpr int SWEEP_WARP_TILES = 2;
+
 void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &rules, int H,
-                  int W, int *tw, int *th, int *ap, int *sweep = nullptr) {
+                  int W, int *tw, int *th, int *ap, int *sweep = nullptr,
+                  bool warp_tiles_ok = true) {
     const long long P = (long long)H * W;
+    int s = c.sweep;
+    bool found = false;
     for (const auto &r : rules) {
         if (P <= r.max_pixels) {
             *tw = r.tile_w;
             *th = r.tile_h;
             *ap = r.apron;
-            if (sweep) *sweep = r.sweep;
-            return;
+            s = r.sweep;
+            found = true;
+            break;
         }
     }
-    *tw = c.tile_w > 0 ? c.tile_w : 64;
-    *th = c.tile_h > 0 ? c.tile_h : 32;
-    *ap = c.apron >= 0 ? c.apron : 4;
-    if (sweep) *sweep = c.sweep;
+    if (!found) {
+        *tw = c.tile_w > 0 ? c.tile_w : 64;
+        *th = c.tile_h > 0 ? c.tile_h : 32;
+        *ap = c.apron >= 0 ? c.apron : (s == SWEEP_WARP_TILES ? 0 : 4);
+    }
+    if (s == SWEEP_WARP_TILES) {
+        if (warp_tiles_ok) {
+            *tw = epic::RELAX_TILE_W;
+            *th = std::min(*th, epic::RELAX_MAX_ROWS);
+            *ap = 0;
+        } else {
+            *tw = 64;
+            *th = 32;
+            *ap = 4;
+            s = 0;
+        }
+    }
+    if (sweep) *sweep = s;
+}
+
+// The interpolator's relaxation kernel for this handle: the warp tiles of
+// k_relax.cu when the configuration and every tile rule ask for them, else
+// k_dt.cu (a frame whose rule asks for warp tiles then takes the default
+// k_dt.cu tile).  A property of the handle, not of a batch, so that a
+// captured launch sequence replays for any batch.
+bool uses_warp_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &rules) {
+    if (c.sweep != SWEEP_WARP_TILES) return false;
+    for (const auto &r : rules)
+        if (r.sweep != SWEEP_WARP_TILES) return false;
+    return true;
 }
 
 struct Layout {
@@ -203,7 +239,8 @@ PairDev make_pair_desc(const epic_config_t &c, const std::vector<epic_tile_rule_
         P.K = std::min(c.prune_K, d.N);
     }
     P.a = d.a;
-    choose_tiles(c, rules, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron, &P.sweep);
+    choose_tiles(c, rules, d.H, d.W, &P.tile_w, &P.tile_h, &P.apron, &P.sweep,
+                 uses_warp_tiles(c, rules));
     P.tiles_x = (d.W + P.tile_w - 1) / P.tile_w;
     P.tiles_y = (d.H + P.tile_h - 1) / P.tile_h;
     P.hash_cap = std::max(1024, next_pow2(8LL * d.N));
@@ -386,6 +423,7 @@ void epic_config_default(epic_config_t *c) {
     c->prune = 0;
     c->prune_threshold = 5.f;
     c->prune_K = 25;
+    c->sweep = SWEEP_WARP_TILES;
 }
 
 int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg) {
@@ -400,16 +438,21 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     if (c.max_pairs <= 0) c.max_pairs = 1;
     if (c.prune_K <= 0) c.prune_K = 25;
     c.max_K = std::min(c.max_K, (int)EPIC_MAX_K);
-    if (c.sweep != 0 && c.sweep != 1) c.sweep = 0;
+    if (c.sweep < 0 || c.sweep > SWEEP_WARP_TILES) c.sweep = SWEEP_WARP_TILES;
     if ((c.estimator != 0 && c.estimator != 1) || !(c.prune_threshold >= 0.f) ||
         !std::isfinite(c.prune_threshold)) {
         int r = fail(h, EPIC_ERR_INVALID, "estimator must be 0 or 1, prune_threshold finite >= 0");
         delete h;
         return r;
     }
-    if ((c.tile_w > 0 && c.tile_w < 8) || (c.tile_h > 0 && c.tile_h < 8) ||
-        c.tile_w > 256 || c.tile_h > 256) {
-        int r = fail(h, EPIC_ERR_INVALID, "tile sides must be in [8, 256]");
+    // warp tiles are 64 columns (a configured width is ignored) and 1..32 rows
+    const bool bad_tile = c.sweep == SWEEP_WARP_TILES
+                              ? c.tile_h > epic::RELAX_MAX_ROWS
+                              : (c.tile_w > 0 && c.tile_w < 8) || (c.tile_h > 0 && c.tile_h < 8) ||
+                                    c.tile_w > 256 || c.tile_h > 256;
+    if (bad_tile) {
+        int r = fail(h, EPIC_ERR_INVALID,
+                     "tile sides must be in [8, 256] (warp tiles: at most 32 rows)");
         delete h;
         return r;
     }
@@ -563,12 +606,22 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     // on this batch: kernel sizes from the configured maxima
     // graph launches size the relaxation's shared memory for the largest
     // tile the handle can pick (configured tile or any rule)
+    const bool warp_tiles = uses_warp_tiles(c, h->rules);
+    // the configured tile counts unless a rule covers every frame size
+    bool rules_cover_all = false;
+    for (const auto &r : h->rules) rules_cover_all |= r.max_pixels >= (1LL << 30);
     int cfg_tw = c.tile_w > 0 ? c.tile_w : 64, cfg_th = c.tile_h > 0 ? c.tile_h : 32;
-    int cfg_ap = c.apron >= 0 ? c.apron : 4;
+    int cfg_ap = c.apron >= 0 ? c.apron : (warp_tiles ? 0 : 4);
+    if (rules_cover_all) cfg_tw = cfg_th = 1, cfg_ap = 0;
     for (const auto &r : h->rules) {
         cfg_tw = std::max(cfg_tw, r.tile_w);
         cfg_th = std::max(cfg_th, r.tile_h);
         cfg_ap = std::max(cfg_ap, r.apron);
+    }
+    if (warp_tiles) {
+        cfg_tw = epic::RELAX_TILE_W;
+        cfg_th = std::min(cfg_th, epic::RELAX_MAX_ROWS);
+        cfg_ap = 0;
     }
     const int cfg_K = std::min((int)EPIC_MAX_K, std::max(c.max_K, c.prune ? c.prune_K : 1));
     const bool graph = c.use_graphs && stream != nullptr && !h->timing && max_K <= cfg_K &&
@@ -614,7 +667,8 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     a.state = h->state;
     if (epic::knn_warps_per_cta(knn_K, h->smem_optin) < 1)
         return fail(h, EPIC_ERR_INVALID, "K too large for the per-warp search tables");
-    if (epic::dt_smem_bytes(dt_tw, dt_th, dt_ap) > (size_t)h->smem_optin)
+    if ((warp_tiles ? epic::relax_smem_bytes(dt_th) : epic::dt_smem_bytes(dt_tw, dt_th, dt_ap)) >
+        (size_t)h->smem_optin)
         return fail(h, EPIC_ERR_INVALID, "relaxation tile does not fit in shared memory");
 
     char *hs = sl.host;
@@ -627,6 +681,10 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
 
     epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
     BatchArgs *dev_rw = reinterpret_cast<BatchArgs *>(sl.dev);
+    auto relax = [&]() -> cudaError_t {
+        return warp_tiles ? epic::launch_relax(a, dev_a, lc, dt_th, graph, nullptr)
+                          : epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr);
+    };
     const bool prune = c.prune != 0;
     // ev (timing only): a start and an end event per stage
     auto enqueue = [&](cudaEvent_t *ev, size_t copy_bytes) -> cudaError_t {
@@ -640,7 +698,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
             // first pass: NW estimate at every match and its keep flag, then
             // the compaction that rewrites the device tables for the second
             if ((r = epic::launch_prepare(a, dev_a, lc))) return r;
-            if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
+            if ((r = relax())) return r;
             if ((r = epic::launch_edges(a, dev_a, lc, dt_tw, dt_th))) return r;
             if ((r = epic::launch_scatter(a, dev_a, lc))) return r;
             if ((r = epic::launch_knn_fit(a, dev_a, lc, knn_K))) return r;
@@ -651,7 +709,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         if ((r = epic::launch_prepare(a, dev_a, lc))) return r;
         mark(1);
         mark(2);
-        if ((r = epic::launch_dt(a, dev_a, lc, dt_tw, dt_th, dt_ap, graph, nullptr))) return r;
+        if ((r = relax())) return r;
         mark(3);
         mark(4);
         if ((r = epic::launch_edges(a, dev_a, lc, dt_tw, dt_th))) return r;
@@ -1010,6 +1068,12 @@ int epic_interp_set_tile_rules(epic_interp_t *h, const epic_tile_rule_t *rules, 
     if (n < 0 || (n > 0 && !rules)) return fail(h, EPIC_ERR_INVALID, "bad rule list");
     std::vector<epic_tile_rule_t> v(rules, rules + n);
     for (const auto &r : v) {
+        if (r.sweep == SWEEP_WARP_TILES) {
+            if (r.tile_w != epic::RELAX_TILE_W || r.tile_h < 1 || r.tile_h > epic::RELAX_MAX_ROWS ||
+                r.apron != 0 || r.max_pixels < 1)
+                return fail(h, EPIC_ERR_INVALID, "warp-tile rule needs 64 x (1..32) tiles, apron 0");
+            continue;
+        }
         if (r.tile_w < 8 || r.tile_h < 8 || r.tile_w > 256 || r.tile_h > 256 || r.apron < 0 ||
             r.apron > 64 || r.apron + 1 > std::min(r.tile_w, r.tile_h) || r.max_pixels < 1 ||
             (r.sweep != 0 && r.sweep != 1))
@@ -1079,7 +1143,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
         // single-source relaxations, Cm matches at a time, each a pseudo-pair
         // with one seed; their distances become row m of D [N][P]
         int tw, th, ap, sw;
-        choose_tiles(c, h->rules, H, W, &tw, &th, &ap, &sw);
+        choose_tiles(c, h->rules, H, W, &tw, &th, &ap, &sw, false);
         const int tx = (W + tw - 1) / tw, ty = (H + th - 1) / th, T = tx * ty;
         const long long chunk_bytes = c.exact_chunk_bytes > 0 ? c.exact_chunk_bytes : (1LL << 30);
         const long long Cm = std::max(1LL, std::min((long long)N, chunk_bytes / (P * 8)));

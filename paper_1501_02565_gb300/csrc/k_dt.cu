@@ -32,59 +32,6 @@ namespace epic {
 
 namespace {
 
-constexpr unsigned long long BARRIER_LIMIT_NS = 2000000000ull;  // 2 s
-constexpr int PASS_CHUNK = 8;  // tiles per dispenser step in chunked verification passes
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Sense-free generation barrier over all CTAs of a cooperative launch.  The
-// wait gives up after BARRIER_LIMIT_NS (or as soon as another CTA has given
-// up) and reports EPIC_ERR_TIMEOUT instead of spinning forever.
-__device__ bool grid_sync(RunState *st, unsigned nblocks,
-                          unsigned long long limit_ns = BARRIER_LIMIT_NS) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        GridBarrier *b = &st->barrier;
-        int ok = 1;
-        unsigned g = ld_acquire(&b->gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&b->count, 1u);
-        if (arrived == nblocks - 1) {
-            b->count = 0;
-            __threadfence();
-            st_release(&b->gen, g + 1);
-        } else {
-            unsigned long long t0 = global_ns();
-            while (ld_acquire(&b->gen) == g) {
-                if (get_status(st) == EPIC_ERR_TIMEOUT) { ok = 0; break; }
-                if (global_ns() - t0 > limit_ns) {
-                    set_status(st, EPIC_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Shared-memory solve region.  Region cell (c, r) is image pixel
 // (x0 + c, y0 + r); row pitch P is odd so that a warp reading one column
 // (32 rows) of 8-byte keys touches every bank pair once.

@@ -1,0 +1,540 @@
+// Stage (a) of the interpolator: geodesic assignment map L and distance D
+// (Sec. 3.4 "Geodesic Voronoi diagram"; D_G of Eq. 3 on the 8-connected
+// grid) by row-closure passes on warp-owned tiles.
+//
+// The keys are the same exact fixed-point (D, L) keys as in k_dt.cu, so any
+// order of relaxation steps that ends when no step improves any key reaches
+// the same keys bit for bit; this kernel reaches them with far fewer steps.
+//
+// Tiles are 64 columns x R rows (R <= 32, one frame's rows per tile from its
+// tile rule); each warp is an independent worker that takes whole tiles from
+// a counter and solves them in its own shared memory, lane l holding columns
+// 2l and 2l+1.  A tile solve alternates two kinds of pass:
+//
+//   down  rows top to bottom: row y takes the three candidates from the row
+//         above (already final in this pass), then is closed along itself --
+//         every pixel takes the best of its row neighbours' keys plus the
+//         exact axis steps, repeated until nothing changes -- so that after
+//         the pass every pixel holds its best key over all paths that never
+//         move up;
+//   up    the same from the bottom row upwards.
+//
+// Per-row flags record which constraints may be violated: a row must be
+// stepped in a down pass only if the row above changed since it was last
+// stepped downwards, or if its own ring neighbours or seeds demand it (and
+// likewise upwards).  A tile is solved when every flag is clear; no pass is
+// run only to confirm.
+//
+// One launch holds the whole relaxation (a cooperative launch, every CTA
+// resident):
+//   phase 1  every tile is solved from its own seeds, with unreached
+//            neighbours around it;
+//   phase 2  repeated passes: a tile whose neighbour tiles were written in
+//            the previous pass (or this one) loads itself and the ring of
+//            pixels around it, sets the flags of the rows its ring can
+//            improve, and re-solves if any; the passes end when no tile
+//            changed, i.e. no step improves any key anywhere.  Passes are
+//            separated by the bounded grid barrier.
+#include "epic_internal.cuh"
+
+namespace epic {
+
+namespace {
+
+constexpr int RT_COLS = 64;   // tile width: two columns per lane
+constexpr int RT_WARPS = 4;   // warps (tile workers) per CTA
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// One warp's tile in shared memory.  Row r is image row y0 - 1 + r, so rows
+// 0 and R + 1 are the ring rows above and below; KL/KR are the ring columns
+// x0 - 1 and x0 + 64 of every row.  Lane l reads its two keys of a row with
+// one 16-byte access (a row is 512 bytes: conflict-free).
+template <int MAXR>
+struct WarpTile {
+    pkey_t K[MAXR + 2][RT_COLS];
+    unsigned h[MAXR + 2][RT_COLS];
+    pkey_t KL[MAXR + 2], KR[MAXR + 2];
+    unsigned hL[MAXR + 2], hR[MAXR + 2];
+};
+
+__device__ __forceinline__ pkey_t kmin(pkey_t a, pkey_t b) { return b < a ? b : a; }
+
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
+    const unsigned lo = __reduce_or_sync(FULL, (unsigned)x);
+    const unsigned hi = __reduce_or_sync(FULL, (unsigned)(x >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Tile geometry of one solve.
+struct TileGeo {
+    int x0, y0;     // image origin
+    int wv, rv;     // valid columns (<= 64) and rows (<= R)
+    bool outa, outb;  // this lane's columns lie outside the image
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const PairDev &P, int tx, int ty, int lane) {
+    TileGeo g;
+    g.x0 = tx * RT_COLS;
+    g.y0 = ty * P.tile_h;
+    g.wv = min(RT_COLS, P.W - g.x0);
+    g.rv = min(P.tile_h, P.H - g.y0);
+    g.outa = 2 * lane >= g.wv;
+    g.outb = 2 * lane + 1 >= g.wv;
+    return g;
+}
+
+// The upstream row yu as seen by this lane: its two keys and half-costs and
+// those of the columns on either side (a neighbour lane's, or the ring).
+struct Up {
+    pkey_t Pa, Pb, lK, rK;
+    unsigned pha, phb, lh, rh;
+};
+
+template <int MAXR>
+__device__ __forceinline__ void load_up(const WarpTile<MAXR> &T, int yu, int lane, Up &u) {
+    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[yu][2 * lane]);
+    const uint2 hh = *reinterpret_cast<const uint2 *>(&T.h[yu][2 * lane]);
+    u.Pa = kk.x;
+    u.Pb = kk.y;
+    u.pha = hh.x;
+    u.phb = hh.y;
+}
+
+template <int MAXR>
+__device__ __forceinline__ void neighbours_up(const WarpTile<MAXR> &T, int yu, int lane, Up &u) {
+    const pkey_t l = __shfl_up_sync(FULL, u.Pb, 1);
+    const unsigned lh = __shfl_up_sync(FULL, u.phb, 1);
+    const pkey_t r = __shfl_down_sync(FULL, u.Pa, 1);
+    const unsigned rh = __shfl_down_sync(FULL, u.pha, 1);
+    u.lK = lane == 0 ? T.KL[yu] : l;
+    u.lh = lane == 0 ? T.hL[yu] : lh;
+    u.rK = lane == 31 ? T.KR[yu] : r;
+    u.rh = lane == 31 ? T.hR[yu] : rh;
+}
+
+// Best keys of this lane's two pixels of a row (keys Ka, Kb, half-costs ha,
+// hb) over their current keys and the three candidates each from row u.
+__device__ __forceinline__ void from_up(const Up &u, pkey_t Ka, pkey_t Kb, unsigned ha,
+                                        unsigned hb, pkey_t &na, pkey_t &nb) {
+    na = kmin(Ka, step_key(u.Pa, step_axis(ha, u.pha)));
+    na = kmin(na, step_key(u.lK, step_diag(ha, u.lh)));
+    na = kmin(na, step_key(u.Pb, step_diag(ha, u.phb)));
+    nb = kmin(Kb, step_key(u.Pb, step_axis(hb, u.phb)));
+    nb = kmin(nb, step_key(u.Pa, step_diag(hb, u.pha)));
+    nb = kmin(nb, step_key(u.rK, step_diag(hb, u.rh)));
+}
+
+// Step row y from the upstream row (registers u, already with neighbours):
+// three candidates per pixel, then the closure along the row (ring columns
+// fixed).  Writes the row back if it changed; returns whether it did.  On
+// return u holds row y (for the next row of the pass).
+template <int MAXR>
+__device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, const TileGeo &g,
+                                         Up &u) {
+    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[y][2 * lane]);
+    const uint2 hh = *reinterpret_cast<const uint2 *>(&T.h[y][2 * lane]);
+    const unsigned ha = hh.x, hb = hh.y;
+    pkey_t na, nb;
+    from_up(u, kk.x, kk.y, ha, hb, na, nb);
+    if (g.outa) na = KEY_INF;
+    if (g.outb) nb = KEY_INF;
+    // closure along the row: each lane sweeps its pair left to right and back
+    // with its neighbours' keys of the previous round, until a round changes
+    // nothing anywhere (at most one round per two columns, plus one)
+    const unsigned hl0 = __shfl_up_sync(FULL, hb, 1);
+    const unsigned hr0 = __shfl_down_sync(FULL, ha, 1);
+    const unsigned hl = lane == 0 ? T.hL[y] : hl0;
+    const unsigned hr = lane == 31 ? T.hR[y] : hr0;
+    const pkey_t ringl = T.KL[y], ringr = T.KR[y];
+    const unsigned long long wl = step_axis(hl, ha), wab = step_axis(ha, hb), wr = step_axis(hb, hr);
+    for (int round = 0; round <= RT_COLS / 2 + 1; ++round) {
+        pkey_t left = __shfl_up_sync(FULL, nb, 1);
+        pkey_t right = __shfl_down_sync(FULL, na, 1);
+        if (lane == 0) left = ringl;
+        if (lane == 31) right = ringr;
+        pkey_t a2 = kmin(na, step_key(left, wl));
+        pkey_t b2 = kmin(nb, step_key(a2, wab));
+        b2 = kmin(b2, step_key(right, wr));
+        a2 = kmin(a2, step_key(b2, wab));
+        if (g.outa) a2 = KEY_INF;
+        if (g.outb) b2 = KEY_INF;
+        const bool ch = (a2 != na) | (b2 != nb);
+        na = a2;
+        nb = b2;
+        if (!__any_sync(FULL, ch)) break;
+    }
+    const bool changed = __any_sync(FULL, (na != kk.x) | (nb != kk.y));
+    if (changed) *reinterpret_cast<ulonglong2 *>(&T.K[y][2 * lane]) = make_ulonglong2(na, nb);
+    u.Pa = na;
+    u.Pb = nb;
+    u.pha = ha;
+    u.phb = hb;
+    return changed;
+}
+
+// Down and up passes over rows 1..rv until every flag is clear.  forD bit r:
+// row r changed since row r + 1 was last stepped downwards (forU: upwards,
+// row r - 1); selfD / selfU bit r: row r must be stepped in the next down /
+// up pass for its own sake (seeds, ring neighbours).  Returns the mask of
+// rows that changed.
+template <int MAXR>
+__device__ unsigned long long tile_passes(WarpTile<MAXR> &T, int lane, const TileGeo &g,
+                                          unsigned long long forD, unsigned long long forU,
+                                          unsigned long long selfD, unsigned long long selfU,
+                                          RunState *st) {
+    const int rv = g.rv;
+    const unsigned long long ring = 1ull | (1ull << (rv + 1));
+    unsigned long long modified = 0;
+    // each pass that changes a row undoes one turn of some shortest path, and
+    // a path in the tile has fewer turns than pixels
+    const int cap = 2 + RT_COLS * rv;
+    for (int pass = 0;; ++pass) {
+        // a ring row is never stepped, so what it would consume is dropped
+        forD &= ~((1ull << rv) | ring);
+        forU &= ~(2ull | ring);
+        if ((forD | forU | selfD | selfU) == 0) break;
+        if (pass >= cap) {
+            if (lane == 0) set_status(st, EPIC_ERR_NOT_CONVERGED);
+            break;
+        }
+        const bool down = (pass & 1) == 0;
+        Up u;
+        int have = -1;   // row whose values u holds
+        for (int i = 1; i <= rv; ++i) {
+            const int y = down ? i : rv + 1 - i;
+            const int yu = down ? y - 1 : y + 1;
+            unsigned long long &fl = down ? forD : forU;
+            unsigned long long &sf = down ? selfD : selfU;
+            if (!(((fl >> yu) | (sf >> y)) & 1ull)) continue;
+            fl &= ~(1ull << yu);
+            sf &= ~(1ull << y);
+            if (have != yu) load_up(T, yu, lane, u);
+            neighbours_up(T, yu, lane, u);
+            if (row_step(T, y, lane, g, u)) {
+                forD |= 1ull << y;
+                forU |= 1ull << y;
+                modified |= 1ull << y;
+            }
+            have = y;
+        }
+    }
+    return modified;
+}
+
+// Can this lane read (write) its two cells of image row gy with one vector
+// access?  The keys (arena, 256-byte aligned) need an even offset; the
+// caller's cost map also an 8-byte-aligned base.
+__device__ __forceinline__ bool row_vec_ok(int gy, int W) { return ((gy * (long long)W) & 1) == 0; }
+__device__ __forceinline__ bool cost_vec_ok(const PairDev &P, int gy) {
+    return row_vec_ok(gy, P.W) && ((uintptr_t)P.C & 7) == 0;
+}
+
+// Write rows `rows` (bit r = tile row r) of the tile back to the key map.
+template <int MAXR>
+__device__ void write_rows(const PairDev &P, const WarpTile<MAXR> &T, const TileGeo &g,
+                           unsigned long long rows, int lane) {
+    const int c = 2 * lane;
+    while (rows) {
+        const int r = __ffsll((long long)rows) - 1;
+        rows &= rows - 1;
+        const int gy = g.y0 + r - 1;
+        pkey_t *dst = P.keys + (size_t)gy * P.W + g.x0 + c;
+        const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[r][c]);
+        if (c + 1 < g.wv && row_vec_ok(gy, P.W)) {
+            *reinterpret_cast<ulonglong2 *>(dst) = kk;
+        } else {
+            if (c < g.wv) dst[0] = kk.x;
+            if (c + 1 < g.wv) dst[1] = kk.y;
+        }
+    }
+}
+
+// Phase 1: solve tile (tx, ty) from its own seeds.  A tile without seeds is
+// written unreached and stamped "never written" (-1), so that in the first
+// pass its seedless neighbours skip it.
+template <int MAXR>
+__device__ void fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T, int lane,
+                           RunState *st) {
+    const TileGeo g = tile_geo(P, tx, ty, lane);
+    const int c = 2 * lane;
+    const int s0 = P.tile_start[t], s1 = P.tile_start[t + 1];
+    if (s0 == s1) {
+        const unsigned long long all = ((1ull << g.rv) - 1) << 1;
+        for (int r = 1; r <= g.rv; ++r)
+            *reinterpret_cast<ulonglong2 *>(&T.K[r][c]) = make_ulonglong2(KEY_INF, KEY_INF);
+        __syncwarp();
+        write_rows(P, T, g, all, lane);
+        if (lane == 0) P.tile_stamp[t] = -1;
+        __syncwarp();
+        return;
+    }
+    bool bad = false;
+    for (int r = 0; r <= g.rv + 1; ++r) {
+        *reinterpret_cast<ulonglong2 *>(&T.K[r][c]) = make_ulonglong2(KEY_INF, KEY_INF);
+        uint2 hh = make_uint2(0u, 0u);
+        if (r >= 1 && r <= g.rv) {
+            const int gy = g.y0 + r - 1;
+            const float *src = P.C + (size_t)gy * P.W + g.x0 + c;
+            if (c + 1 < g.wv && cost_vec_ok(P, gy)) {
+                const float2 cc = __ldg(reinterpret_cast<const float2 *>(src));
+                hh = make_uint2(half_cost(cc.x, &bad), half_cost(cc.y, &bad));
+            } else {
+                if (c < g.wv) hh.x = half_cost(__ldg(src), &bad);
+                if (c + 1 < g.wv) hh.y = half_cost(__ldg(src + 1), &bad);
+            }
+        }
+        *reinterpret_cast<uint2 *>(&T.h[r][c]) = hh;
+    }
+    for (int r = lane; r < g.rv + 2; r += 32) {
+        T.KL[r] = KEY_INF;
+        T.KR[r] = KEY_INF;
+        T.hL[r] = 0u;
+        T.hR[r] = 0u;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) set_status(st, EPIC_ERR_INVALID);
+    __syncwarp();
+    unsigned long long seeded = 0;
+    for (int s = s0 + lane; s < s1; s += 32) {
+        const int m = P.tile_seeds[s];
+        const float4 mt = __ldg(P.matches + m);
+        const int px = (int)floorf(mt.x + 0.5f) - g.x0;
+        const int py = (int)floorf(mt.y + 0.5f) - g.y0;
+        if (px >= 0 && px < g.wv && py >= 0 && py < g.rv) {
+            atomicMin(&T.K[py + 1][px], make_key(P.seed_init ? P.seed_init[m] : 0ull, (unsigned)m));
+            seeded |= 1ull << (py + 1);
+        }
+    }
+    seeded = warp_or64(seeded);
+    __syncwarp();
+    tile_passes(T, lane, g, seeded, seeded, seeded, 0ull, st);
+    __syncwarp();
+    write_rows(P, T, g, ((1ull << g.rv) - 1) << 1, lane);
+    __threadfence();
+    if (lane == 0) P.tile_stamp[t] = 0;
+    __syncwarp();
+}
+
+// Phase 2: load tile (tx, ty) with its ring from the current key map, set
+// the flags of the rows the ring can improve and re-solve.  Returns whether
+// any key of the tile changed (then it was written back and stamped `stamp`).
+template <int MAXR>
+__device__ bool resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T,
+                             int lane, RunState *st, int stamp) {
+    const TileGeo g = tile_geo(P, tx, ty, lane);
+    const int c = 2 * lane;
+    bool bad = false;
+    // keys of other tiles may be rewritten during the launch: read through L2
+    for (int r = 0; r <= g.rv + 1; ++r) {
+        const int gy = g.y0 + r - 1;
+        ulonglong2 kk = make_ulonglong2(KEY_INF, KEY_INF);
+        uint2 hh = make_uint2(0u, 0u);
+        if (gy >= 0 && gy < P.H) {
+            const size_t o = (size_t)gy * P.W + g.x0 + c;
+            if (c + 1 < g.wv && cost_vec_ok(P, gy)) {
+                kk = __ldcg(reinterpret_cast<const ulonglong2 *>(P.keys + o));
+                const float2 cc = __ldg(reinterpret_cast<const float2 *>(P.C + o));
+                hh = make_uint2(half_cost(cc.x, &bad), half_cost(cc.y, &bad));
+            } else {
+                if (c < g.wv) {
+                    kk.x = __ldcg(P.keys + o);
+                    hh.x = half_cost(__ldg(P.C + o), &bad);
+                }
+                if (c + 1 < g.wv) {
+                    kk.y = __ldcg(P.keys + o + 1);
+                    hh.y = half_cost(__ldg(P.C + o + 1), &bad);
+                }
+            }
+        }
+        *reinterpret_cast<ulonglong2 *>(&T.K[r][c]) = kk;
+        *reinterpret_cast<uint2 *>(&T.h[r][c]) = hh;
+    }
+    for (int r = lane; r < g.rv + 2; r += 32) {
+        const int gy = g.y0 + r - 1;
+        const bool row_in = gy >= 0 && gy < P.H;
+        pkey_t kl = KEY_INF, kr = KEY_INF;
+        unsigned hl = 0u, hr = 0u;
+        if (row_in && g.x0 > 0) {
+            const size_t o = (size_t)gy * P.W + g.x0 - 1;
+            kl = __ldcg(P.keys + o);
+            hl = half_cost(__ldg(P.C + o), &bad);
+        }
+        if (row_in && g.x0 + RT_COLS < P.W) {
+            const size_t o = (size_t)gy * P.W + g.x0 + RT_COLS;
+            kr = __ldcg(P.keys + o);
+            hr = half_cost(__ldg(P.C + o), &bad);
+        }
+        T.KL[r] = kl;
+        T.KR[r] = kr;
+        T.hL[r] = hl;
+        T.hR[r] = hr;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) set_status(st, EPIC_ERR_INVALID);
+    __syncwarp();
+    // which rows can a ring pixel improve?  The top row from ring row 0 (a
+    // down step of row 1), the bottom row from ring row rv + 1 (an up step
+    // of row rv); the end columns of row r from the ring column in rows
+    // r - 1 and r (a down step) and r + 1 (an up step).
+    unsigned long long selfD = 0, selfU = 0;
+    {
+        Up u;
+        pkey_t na, nb;
+        load_up(T, 0, lane, u);
+        neighbours_up(T, 0, lane, u);
+        const ulonglong2 k1 = *reinterpret_cast<const ulonglong2 *>(&T.K[1][c]);
+        const uint2 h1 = *reinterpret_cast<const uint2 *>(&T.h[1][c]);
+        from_up(u, k1.x, k1.y, h1.x, h1.y, na, nb);
+        const bool top = (!g.outa && na < k1.x) || (!g.outb && nb < k1.y);
+        load_up(T, g.rv + 1, lane, u);
+        neighbours_up(T, g.rv + 1, lane, u);
+        const ulonglong2 kb = *reinterpret_cast<const ulonglong2 *>(&T.K[g.rv][c]);
+        const uint2 hb = *reinterpret_cast<const uint2 *>(&T.h[g.rv][c]);
+        from_up(u, kb.x, kb.y, hb.x, hb.y, na, nb);
+        const bool bot = (!g.outa && na < kb.x) || (!g.outb && nb < kb.y);
+        if (__any_sync(FULL, top)) selfD |= 2ull;
+        if (__any_sync(FULL, bot)) selfU |= 1ull << g.rv;
+    }
+    {
+        // lane r - 1 looks at row r's end columns (rv <= 32 rows)
+        const int r = lane + 1;
+        bool d = false, up = false;
+        if (r <= g.rv) {
+            const pkey_t k0 = T.K[r][0];
+            const unsigned h0 = T.h[r][0];
+            d |= step_key(T.KL[r - 1], step_diag(h0, T.hL[r - 1])) < k0;
+            d |= step_key(T.KL[r], step_axis(h0, T.hL[r])) < k0;
+            up |= step_key(T.KL[r + 1], step_diag(h0, T.hL[r + 1])) < k0;
+            if (g.wv == RT_COLS) {
+                const pkey_t k1 = T.K[r][RT_COLS - 1];
+                const unsigned h1 = T.h[r][RT_COLS - 1];
+                d |= step_key(T.KR[r - 1], step_diag(h1, T.hR[r - 1])) < k1;
+                d |= step_key(T.KR[r], step_axis(h1, T.hR[r])) < k1;
+                up |= step_key(T.KR[r + 1], step_diag(h1, T.hR[r + 1])) < k1;
+            }
+        }
+        selfD |= (unsigned long long)__ballot_sync(FULL, d) << 1;
+        selfU |= (unsigned long long)__ballot_sync(FULL, up) << 1;
+    }
+    if ((selfD | selfU) == 0) return false;
+    const unsigned long long mod = tile_passes(T, lane, g, 0ull, 0ull, selfD, selfU, st);
+    if (mod == 0) return false;
+    __syncwarp();
+    write_rows(P, T, g, mod, lane);
+    __threadfence();
+    if (lane == 0) P.tile_stamp[t] = stamp;
+    __syncwarp();
+    return true;
+}
+
+__device__ __forceinline__ int take_tile(unsigned *dispenser, int lane) {
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(dispenser, 1u);
+    return __shfl_sync(FULL, t, 0);
+}
+
+template <int MAXR>
+__global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *__restrict__ ap) {
+    const BatchArgs a = *ap;
+    RunState *st = a.state;
+    if (get_status(st) != 0) return;  // same decision in every CTA
+    // a launch replayed for a smaller batch may have more CTAs than tile
+    // workers need: the extra CTAs leave at once and the barrier counts only
+    // the others
+    const unsigned nblocks =
+        min(gridDim.x, (unsigned)((a.total_tiles + RT_WARPS - 1) / RT_WARPS));
+    if (blockIdx.x >= nblocks) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    WarpTile<MAXR> &T = reinterpret_cast<WarpTile<MAXR> *>(smem)[threadIdx.x >> 5];
+
+    // phase 1
+    for (int t = take_tile(&st->work[3], lane); t < a.total_tiles;
+         t = take_tile(&st->work[3], lane)) {
+        const int pi = find_pair(a.tile_base, a.npairs, t);
+        const PairDev &P = a.pairs[pi];
+        const int lt = t - a.tile_base[pi];
+        fresh_tile(P, lt, lt % P.tiles_x, lt / P.tiles_x, T, lane, st);
+    }
+    if (!grid_sync(st, nblocks)) return;
+
+    // phase 2
+    for (int pass = 0;; ++pass) {
+        if (pass >= a.max_passes) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                set_status(st, EPIC_ERR_NOT_CONVERGED);
+                st->passes = pass;
+            }
+            return;
+        }
+        unsigned *cnt = &st->changed[pass % 3];
+        unsigned *disp = &st->work[pass % 3];
+        for (int t = take_tile(disp, lane); t < a.total_tiles; t = take_tile(disp, lane)) {
+            const int pi = find_pair(a.tile_base, a.npairs, t);
+            const PairDev &P = a.pairs[pi];
+            const int lt = t - a.tile_base[pi];
+            const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
+            // lanes 0-7 read the eight neighbour stamps: a tile is looked at
+            // only if a neighbour was written since the previous pass began
+            bool nb = false;
+            if (lane < 8) {
+                const int k = lane;
+                const int x = tx + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
+                const int y = ty + (k < 3 ? -1 : k < 5 ? 0 : 1);
+                nb = x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
+                     __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass;
+            }
+            if (!__any_sync(FULL, nb)) continue;
+            if (resolve_tile(P, lt, tx, ty, T, lane, st, pass + 1) && lane == 0)
+                atomicAdd(cnt, 1u);
+        }
+        if (!grid_sync(st, nblocks)) return;
+        const unsigned dirty = ld_acquire(cnt);
+        // the counters of pass - 1 (== pass + 2 mod 3) were last used before
+        // this barrier; clear them for pass + 2
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->changed[(pass + 2) % 3] = 0;
+            st->work[(pass + 2) % 3] = 0;
+        }
+        if (dirty == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->passes = pass + 1;
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+size_t relax_smem_bytes(int max_rows) {
+    return RT_WARPS * (max_rows <= 16 ? sizeof(WarpTile<16>) : sizeof(WarpTile<32>));
+}
+
+cudaError_t launch_relax(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
+                         int max_rows, bool fixed_grid, int *grid_used) {
+    if (max_rows < 1 || max_rows > 32) return cudaErrorInvalidValue;
+    void (*kernel)(const BatchArgs *) = max_rows <= 16 ? relax_kernel<16> : relax_kernel<32>;
+    const size_t smem = relax_smem_bytes(max_rows);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, RT_WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = per_sm * lc.num_sms;
+    const int need = (a.total_tiles + RT_WARPS - 1) / RT_WARPS;
+    if (!fixed_grid && grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(RT_WARPS * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = lc.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (grid_used) *grid_used = grid;
+    return cudaLaunchKernelEx(&cfg, kernel, dev);
+}
+
+}  // namespace epic

@@ -2,15 +2,26 @@
 //
 // Every pixel p takes the model of its cell's match m = L(p):
 //     flow(p) = F(p) - p = c_m + B_m (p - p_m).
-// A work item is WRITEOUT_CHUNK consecutive pixels of one pair; a thread
-// handles four consecutive pixels with two 16-byte key loads and two 16-byte
-// streaming flow stores.  The model table (32 bytes per match) is small and
-// read through the read-only path, where it stays cache resident.
+// The kernel is a single pass over the packed keys (8 B in) and the flow
+// (8 B out) of every pixel of the batch, so it is bound by HBM bandwidth:
+//   * a work item is WRITEOUT_CHUNK pixels of one pair, and each CTA takes a
+//     contiguous run of items, so the pair of an item is found once per run
+//     and then followed forward (no search per item);
+//   * a thread handles eight consecutive pixels: its four 16-byte key loads
+//     are all issued before the first model gather, so each thread keeps 64
+//     bytes of loads in flight;
+//   * the model table (32 bytes per match, a few MB for a batch) is read
+//     through the read-only path, where it stays cache resident; flows are
+//     written with streaming 16-byte stores.
 #include "epic_internal.cuh"
 
 namespace epic {
 
 namespace {
+
+constexpr int WO_THREADS = 128;
+constexpr int WO_PER_THREAD = WRITEOUT_CHUNK / WO_THREADS;
+static_assert(WO_PER_THREAD == 8, "eight pixels per thread");
 
 __device__ __forceinline__ float2 apply(const float4 *models, unsigned m, int n, int x,
                                         int y) {
@@ -21,44 +32,57 @@ __device__ __forceinline__ float2 apply(const float4 *models, unsigned m, int n,
     return make_float2(r0.x + r0.z * dx + r0.w * dy, r0.y + r1.x * dx + r1.y * dy);
 }
 
-__device__ __forceinline__ void st_stream(float4 *p, float4 v) { __stcs(p, v); }
-
-__global__ void __launch_bounds__(256) writeout_kernel(const BatchArgs *__restrict__ ap) {
-    const BatchArgs a = *ap;
-    RunState *st = a.state;
+__global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *__restrict__ ap) {
+    RunState *st = ap->state;
     if (get_status(st) != 0) return;
-    constexpr int PER_THREAD = WRITEOUT_CHUNK / 256;
-    static_assert(PER_THREAD == 4, "four pixels per thread");
-    for (int c = blockIdx.x; c < a.total_chunks; c += gridDim.x) {
-        const int pi = find_pair(a.chunk_base, a.npairs, c);
-        const PairDev &P = a.pairs[pi];
-        const long long npix = (long long)P.H * P.W;
-        const long long p0 = (long long)(c - a.chunk_base[pi]) * WRITEOUT_CHUNK +
-                             (long long)threadIdx.x * PER_THREAD;
+    const PairDev *pairs = ap->pairs;
+    const int *chunk_base = ap->chunk_base;
+    const int npairs = ap->npairs, total = ap->total_chunks;
+    // contiguous runs of items per CTA
+    const int per = (total + gridDim.x - 1) / gridDim.x;
+    const int c0 = blockIdx.x * per, c1 = min(total, c0 + per);
+    if (c0 >= c1) return;
+    int pi = find_pair(chunk_base, npairs, c0);
+    int next_base = __ldg(chunk_base + pi + 1);
+    for (int c = c0; c < c1; ++c) {
+        while (c >= next_base) {
+            ++pi;
+            next_base = __ldg(chunk_base + pi + 1);
+        }
+        const PairDev &P = pairs[pi];
+        const int W = P.W, N = P.N;
+        const long long npix = (long long)P.H * W;
+        const long long p0 = (long long)(c - __ldg(chunk_base + pi)) * WRITEOUT_CHUNK +
+                             (long long)threadIdx.x * WO_PER_THREAD;
         if (p0 >= npix) continue;
-        int y = (int)(p0 / P.W), x = (int)(p0 - (long long)y * P.W);
-        if (P.flow_vec_ok && p0 + 3 < npix) {
-            const ulonglong2 k01 = __ldg(reinterpret_cast<const ulonglong2 *>(P.keys + p0));
-            const ulonglong2 k23 = __ldg(reinterpret_cast<const ulonglong2 *>(P.keys + p0 + 2));
-            const pkey_t ks[4] = {k01.x, k01.y, k23.x, k23.y};
-            float f[8];
+        const pkey_t *keys = P.keys;
+        const float4 *models = P.models;
+        float *flow = P.flow;
+        int y = (int)(p0 / W), x = (int)(p0 - (long long)y * W);
+        if (P.flow_vec_ok && p0 + WO_PER_THREAD <= npix) {
+            ulonglong2 k[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                k[i] = __ldcs(reinterpret_cast<const ulonglong2 *>(keys + p0) + i);
+            float4 o[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                float2 v = apply(P.models, key_label(ks[i]), P.N, x, y);
-                f[2 * i] = v.x;
-                f[2 * i + 1] = v.y;
-                if (++x == P.W) { x = 0; ++y; }
+                const float2 v0 = apply(models, key_label(k[i].x), N, x, y);
+                if (++x == W) { x = 0; ++y; }
+                const float2 v1 = apply(models, key_label(k[i].y), N, x, y);
+                if (++x == W) { x = 0; ++y; }
+                o[i] = make_float4(v0.x, v0.y, v1.x, v1.y);
             }
-            float4 *out = reinterpret_cast<float4 *>(P.flow + 2 * p0);
-            st_stream(out, make_float4(f[0], f[1], f[2], f[3]));
-            st_stream(out + 1, make_float4(f[4], f[5], f[6], f[7]));
+            float4 *out = reinterpret_cast<float4 *>(flow + 2 * p0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) __stcs(out + i, o[i]);
         } else {
-            for (int i = 0; i < 4 && p0 + i < npix; ++i) {
-                const pkey_t k = __ldg(P.keys + p0 + i);
-                float2 v = apply(P.models, key_label(k), P.N, x, y);
-                P.flow[2 * (p0 + i)] = v.x;
-                P.flow[2 * (p0 + i) + 1] = v.y;
-                if (++x == P.W) { x = 0; ++y; }
+            for (int i = 0; i < WO_PER_THREAD && p0 + i < npix; ++i) {
+                const pkey_t kk = __ldg(keys + p0 + i);
+                const float2 v = apply(models, key_label(kk), N, x, y);
+                flow[2 * (p0 + i)] = v.x;
+                flow[2 * (p0 + i) + 1] = v.y;
+                if (++x == W) { x = 0; ++y; }
             }
         }
     }
@@ -68,7 +92,7 @@ __global__ void __launch_bounds__(256) writeout_kernel(const BatchArgs *__restri
 
 cudaError_t launch_writeout(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
     (void)a;
-    writeout_kernel<<<lc.num_sms * 8, 256, 0, lc.stream>>>(dev);
+    writeout_kernel<<<lc.num_sms * 16, WO_THREADS, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

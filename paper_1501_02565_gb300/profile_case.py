@@ -1,8 +1,9 @@
 """A short, fixed launch sequence for kernel profilers.
 
---what interp (default): the batched interpolator on `--batch`
-Sintel-shaped synthetic pairs (1024x436, N = 5000, K = 100): `--warmup`
-runs, then `--runs` runs, then the device status is checked.  10 kernels per
+--what interp (default): the batched interpolator on `--batch` synthetic
+pairs of `--config` (2: Sintel-shaped 1024x436, N = 5000, K = 100; 4: the
+mixed-size batch): `--warmup` runs, then `--runs` runs, then the device
+status is checked.  10 kernels per
 run (20 with --prune).
 --what gradcost: the image-gradient cost map of `--batch` synthetic frames,
 one launch per run.
@@ -26,7 +27,10 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--runs", type=int, default=1)
-    ap.add_argument("--tile", default="64,32,8", help="tile_w,tile_h,apron of the relaxation")
+    ap.add_argument("--tile", default="64,16,0", help="tile_w,tile_h,apron of the relaxation")
+    ap.add_argument("--sweep", type=int, default=2, help="relaxation schedule (0, 1, 2)")
+    ap.add_argument("--config", type=int, default=2,
+                    help="2: Sintel-shaped pairs; 4: the mixed-size batch")
     ap.add_argument("--prune", action="store_true", help="consistency pruning (two passes)")
     ap.add_argument("--what", default="interp", choices=("interp", "gradcost", "refine"))
     args = ap.parse_args(argv)
@@ -38,10 +42,12 @@ def main(argv=None):
     from .native import EpicInterp
 
     tw, th, apron = (int(x) for x in args.tile.split(","))
-    pairs = [synth.config_pair(2, i) for i in range(args.batch)]
+    pairs = [synth.config_pair(args.config, i) for i in range(args.batch)]
     dev = torch.device("cuda", 0)
     eng = EpicInterp(0, max_pairs=len(pairs), tile_w=tw, tile_h=th, apron=apron,
-                     prune=int(args.prune))
+                     sweep=args.sweep, prune=int(args.prune),
+                     max_H=max(p.H for p in pairs), max_W=max(p.W for p in pairs),
+                     max_N=max(p.N for p in pairs), max_K=max(p.K for p in pairs))
     items = [(torch.from_numpy(p.C).to(dev), torch.from_numpy(p.matches).to(dev), p.K, p.a,
               torch.empty((p.H, p.W, 2), dtype=torch.float32, device=dev)) for p in pairs]
     torch.cuda.synchronize()

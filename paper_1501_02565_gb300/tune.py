@@ -17,9 +17,14 @@ from __future__ import annotations
 import json
 import os
 
-# (tile_w, tile_h, apron, sweep): the region (tile + 2 apron) stays within
-# shared memory at 256 threads per CTA
-CANDIDATES = (
+# (tile_w, tile_h, apron, sweep).  sweep 2: the row-closure passes on warp
+# tiles of 64 x tile_h (the interpolator's default relaxation); the library
+# uses them only when every rule asks for them, so a rule set is tuned from
+# one family at a time.
+CANDIDATES = ((64, 32, 0, 2), (64, 24, 0, 2), (64, 16, 0, 2))
+# sweep 0 / 1: the sweep schedules of the tiled relaxation with an apron
+# (region = tile + 2 apron within shared memory at 256 threads per CTA)
+SWEEP_CANDIDATES = (
     (64, 32, 4, 0), (32, 32, 4, 0), (64, 32, 0, 0), (64, 32, 8, 0), (48, 48, 8, 0),
     (64, 64, 8, 0), (96, 32, 4, 0), (128, 32, 4, 0), (32, 16, 2, 0), (128, 64, 8, 0),
     (64, 32, 8, 1), (48, 48, 8, 1), (32, 32, 4, 1),
@@ -44,9 +49,17 @@ def group_by_class(pairs):
     return dict(sorted(groups.items()))
 
 
+# the bound given to the last rule: every larger frame uses it too, so the
+# handle's configured tile never applies (and a captured launch sequence is
+# sized for the tuned tiles alone)
+ALL_SIZES = 1 << 62
+
+
 def rules_from_choice(choice):
-    """{class bound: (tw, th, apron[, sweep])} -> sorted rule list for the library."""
-    return [(bound, *choice[bound]) for bound in sorted(choice)]
+    """{class bound: (tw, th, apron[, sweep])} -> sorted rule list for the
+    library; the largest class's rule also covers every larger frame."""
+    bounds = sorted(choice)
+    return [(ALL_SIZES if i == len(bounds) - 1 else b, *choice[b]) for i, b in enumerate(bounds)]
 
 
 def time_candidate(pairs, tile, device=0, reps=3, warmup=2):

@@ -35,17 +35,46 @@ def test_small_random_cases_several_tiles_ragged_tail(seed):
 
 
 @pytest.mark.parametrize("tile", [(8, 8, 0, 0), (16, 8, 3, 1), (32, 32, 0, 0), (64, 32, 4, 1),
-                                  (128, 64, 8, 0), (256, 16, 8, 0), (256, 16, 8, 1)])
+                                  (128, 64, 8, 0), (256, 16, 8, 0), (256, 16, 8, 1),
+                                  (64, 32, 0, 2), (64, 16, 0, 2), (64, 7, 0, 2), (64, 1, 0, 2)])
 def test_tile_shapes_give_identical_keys(tile):
-    # every tile shape and sweep schedule reaches the same fixed point bit
-    # for bit (256-wide tiles have more region columns than CTA threads)
+    # every tile shape and relaxation schedule reaches the same fixed point
+    # bit for bit: the sweep schedules of the apron tiles (256-wide tiles
+    # have more region columns than CTA threads) and the row-closure passes
+    # of the 64-column warp tiles (ragged tile rows against the 128 frame rows)
     p = synth.config_pair(1, 1)
     tw, th, ap, sw = tile
     g = run_gpu(p, tile_w=tw, tile_h=th, apron=ap, sweep=sw)
-    base = run_gpu(p, tile_w=64, tile_h=32, apron=4)
+    base = run_gpu(p, tile_w=64, tile_h=32, apron=4, sweep=0)
     assert np.array_equal(g["L"], base["L"])
     assert np.array_equal(g["D"], base["D"])
     assert np.array_equal(g["flow"], base["flow"])
+
+
+@pytest.mark.parametrize("shape", [(83, 150), (37, 71), (130, 257), (1, 200), (200, 1)])
+def test_warp_tile_relaxation_matches_sweep_relaxation(shape):
+    # odd widths (unaligned rows: scalar loads), frames narrower than a warp
+    # tile, single rows and columns, and a cost map 4 bytes off its 8-byte
+    # alignment: the warp-tile relaxation gives the same keys as the sweep
+    # schedule, bit for bit
+    import torch
+    from paper_1501_02565_gb300.native import EpicInterp
+    H, W = shape
+    C, M = random_small_case(620 + H, H=H, W=W, N=max(2, min(40, H * W // 60)),
+                             c_lo=0.01, c_hi=1.0)
+    out = []
+    for sweep, offset in ((0, 0), (2, 0), (2, 1)):
+        buf = torch.zeros(H * W + 2, dtype=torch.float32, device="cuda")
+        Ct = buf[offset:offset + H * W].view(H, W)
+        Ct.copy_(torch.from_numpy(C))
+        eng = EpicInterp(0, sweep=sweep, tile_w=64, tile_h=32, apron=4 if sweep == 0 else 0)
+        eng.run(Ct, torch.from_numpy(M).cuda(), 4, 1.0)
+        eng.sync()
+        L, D = eng.get_labels(0, H, W)
+        out.append((L.cpu().numpy(), D.cpu().numpy()))
+        eng.close()
+    for L, D in out[1:]:
+        assert np.array_equal(L, out[0][0]) and np.array_equal(D, out[0][1])
 
 
 def test_hub_graph_searches_outgrow_the_small_tables():
@@ -130,8 +159,10 @@ def test_sparse_seeds_leave_most_tiles_empty():
     C = rng.uniform(0.05, 0.6, (300, 700)).astype(np.float32)
     M = np.array([[10, 12, 12.5, 11.0], [650, 280, 648.0, 281.5], [350, 150, 351.0, 149.0]],
                  np.float32)
-    g, ref, rep = full_parity((C, M), K=3, a=0.02, tile_w=32, tile_h=32, apron=4)
-    _print("sparse", rep)
+    for sweep in (0, 2):
+        g, ref, rep = full_parity((C, M), K=3, a=0.02, tile_w=64 if sweep == 2 else 32,
+                                  tile_h=32, apron=4 if sweep == 0 else 0, sweep=sweep)
+        _print(f"sparse sweep={sweep}", rep)
 
 
 def test_largest_neighbourhood_size():

@@ -17,7 +17,8 @@ def test_size_classes_are_monotone_and_cover_everything():
 
 def test_rules_are_sorted_by_class():
     rules = tune.rules_from_choice({1 << 20: (64, 32, 4), 1 << 16: (32, 16, 2)})
-    assert rules == [(1 << 16, 32, 16, 2), (1 << 20, 64, 32, 4)]
+    # the largest class's rule covers every larger frame as well
+    assert rules == [(1 << 16, 32, 16, 2), (tune.ALL_SIZES, 64, 32, 4)]
 
 
 def test_cache_round_trip(tmp_path):
@@ -31,11 +32,15 @@ def test_cache_round_trip(tmp_path):
 
 
 def test_candidates_are_valid_tiles():
+    # warp tiles: 64 columns, 1..32 rows, no apron
     for tw, th, ap, sw in tune.CANDIDATES:
+        assert sw == 2 and tw == 64 and 1 <= th <= 32 and ap == 0
+    for tw, th, ap, sw in tune.SWEEP_CANDIDATES:
         assert 8 <= tw <= 256 and 8 <= th <= 256 and 0 <= ap <= 64
         assert ap + 1 <= min(tw, th)
         assert sw in (0, 1)
-    assert any(c[3] == 1 for c in tune.CANDIDATES) and any(c[3] == 0 for c in tune.CANDIDATES)
+    assert any(c[3] == 1 for c in tune.SWEEP_CANDIDATES)
+    assert any(c[3] == 0 for c in tune.SWEEP_CANDIDATES)
 
 
 @pytest.mark.gpu
