@@ -135,6 +135,12 @@ class Server:
         self.engine.close()
         return status
 
+    def load(self) -> int:
+        """Device bytes this server has committed: admitted requests plus the
+        ones waiting for admission (what a dispatcher balances on)."""
+        with self.lock:
+            return self.in_use + sum(r._bytes for r in self.pending)
+
     @staticmethod
     def validate(req: Request):
         """Host-side checks of what the device would otherwise report

@@ -131,3 +131,22 @@ def test_streamed_host_batches_match_device_batches():
             for hh, e in zip(h, ex):
                 assert torch.equal(hh[4], e)
     eng.close()
+
+
+def test_dispatcher_over_the_devices_matches_single_runs():
+    # the dispatcher over every visible device (one on this machine): each
+    # request lands on the least-loaded server and its flow is the one a
+    # single run gives
+    import torch
+    from paper_1501_02565_gb300.dispatch import Dispatcher
+    reqs = _requests()[:6]
+    ref = _alone(reqs)
+    d = Dispatcher.on_devices(range(torch.cuda.device_count()), max_batch=4)
+    for r in reqs:
+        d.submit(r)
+    for r in reqs:
+        r.wait(timeout=60)
+    assert all(s == 0 for s in d.stop())
+    assert sum(st["assigned"] for st in d.stats()) == len(reqs)
+    for r, f in zip(reqs, ref):
+        assert np.array_equal(r.flow.numpy(), f), r.rid
