@@ -69,15 +69,15 @@ def warp_bilinear(I, u, v):
     """I [H, W, C] sampled at (x + u, y + v), coordinates clamped to the
     image, bilinear."""
     H, W = I.shape[:2]
-    ys, xs = np.mgrid[0:H, 0:W].astype(u.dtype)
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
     X = np.clip(xs + u, 0.0, W - 1.0)
     Y = np.clip(ys + v, 0.0, H - 1.0)
     x0 = np.minimum(np.floor(X).astype(np.int64), W - 2) if W > 1 else np.zeros_like(X, np.int64)
     y0 = np.minimum(np.floor(Y).astype(np.int64), H - 2) if H > 1 else np.zeros_like(Y, np.int64)
     x1 = np.minimum(x0 + 1, W - 1)
     y1 = np.minimum(y0 + 1, H - 1)
-    ax = (X - x0.astype(X.dtype))[..., None]
-    ay = (Y - y0.astype(Y.dtype))[..., None]
+    ax = (X - x0)[..., None]
+    ay = (Y - y0)[..., None]
     return ((1 - ay) * ((1 - ax) * I[y0, x0] + ax * I[y0, x1]) +
             ay * ((1 - ax) * I[y1, x0] + ax * I[y1, x1]))
 
@@ -124,22 +124,21 @@ def sor(u, v, A11, A12, A22, b1, b2, phi, omega, iterations):
     """Red-black SOR for the update (du, dv) of one fixed-point iteration."""
     H, W = u.shape
     # edge weights: sx between (x, y) and (x + 1, y), sy between (x, y) and (x, y + 1)
-    dt = u.dtype
-    sx = np.zeros((H, W), dt)
-    sy = np.zeros((H, W), dt)
+    sx = np.zeros((H, W))
+    sy = np.zeros((H, W))
     sx[:, :-1] = 0.5 * (phi[:, :-1] + phi[:, 1:])
     sy[:-1, :] = 0.5 * (phi[:-1, :] + phi[1:, :])
-    sl = np.zeros((H, W), dt); sl[:, 1:] = sx[:, :-1]     # edge to the left neighbour
-    su = np.zeros((H, W), dt); su[1:, :] = sy[:-1, :]     # edge to the upper neighbour
+    sl = np.zeros((H, W)); sl[:, 1:] = sx[:, :-1]     # edge to the left neighbour
+    su = np.zeros((H, W)); su[1:, :] = sy[:-1, :]     # edge to the upper neighbour
     S = sx + sl + sy + su
-    du = np.zeros((H, W), dt)
-    dv = np.zeros((H, W), dt)
+    du = np.zeros((H, W))
+    dv = np.zeros((H, W))
     ys, xs = np.mgrid[0:H, 0:W]
     red = (xs + ys) % 2 == 0
 
     def nsum(f):
         """sum over the 4-neighbours q of s_pq * f(q) (zero weight off the image)."""
-        out = np.zeros((H, W), dt)
+        out = np.zeros((H, W))
         out[:, :-1] += sx[:, :-1] * f[:, 1:]
         out[:, 1:] += sl[:, 1:] * f[:, :-1]
         out[:-1, :] += sy[:-1, :] * f[1:, :]
@@ -163,18 +162,15 @@ def sor(u, v, A11, A12, A22, b1, b2, phi, omega, iterations):
     return du, dv
 
 
-def refine(I1, I2, flow, prm: RefineParams = RefineParams(), dtype=np.float64):
+def refine(I1, I2, flow, prm: RefineParams = RefineParams()):
     """Variational refinement of `flow` [H, W, 2] between images I1, I2
-    [H, W, C] (or [H, W]); returns the refined flow.  The arithmetic runs in
-    `dtype`: float64 is the oracle; float32 evaluates the same steps at
-    float32 precision, which the tests use to measure how far float32
-    rounding alone moves the result (the problem's conditioning)."""
-    I1 = np.asarray(I1, dtype)
-    I2 = np.asarray(I2, dtype)
+    [H, W, C] (or [H, W]); returns the refined flow, float64."""
+    I1 = np.asarray(I1, np.float64)
+    I2 = np.asarray(I2, np.float64)
     if I1.ndim == 2:
         I1, I2 = I1[..., None], I2[..., None]
-    u = np.array(flow[..., 0], dtype)
-    v = np.array(flow[..., 1], dtype)
+    u = np.array(flow[..., 0], np.float64)
+    v = np.array(flow[..., 1], np.float64)
     for _ in range(prm.iterations):
         I2w = warp_bilinear(I2, u, v)
         A11, A12, A22, b1, b2, phi = coefficients(I1, I2w, u, v, prm)

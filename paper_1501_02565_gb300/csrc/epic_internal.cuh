@@ -132,6 +132,12 @@ struct PairDev {
     int tma_bw_fresh, tma_bw_again;
     CUtensorMap tm_cost_fresh;
     CUtensorMap tm_cost_again;
+    // TMA staging of the warp tiles (k_relax.cu; tma_warp = 0: plain loads):
+    // boxes of the keys (u64, 68 x (tile_h + 2) from x0 - 2) and of the
+    // costs (float32, 72 x (tile_h + 2) from x0 - 4), tile and ring
+    int tma_warp;
+    CUtensorMap tm_warp_keys;
+    CUtensorMap tm_warp_cost;
 };
 
 struct GridBarrier {

@@ -297,6 +297,37 @@ void encode_cost_maps(PairDev &P) {
     P.tma_cost = 1;
 }
 
+// Tensor maps of the warp-tile relaxation (k_relax.cu): the pair's keys as a
+// W x H array of 8-byte elements with boxes of 68 x (tile_h + 2), and its
+// cost map as float32 with boxes of 72 x (tile_h + 2); both boxes start at
+// an x coordinate that is a multiple of 64 minus 2 (keys) or 4 (costs), so
+// every copy starts on a 16-byte boundary.  Leaves tma_warp = 0 (plain
+// loads) unless both maps can be encoded: 16-byte-aligned bases and row
+// pitches that are multiples of 16 bytes (W even for the keys, W a multiple
+// of 4 for the costs).
+void encode_warp_maps(PairDev &P) {
+    P.tma_warp = 0;
+    if (P.sweep != SWEEP_WARP_TILES) return;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || ((uintptr_t)P.C % 16) != 0 || ((uintptr_t)P.keys % 16) != 0 ||
+        ((size_t)P.W * 4) % 16 != 0 || P.tile_h + 2 > 256)
+        return;
+    const cuuint64_t dims[2] = {(cuuint64_t)P.W, (cuuint64_t)P.H};
+    const cuuint64_t kstr[1] = {(cuuint64_t)P.W * 8};
+    const cuuint64_t cstr[1] = {(cuuint64_t)P.W * 4};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint32_t kbox[2] = {68u, (cuuint32_t)(P.tile_h + 2)};
+    const cuuint32_t cbox[2] = {72u, (cuuint32_t)(P.tile_h + 2)};
+    if (fn(&P.tm_warp_keys, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, P.keys, dims, kstr, kbox, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        fn(&P.tm_warp_cost, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(P.C), dims,
+           cstr, cbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    P.tma_warp = 1;
+}
+
 int validate(epic_interp_t *h, const epic_pair_desc_t &d, int i) {
     char buf[256];
     if (!d.cost_map || !d.matches || !d.flow_out) {
@@ -565,6 +596,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
             P[i].knn_count = reinterpret_cast<int *>(b + L[i].knn_count);
         }
         P[i].info = reinterpret_cast<int *>(b + L[i].info);
+        encode_warp_maps(P[i]);
         if (c.prune) {
             P[i].keep = reinterpret_cast<int *>(b + L[i].keep);
             P[i].pruned = reinterpret_cast<float4 *>(b + L[i].pruned);

@@ -42,20 +42,27 @@ namespace epic {
 namespace {
 
 constexpr int RT_COLS = 64;   // tile width: two columns per lane
-constexpr int RT_WARPS = 4;   // warps (tile workers) per CTA
+constexpr int RT_WARPS = 1;   // warps (tile workers) per CTA
 constexpr unsigned FULL = 0xFFFFFFFFu;
+// shared-memory row pitches, as the TMA boxes land them: keys from column
+// x0 - 2 (68 x 8 bytes; the tile at 2..65, ring columns at 1 and 66) and
+// costs from column x0 - 4 (72 x 4 bytes; the tile at 4..67, ring columns at
+// 3 and 68), so a lane's two keys are one aligned 16-byte access
+constexpr int KP = 68, KO = 2;
+constexpr int CP = 72, CO = 4;
+constexpr unsigned long long TMA_LIMIT_NS = 1000000000ull;  // 1 s
 
 // One warp's tile in shared memory.  Row r is image row y0 - 1 + r, so rows
-// 0 and R + 1 are the ring rows above and below; KL/KR are the ring columns
-// x0 - 1 and x0 + 64 of every row.  Lane l reads its two keys of a row with
-// one 16-byte access (a row is 512 bytes: conflict-free).
+// 0 and R + 1 are the ring rows above and below.  hC holds the costs as
+// staged, then the half-costs (as unsigned bits) after conversion.
 template <int MAXR>
 struct WarpTile {
-    pkey_t K[MAXR + 2][RT_COLS];
-    unsigned h[MAXR + 2][RT_COLS];
-    pkey_t KL[MAXR + 2], KR[MAXR + 2];
-    unsigned hL[MAXR + 2], hR[MAXR + 2];
+    alignas(128) pkey_t K[MAXR + 2][KP];       // TMA destinations are 128-byte aligned
+    alignas(128) unsigned hC[MAXR + 2][CP];
+    unsigned long long bar;   // mbarrier of the warp's TMA copies
 };
+static_assert(sizeof(WarpTile<16>) % 128 == 0 && sizeof(WarpTile<32>) % 128 == 0,
+              "warp tiles stay 128-byte aligned in an array");
 
 __device__ __forceinline__ pkey_t kmin(pkey_t a, pkey_t b) { return b < a ? b : a; }
 
@@ -92,8 +99,8 @@ struct Up {
 
 template <int MAXR>
 __device__ __forceinline__ void load_up(const WarpTile<MAXR> &T, int yu, int lane, Up &u) {
-    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[yu][2 * lane]);
-    const uint2 hh = *reinterpret_cast<const uint2 *>(&T.h[yu][2 * lane]);
+    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[yu][KO + 2 * lane]);
+    const uint2 hh = *reinterpret_cast<const uint2 *>(&T.hC[yu][CO + 2 * lane]);
     u.Pa = kk.x;
     u.Pb = kk.y;
     u.pha = hh.x;
@@ -106,10 +113,10 @@ __device__ __forceinline__ void neighbours_up(const WarpTile<MAXR> &T, int yu, i
     const unsigned lh = __shfl_up_sync(FULL, u.phb, 1);
     const pkey_t r = __shfl_down_sync(FULL, u.Pa, 1);
     const unsigned rh = __shfl_down_sync(FULL, u.pha, 1);
-    u.lK = lane == 0 ? T.KL[yu] : l;
-    u.lh = lane == 0 ? T.hL[yu] : lh;
-    u.rK = lane == 31 ? T.KR[yu] : r;
-    u.rh = lane == 31 ? T.hR[yu] : rh;
+    u.lK = lane == 0 ? T.K[yu][KO - 1] : l;
+    u.lh = lane == 0 ? T.hC[yu][CO - 1] : lh;
+    u.rK = lane == 31 ? T.K[yu][KO + RT_COLS] : r;
+    u.rh = lane == 31 ? T.hC[yu][CO + RT_COLS] : rh;
 }
 
 // Best keys of this lane's two pixels of a row (keys Ka, Kb, half-costs ha,
@@ -131,8 +138,8 @@ __device__ __forceinline__ void from_up(const Up &u, pkey_t Ka, pkey_t Kb, unsig
 template <int MAXR>
 __device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, const TileGeo &g,
                                          Up &u) {
-    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[y][2 * lane]);
-    const uint2 hh = *reinterpret_cast<const uint2 *>(&T.h[y][2 * lane]);
+    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[y][KO + 2 * lane]);
+    const uint2 hh = *reinterpret_cast<const uint2 *>(&T.hC[y][CO + 2 * lane]);
     const unsigned ha = hh.x, hb = hh.y;
     pkey_t na, nb;
     from_up(u, kk.x, kk.y, ha, hb, na, nb);
@@ -143,9 +150,9 @@ __device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, con
     // nothing anywhere (at most one round per two columns, plus one)
     const unsigned hl0 = __shfl_up_sync(FULL, hb, 1);
     const unsigned hr0 = __shfl_down_sync(FULL, ha, 1);
-    const unsigned hl = lane == 0 ? T.hL[y] : hl0;
-    const unsigned hr = lane == 31 ? T.hR[y] : hr0;
-    const pkey_t ringl = T.KL[y], ringr = T.KR[y];
+    const unsigned hl = lane == 0 ? T.hC[y][CO - 1] : hl0;
+    const unsigned hr = lane == 31 ? T.hC[y][CO + RT_COLS] : hr0;
+    const pkey_t ringl = T.K[y][KO - 1], ringr = T.K[y][KO + RT_COLS];
     const unsigned long long wl = step_axis(hl, ha), wab = step_axis(ha, hb), wr = step_axis(hb, hr);
     for (int round = 0; round <= RT_COLS / 2 + 1; ++round) {
         pkey_t left = __shfl_up_sync(FULL, nb, 1);
@@ -164,7 +171,7 @@ __device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, con
         if (!__any_sync(FULL, ch)) break;
     }
     const bool changed = __any_sync(FULL, (na != kk.x) | (nb != kk.y));
-    if (changed) *reinterpret_cast<ulonglong2 *>(&T.K[y][2 * lane]) = make_ulonglong2(na, nb);
+    if (changed) *reinterpret_cast<ulonglong2 *>(&T.K[y][KO + 2 * lane]) = make_ulonglong2(na, nb);
     u.Pa = na;
     u.Pb = nb;
     u.pha = ha;
@@ -239,7 +246,7 @@ __device__ void write_rows(const PairDev &P, const WarpTile<MAXR> &T, const Tile
         rows &= rows - 1;
         const int gy = g.y0 + r - 1;
         pkey_t *dst = P.keys + (size_t)gy * P.W + g.x0 + c;
-        const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[r][c]);
+        const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[r][KO + c]);
         if (c + 1 < g.wv && row_vec_ok(gy, P.W)) {
             *reinterpret_cast<ulonglong2 *>(dst) = kk;
         } else {
@@ -249,50 +256,191 @@ __device__ void write_rows(const PairDev &P, const WarpTile<MAXR> &T, const Tile
     }
 }
 
+__device__ __forceinline__ unsigned long long warp_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// TMA staging of one tile: lane 0 starts the box copies of the keys (if
+// `keys`) and the costs into the warp's tile, completing on its mbarrier;
+// every lane then waits, at most TMA_LIMIT_NS.  Returns false in every lane
+// if the wait gave up (the run has recorded EPIC_ERR_TIMEOUT; a copy may
+// still land in this CTA's shared memory after the kernel has left).
+template <int MAXR>
+__device__ bool tma_stage(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g, bool keys,
+                          unsigned &phase, int lane, RunState *st) {
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&T.bar);
+    __syncwarp();   // every lane is done with the previous tile's data
+    if (lane == 0) {
+        const unsigned kbytes = (unsigned)(KP * (P.tile_h + 2) * 8);
+        const unsigned cbytes = (unsigned)(CP * (P.tile_h + 2) * 4);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(cbytes + (keys ? kbytes : 0u))
+                     : "memory");
+        const int y = g.y0 - 1;
+        if (keys) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                             &P.tm_warp_keys)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3}], [%4];" ::"r"((unsigned)__cvta_generic_to_shared(&T.K[0][0])),
+                "l"(&P.tm_warp_keys), "r"(g.x0 - KO), "r"(y), "r"(bar)
+                : "memory");
+        }
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&P.tm_warp_cost)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"((unsigned)__cvta_generic_to_shared(&T.hC[0][0])),
+            "l"(&P.tm_warp_cost), "r"(g.x0 - CO), "r"(y), "r"(bar)
+            : "memory");
+    }
+    const unsigned long long t0 = warp_ns();
+    int gave_up = 0;
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+            " selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) break;
+        if (warp_ns() - t0 > TMA_LIMIT_NS) {
+            set_status(st, EPIC_ERR_TIMEOUT);
+            gave_up = 1;
+            break;
+        }
+    }
+    phase ^= 1u;
+    return !__any_sync(FULL, gave_up);
+}
+
+// Plain-load staging into the same layout (maps whose pitch or base does
+// not meet TMA's 16-byte rules).  Keys and costs outside the image read as
+// unreached and zero.  Keys of other tiles may be rewritten during the
+// launch: they are read through L2.
+template <int MAXR>
+__device__ void plain_stage(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g, bool keys,
+                            int lane) {
+    const int c = 2 * lane;
+    for (int r = 0; r <= g.rv + 1; ++r) {
+        const int gy = g.y0 + r - 1;
+        ulonglong2 kk = make_ulonglong2(KEY_INF, KEY_INF);
+        uint2 cc = make_uint2(0u, 0u);
+        if (gy >= 0 && gy < P.H) {
+            const size_t o = (size_t)gy * P.W + g.x0 + c;
+            if (c + 1 < g.wv && cost_vec_ok(P, gy)) {
+                if (keys) kk = __ldcg(reinterpret_cast<const ulonglong2 *>(P.keys + o));
+                const float2 f = __ldg(reinterpret_cast<const float2 *>(P.C + o));
+                cc = make_uint2(__float_as_uint(f.x), __float_as_uint(f.y));
+            } else {
+                if (c < g.wv) {
+                    if (keys) kk.x = __ldcg(P.keys + o);
+                    cc.x = __float_as_uint(__ldg(P.C + o));
+                }
+                if (c + 1 < g.wv) {
+                    if (keys) kk.y = __ldcg(P.keys + o + 1);
+                    cc.y = __float_as_uint(__ldg(P.C + o + 1));
+                }
+            }
+        }
+        if (keys) *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = kk;
+        *reinterpret_cast<uint2 *>(&T.hC[r][CO + c]) = cc;
+    }
+    for (int r = lane; r < g.rv + 2; r += 32) {
+        const int gy = g.y0 + r - 1;
+        const bool row_in = gy >= 0 && gy < P.H;
+        pkey_t kl = KEY_INF, kr = KEY_INF;
+        unsigned cl = 0u, cr = 0u;
+        if (row_in && g.x0 > 0) {
+            const size_t o = (size_t)gy * P.W + g.x0 - 1;
+            if (keys) kl = __ldcg(P.keys + o);
+            cl = __float_as_uint(__ldg(P.C + o));
+        }
+        if (row_in && g.x0 + RT_COLS < P.W) {
+            const size_t o = (size_t)gy * P.W + g.x0 + RT_COLS;
+            if (keys) kr = __ldcg(P.keys + o);
+            cr = __float_as_uint(__ldg(P.C + o));
+        }
+        if (keys) {
+            T.K[r][KO - 1] = kl;
+            T.K[r][KO + RT_COLS] = kr;
+        }
+        T.hC[r][CO - 1] = cl;
+        T.hC[r][CO + RT_COLS] = cr;
+    }
+}
+
+// Stage tile (tx, ty) and its ring: keys (if `keys`, else unreached) and
+// half-costs.  Cells outside the image end as unreached keys and zero
+// half-costs, whichever way they were copied.  Returns false when a TMA
+// wait gave up (the caller leaves the kernel).
+template <int MAXR>
+__device__ bool stage_tile(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g, bool keys,
+                           unsigned &phase, int lane, RunState *st) {
+    const int c = 2 * lane;
+    if (P.tma_warp) {
+        if (!tma_stage(P, T, g, keys, phase, lane, st)) return false;
+    } else {
+        __syncwarp();
+        plain_stage(P, T, g, keys, lane);
+    }
+    bool bad = false;
+    for (int r = 0; r <= g.rv + 1; ++r) {
+        const int gy = g.y0 + r - 1;
+        const bool row_in = gy >= 0 && gy < P.H;
+        // keys: a fresh tile starts unreached; out-of-image cells are
+        // unreached (TMA fills them with zeros)
+        ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[r][KO + c]);
+        if (!keys || !row_in || g.outa) kk.x = KEY_INF;
+        if (!keys || !row_in || g.outb) kk.y = KEY_INF;
+        *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = kk;
+        // half-costs, in place
+        uint2 cc = *reinterpret_cast<const uint2 *>(&T.hC[r][CO + c]);
+        cc.x = row_in && !g.outa ? half_cost(__uint_as_float(cc.x), &bad) : 0u;
+        cc.y = row_in && !g.outb ? half_cost(__uint_as_float(cc.y), &bad) : 0u;
+        *reinterpret_cast<uint2 *>(&T.hC[r][CO + c]) = cc;
+    }
+    for (int r = lane; r < g.rv + 2; r += 32) {
+        const int gy = g.y0 + r - 1;
+        const bool row_in = gy >= 0 && gy < P.H;
+        const bool lin = row_in && g.x0 > 0, rin = row_in && g.x0 + RT_COLS < P.W;
+        if (!keys || !lin) T.K[r][KO - 1] = KEY_INF;
+        if (!keys || !rin) T.K[r][KO + RT_COLS] = KEY_INF;
+        T.hC[r][CO - 1] = lin ? half_cost(__uint_as_float(T.hC[r][CO - 1]), &bad) : 0u;
+        T.hC[r][CO + RT_COLS] = rin ? half_cost(__uint_as_float(T.hC[r][CO + RT_COLS]), &bad) : 0u;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) set_status(st, EPIC_ERR_INVALID);
+    __syncwarp();
+    return true;
+}
+
 // Phase 1: solve tile (tx, ty) from its own seeds.  A tile without seeds is
 // written unreached and stamped "never written" (-1), so that in the first
-// pass its seedless neighbours skip it.
+// pass its seedless neighbours skip it.  Returns false when the staging
+// timed out.
 template <int MAXR>
-__device__ void fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T, int lane,
-                           RunState *st) {
+__device__ bool fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T, int lane,
+                           unsigned &phase, RunState *st) {
     const TileGeo g = tile_geo(P, tx, ty, lane);
     const int c = 2 * lane;
     const int s0 = P.tile_start[t], s1 = P.tile_start[t + 1];
+    const unsigned long long all = ((1ull << g.rv) - 1) << 1;
     if (s0 == s1) {
-        const unsigned long long all = ((1ull << g.rv) - 1) << 1;
+        __syncwarp();
         for (int r = 1; r <= g.rv; ++r)
-            *reinterpret_cast<ulonglong2 *>(&T.K[r][c]) = make_ulonglong2(KEY_INF, KEY_INF);
+            *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = make_ulonglong2(KEY_INF, KEY_INF);
         __syncwarp();
         write_rows(P, T, g, all, lane);
         if (lane == 0) P.tile_stamp[t] = -1;
         __syncwarp();
-        return;
+        return true;
     }
-    bool bad = false;
-    for (int r = 0; r <= g.rv + 1; ++r) {
-        *reinterpret_cast<ulonglong2 *>(&T.K[r][c]) = make_ulonglong2(KEY_INF, KEY_INF);
-        uint2 hh = make_uint2(0u, 0u);
-        if (r >= 1 && r <= g.rv) {
-            const int gy = g.y0 + r - 1;
-            const float *src = P.C + (size_t)gy * P.W + g.x0 + c;
-            if (c + 1 < g.wv && cost_vec_ok(P, gy)) {
-                const float2 cc = __ldg(reinterpret_cast<const float2 *>(src));
-                hh = make_uint2(half_cost(cc.x, &bad), half_cost(cc.y, &bad));
-            } else {
-                if (c < g.wv) hh.x = half_cost(__ldg(src), &bad);
-                if (c + 1 < g.wv) hh.y = half_cost(__ldg(src + 1), &bad);
-            }
-        }
-        *reinterpret_cast<uint2 *>(&T.h[r][c]) = hh;
-    }
-    for (int r = lane; r < g.rv + 2; r += 32) {
-        T.KL[r] = KEY_INF;
-        T.KR[r] = KEY_INF;
-        T.hL[r] = 0u;
-        T.hR[r] = 0u;
-    }
-    if (__any_sync(FULL, bad) && lane == 0) set_status(st, EPIC_ERR_INVALID);
-    __syncwarp();
+    if (!stage_tile(P, T, g, false, phase, lane, st)) return false;
     unsigned long long seeded = 0;
     for (int s = s0 + lane; s < s1; s += 32) {
         const int m = P.tile_seeds[s];
@@ -300,7 +448,8 @@ __device__ void fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAX
         const int px = (int)floorf(mt.x + 0.5f) - g.x0;
         const int py = (int)floorf(mt.y + 0.5f) - g.y0;
         if (px >= 0 && px < g.wv && py >= 0 && py < g.rv) {
-            atomicMin(&T.K[py + 1][px], make_key(P.seed_init ? P.seed_init[m] : 0ull, (unsigned)m));
+            atomicMin(&T.K[py + 1][KO + px],
+                      make_key(P.seed_init ? P.seed_init[m] : 0ull, (unsigned)m));
             seeded |= 1ull << (py + 1);
         }
     }
@@ -308,68 +457,23 @@ __device__ void fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAX
     __syncwarp();
     tile_passes(T, lane, g, seeded, seeded, seeded, 0ull, st);
     __syncwarp();
-    write_rows(P, T, g, ((1ull << g.rv) - 1) << 1, lane);
+    write_rows(P, T, g, all, lane);
     __threadfence();
     if (lane == 0) P.tile_stamp[t] = 0;
     __syncwarp();
+    return true;
 }
 
-// Phase 2: load tile (tx, ty) with its ring from the current key map, set
-// the flags of the rows the ring can improve and re-solve.  Returns whether
-// any key of the tile changed (then it was written back and stamped `stamp`).
+// Phase 2: stage tile (tx, ty) with its ring from the current key map, set
+// the flags of the rows the ring can improve and re-solve.  Returns 1 if any
+// key of the tile changed (then it was written back and stamped `stamp`),
+// 0 if none did, -1 if the staging timed out.
 template <int MAXR>
-__device__ bool resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T,
-                             int lane, RunState *st, int stamp) {
+__device__ int resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T,
+                            int lane, unsigned &phase, RunState *st, int stamp) {
     const TileGeo g = tile_geo(P, tx, ty, lane);
     const int c = 2 * lane;
-    bool bad = false;
-    // keys of other tiles may be rewritten during the launch: read through L2
-    for (int r = 0; r <= g.rv + 1; ++r) {
-        const int gy = g.y0 + r - 1;
-        ulonglong2 kk = make_ulonglong2(KEY_INF, KEY_INF);
-        uint2 hh = make_uint2(0u, 0u);
-        if (gy >= 0 && gy < P.H) {
-            const size_t o = (size_t)gy * P.W + g.x0 + c;
-            if (c + 1 < g.wv && cost_vec_ok(P, gy)) {
-                kk = __ldcg(reinterpret_cast<const ulonglong2 *>(P.keys + o));
-                const float2 cc = __ldg(reinterpret_cast<const float2 *>(P.C + o));
-                hh = make_uint2(half_cost(cc.x, &bad), half_cost(cc.y, &bad));
-            } else {
-                if (c < g.wv) {
-                    kk.x = __ldcg(P.keys + o);
-                    hh.x = half_cost(__ldg(P.C + o), &bad);
-                }
-                if (c + 1 < g.wv) {
-                    kk.y = __ldcg(P.keys + o + 1);
-                    hh.y = half_cost(__ldg(P.C + o + 1), &bad);
-                }
-            }
-        }
-        *reinterpret_cast<ulonglong2 *>(&T.K[r][c]) = kk;
-        *reinterpret_cast<uint2 *>(&T.h[r][c]) = hh;
-    }
-    for (int r = lane; r < g.rv + 2; r += 32) {
-        const int gy = g.y0 + r - 1;
-        const bool row_in = gy >= 0 && gy < P.H;
-        pkey_t kl = KEY_INF, kr = KEY_INF;
-        unsigned hl = 0u, hr = 0u;
-        if (row_in && g.x0 > 0) {
-            const size_t o = (size_t)gy * P.W + g.x0 - 1;
-            kl = __ldcg(P.keys + o);
-            hl = half_cost(__ldg(P.C + o), &bad);
-        }
-        if (row_in && g.x0 + RT_COLS < P.W) {
-            const size_t o = (size_t)gy * P.W + g.x0 + RT_COLS;
-            kr = __ldcg(P.keys + o);
-            hr = half_cost(__ldg(P.C + o), &bad);
-        }
-        T.KL[r] = kl;
-        T.KR[r] = kr;
-        T.hL[r] = hl;
-        T.hR[r] = hr;
-    }
-    if (__any_sync(FULL, bad) && lane == 0) set_status(st, EPIC_ERR_INVALID);
-    __syncwarp();
+    if (!stage_tile(P, T, g, true, phase, lane, st)) return -1;
     // which rows can a ring pixel improve?  The top row from ring row 0 (a
     // down step of row 1), the bottom row from ring row rv + 1 (an up step
     // of row rv); the end columns of row r from the ring column in rows
@@ -380,14 +484,14 @@ __device__ bool resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<M
         pkey_t na, nb;
         load_up(T, 0, lane, u);
         neighbours_up(T, 0, lane, u);
-        const ulonglong2 k1 = *reinterpret_cast<const ulonglong2 *>(&T.K[1][c]);
-        const uint2 h1 = *reinterpret_cast<const uint2 *>(&T.h[1][c]);
+        const ulonglong2 k1 = *reinterpret_cast<const ulonglong2 *>(&T.K[1][KO + c]);
+        const uint2 h1 = *reinterpret_cast<const uint2 *>(&T.hC[1][CO + c]);
         from_up(u, k1.x, k1.y, h1.x, h1.y, na, nb);
         const bool top = (!g.outa && na < k1.x) || (!g.outb && nb < k1.y);
         load_up(T, g.rv + 1, lane, u);
         neighbours_up(T, g.rv + 1, lane, u);
-        const ulonglong2 kb = *reinterpret_cast<const ulonglong2 *>(&T.K[g.rv][c]);
-        const uint2 hb = *reinterpret_cast<const uint2 *>(&T.h[g.rv][c]);
+        const ulonglong2 kb = *reinterpret_cast<const ulonglong2 *>(&T.K[g.rv][KO + c]);
+        const uint2 hb = *reinterpret_cast<const uint2 *>(&T.hC[g.rv][CO + c]);
         from_up(u, kb.x, kb.y, hb.x, hb.y, na, nb);
         const bool bot = (!g.outa && na < kb.x) || (!g.outb && nb < kb.y);
         if (__any_sync(FULL, top)) selfD |= 2ull;
@@ -398,31 +502,33 @@ __device__ bool resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<M
         const int r = lane + 1;
         bool d = false, up = false;
         if (r <= g.rv) {
-            const pkey_t k0 = T.K[r][0];
-            const unsigned h0 = T.h[r][0];
-            d |= step_key(T.KL[r - 1], step_diag(h0, T.hL[r - 1])) < k0;
-            d |= step_key(T.KL[r], step_axis(h0, T.hL[r])) < k0;
-            up |= step_key(T.KL[r + 1], step_diag(h0, T.hL[r + 1])) < k0;
+            const pkey_t k0 = T.K[r][KO];
+            const unsigned h0 = T.hC[r][CO];
+            const int L = KO - 1, LC = CO - 1;
+            d |= step_key(T.K[r - 1][L], step_diag(h0, T.hC[r - 1][LC])) < k0;
+            d |= step_key(T.K[r][L], step_axis(h0, T.hC[r][LC])) < k0;
+            up |= step_key(T.K[r + 1][L], step_diag(h0, T.hC[r + 1][LC])) < k0;
             if (g.wv == RT_COLS) {
-                const pkey_t k1 = T.K[r][RT_COLS - 1];
-                const unsigned h1 = T.h[r][RT_COLS - 1];
-                d |= step_key(T.KR[r - 1], step_diag(h1, T.hR[r - 1])) < k1;
-                d |= step_key(T.KR[r], step_axis(h1, T.hR[r])) < k1;
-                up |= step_key(T.KR[r + 1], step_diag(h1, T.hR[r + 1])) < k1;
+                const pkey_t k1 = T.K[r][KO + RT_COLS - 1];
+                const unsigned h1 = T.hC[r][CO + RT_COLS - 1];
+                const int R = KO + RT_COLS, RC = CO + RT_COLS;
+                d |= step_key(T.K[r - 1][R], step_diag(h1, T.hC[r - 1][RC])) < k1;
+                d |= step_key(T.K[r][R], step_axis(h1, T.hC[r][RC])) < k1;
+                up |= step_key(T.K[r + 1][R], step_diag(h1, T.hC[r + 1][RC])) < k1;
             }
         }
         selfD |= (unsigned long long)__ballot_sync(FULL, d) << 1;
         selfU |= (unsigned long long)__ballot_sync(FULL, up) << 1;
     }
-    if ((selfD | selfU) == 0) return false;
+    if ((selfD | selfU) == 0) return 0;
     const unsigned long long mod = tile_passes(T, lane, g, 0ull, 0ull, selfD, selfU, st);
-    if (mod == 0) return false;
+    if (mod == 0) return 0;
     __syncwarp();
     write_rows(P, T, g, mod, lane);
     __threadfence();
     if (lane == 0) P.tile_stamp[t] = stamp;
     __syncwarp();
-    return true;
+    return 1;
 }
 
 __device__ __forceinline__ int take_tile(unsigned *dispenser, int lane) {
@@ -442,9 +548,16 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
     const unsigned nblocks =
         min(gridDim.x, (unsigned)((a.total_tiles + RT_WARPS - 1) / RT_WARPS));
     if (blockIdx.x >= nblocks) return;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     WarpTile<MAXR> &T = reinterpret_cast<WarpTile<MAXR> *>(smem)[threadIdx.x >> 5];
+    unsigned phase = 0;   // parity of the warp's mbarrier
+    if (lane == 0) {
+        const unsigned bar = (unsigned)__cvta_generic_to_shared(&T.bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
 
     // phase 1
     for (int t = take_tile(&st->work[3], lane); t < a.total_tiles;
@@ -452,7 +565,7 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
         const int pi = find_pair(a.tile_base, a.npairs, t);
         const PairDev &P = a.pairs[pi];
         const int lt = t - a.tile_base[pi];
-        fresh_tile(P, lt, lt % P.tiles_x, lt / P.tiles_x, T, lane, st);
+        if (!fresh_tile(P, lt, lt % P.tiles_x, lt / P.tiles_x, T, lane, phase, st)) return;
     }
     if (!grid_sync(st, nblocks)) return;
 
@@ -483,8 +596,9 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
                      __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass;
             }
             if (!__any_sync(FULL, nb)) continue;
-            if (resolve_tile(P, lt, tx, ty, T, lane, st, pass + 1) && lane == 0)
-                atomicAdd(cnt, 1u);
+            const int r = resolve_tile(P, lt, tx, ty, T, lane, phase, st, pass + 1);
+            if (r < 0) return;
+            if (r > 0 && lane == 0) atomicAdd(cnt, 1u);
         }
         if (!grid_sync(st, nblocks)) return;
         const unsigned dirty = ld_acquire(cnt);

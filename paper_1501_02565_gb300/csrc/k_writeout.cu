@@ -92,7 +92,13 @@ __global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *_
 
 cudaError_t launch_writeout(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
     (void)a;
-    writeout_kernel<<<lc.num_sms * 16, WO_THREADS, 0, lc.stream>>>(dev);
+    // one resident wave: every CTA runs its contiguous share at once (a
+    // second, partial wave would leave most of the GPU idle at the end)
+    int per_sm = 0;
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, writeout_kernel, WO_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    writeout_kernel<<<lc.num_sms * (per_sm > 0 ? per_sm : 1), WO_THREADS, 0, lc.stream>>>(dev);
     return cudaGetLastError();
 }
 

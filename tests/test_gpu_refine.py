@@ -6,15 +6,13 @@ interpolator (REF_TOL = 1e-3 px): at every pixel on small frames, and on a
 full Sintel-shaped 1024x436 frame at every well-conditioned pixel.
 
 The full frame has a few hundred pixels where the refinement is
-ill-conditioned: the FP64 result itself moves by up to ~0.08 px when the
-inputs change by float32 rounding, and the oracle's own steps evaluated in
-float32 miss the FP64 result by up to ~0.07 px there, so no float32
-computation can hold those pixels to 1e-3 px.  The rule: a pixel is
-well-conditioned when three float32-sized probes -- the oracle evaluated in
-float32, and two FP64 runs from inputs perturbed by float32 rounding (the
-starting flow by +-1e-5 px, the images by +-2^-24 relative) -- all stay
-within REF_TOL / 5 of the FP64 result.  The GPU must be within REF_TOL at
-every well-conditioned pixel, at least 99.5 % of the pixels must be
+ill-conditioned: the FP64 result itself moves by up to ~0.08 px when its
+inputs change by float32 rounding, so no float32 computation can hold those
+pixels to 1e-3 px.  The rule: a pixel is well-conditioned when three FP64
+runs from inputs perturbed by float32 rounding (the starting flow by
++-1e-5 px, the images by +-2^-24 relative, independent draws) all stay within
+REF_TOL / 5 of the unperturbed FP64 result.  The GPU must be within REF_TOL
+at every well-conditioned pixel, at least 99.5 % of the pixels must be
 well-conditioned, and the others are counted and reported."""
 
 import numpy as np
@@ -31,12 +29,12 @@ PROBE_FLOW_PX = 1e-5      # float32 ulp of a 128 px flow is 1.5e-5
 PROBE_IMAGE_REL = 2.0 ** -24
 
 
-def _conditioning(I1, I2, flow0, ref):
-    """Per pixel, the largest move of the FP64 result under the float32-sized
-    probes (see the module docstring)."""
-    s = np.abs(R.refine(I1, I2, flow0, dtype=np.float32) - ref).max(-1)
+def _conditioning(I1, I2, flow0, ref, draws=3):
+    """Per pixel, the largest move of the FP64 result under float32-sized
+    perturbations of its inputs (see the module docstring)."""
+    s = np.zeros(ref.shape[:2])
     rng = np.random.default_rng(11)
-    for _ in range(2):
+    for _ in range(draws):
         f = flow0.astype(np.float64) + PROBE_FLOW_PX * rng.uniform(-1, 1, flow0.shape)
         a = I1.astype(np.float64) * (1 + PROBE_IMAGE_REL * rng.uniform(-1, 1, I1.shape))
         b = I2.astype(np.float64) * (1 + PROBE_IMAGE_REL * rng.uniform(-1, 1, I2.shape))
