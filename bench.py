@@ -384,6 +384,11 @@ def run_served(pool, device, rules, n_requests, stream):
     from paper_1501_02565_gb300.serve import Request, Server, replay
     cfg = dict(max_H=max(p.H for p in pool), max_W=max(p.W for p in pool),
                max_N=max(p.N for p in pool), max_K=100, use_graphs=1)
+    # the request submitter and the server loop are Python threads: with the
+    # interpreter's default 5 ms switch interval a submission can wait that
+    # long for the GIL, and latencies count from the scheduled arrival
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(5e-5)
     # capacities: the one-pair path and the batched path on the pool
     items = device_items(pool, stream.device)
     peng = engine_for(pool[:1], device, use_graphs=1)
@@ -433,7 +438,9 @@ def run_served(pool, device, rules, n_requests, stream):
             st.update({"status": status, "unit": "Mpix/s"})
             row[name] = st
         sweep.append(row)
+    sys.setswitchinterval(switch)
     return {"requests_per_rate": n_requests, "distinct_pairs": len(pool),
+            "latency_from": "scheduled arrival", "gil_switch_interval_s": 5e-5,
             "sizes": sorted({f"{p.W}x{p.H}" for p in pool}),
             "capacity": {"one_at_a_time_mpix_s": plain_mpix, "batched_mpix_s": batched_mpix,
                          "one_at_a_time_latency_ms_p50": float(np.percentile(lat, 50)),

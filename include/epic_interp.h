@@ -23,10 +23,17 @@
  *
  * Conventions shared by every entry point
  *   - Images are row-major, x = column, y = row; pixel centres are integer.
- *   - cost_map: float32 [H*W], every value finite and in [0, 2) (edge
- *     strengths).  The relaxation adds exact fixed-point step costs (units
- *     of 2^-31), so geodesic distances must stay below 1024; a value outside
- *     the range, or a pixel left unreached, is reported as EPIC_ERR_INVALID.
+ *   - cost_map: float32 [H*W], every value finite and >= 0 (edge
+ *     strengths).  The relaxation adds exact fixed-point step costs.  With
+ *     the default warp-tile relaxation each pair gets its own unit,
+ *     2^-(31 - s): s = 0 (units of 2^-31) unless the pair's largest cost
+ *     reaches 2 or a bound on its distances (its largest cost times the
+ *     distance from any pixel to a seed, counted in relaxation tiles)
+ *     reaches 1024, then the smallest s that holds both; costs up to 2^21
+ *     and distances up to 2^30 fit.  The exact variant, the no-allocation
+ *     entry point and the relaxation schedules 0 and 1 keep the unit 2^-31:
+ *     costs below 2, distances below 1024.  A value outside the range, or a
+ *     pixel left unreached, is reported as EPIC_ERR_INVALID.
  *   - matches:  float32 [N*4], rows (x, y, x', y').  The source pixel of match
  *     m is (floor(x+0.5), floor(y+0.5)) and must lie inside the image; two
  *     matches may share a source pixel (the smaller index owns it).
@@ -254,6 +261,12 @@ int epic_interp_get_pruning(epic_interp_t *h, int pair, int *keep,
 /* Number of relaxation verification passes the last run needed for its
  * whole batch (waits for the stream). */
 int epic_interp_get_passes(epic_interp_t *h, int *passes);
+
+/* Distance unit of pair `pair` of the last run: its keys count distance in
+ * units of 2^-(31 - *shift) (waits for the stream).  0 unless the pair's
+ * costs reach 2 or its distances could reach 1024 (see the cost range in the
+ * conventions above); always 0 with relaxation schedules 0 and 1. */
+int epic_interp_get_distance_unit(epic_interp_t *h, int pair, int *shift);
 
 /* Number of matches of the last run whose K-NN search outgrew the per-warp
  * tables of the main pass and was run again with large tables (the final

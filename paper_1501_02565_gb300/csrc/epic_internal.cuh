@@ -12,6 +12,7 @@
 #include <cuda.h>            // CUtensorMap (type only; no driver library is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/epic_interp.h"
 
@@ -72,6 +73,43 @@ __device__ __forceinline__ unsigned half_cost(float c, bool *bad) {
     }
     return __float2uint_rn(__fmul_rn(c, 1073741824.0f));
 }
+// Per-pair distance unit of the warp-tile relaxation.  A pair's keys count
+// distance in units of 2^-(31 - s) and its half-costs are
+// h = rint(C 2^(30 - s)), so costs up to 2^(1 + s) and distances up to
+// 2^(10 + s) fit; s = 0 (the unit above) unless the pair needs more.  The
+// prepare kernel records the pair's largest cost (cmax_bits) and how many
+// tile steps separate the farthest tile from a tile holding a seed
+// (seed_reach); every pixel then lies within an octile distance of
+// (reach + 1) (max(tw, th) + (sqrt 2 - 1) min(tw, th)) pixels of a seed, and
+// its geodesic distance is at most the largest cost times that.  Every kernel
+// derives s from these two fields with this function, so they agree.
+constexpr int MAX_UNIT_SHIFT = 20;
+constexpr int SWEEP_WARP = 2;   // relaxation schedule of the warp tiles
+__host__ __device__ __forceinline__ int unit_shift_of(unsigned cmax_bits, int reach, int tw,
+                                                      int th) {
+    if (cmax_bits > 0x7f800000u) return 0;   // NaN or negative: reported as an invalid cost
+    float cmax;
+    memcpy(&cmax, &cmax_bits, sizeof cmax);
+    const float r = (float)(reach + 1);
+    const float ext = r * (float)(tw > th ? tw : th) + 0.41421357f * r * (float)(tw < th ? tw : th);
+    const float dbound = cmax * ext * 1.001f + 1e-3f;
+    int s = 0;
+    while (s < MAX_UNIT_SHIFT && (cmax >= ldexpf(2.f, s) || dbound >= ldexpf(1024.f, s))) ++s;
+    return s;
+}
+// h = rint(C 2^(30 - s)) for 0 <= C < C_MAX 2^s, else 0 and *bad set.
+__device__ __forceinline__ unsigned half_cost_s(float c, int s, bool *bad) {
+    if (!(c >= 0.f && c < ldexpf(C_MAX, s))) {
+        *bad = true;
+        return 0u;
+    }
+    return __float2uint_rn(__fmul_rn(c, ldexpf(1073741824.0f, -s)));
+}
+// Distance of `units` fixed-point units of shift s, rounded once to float32.
+__device__ __forceinline__ float units_dist(unsigned long long units, int s) {
+    return __fmul_rn(__ull2float_rn(units), ldexpf(ONE_PER_UNIT, s));
+}
+
 // Candidate key at p from neighbour key kq over a step of w units; an
 // unreached neighbour offers nothing (its flag bit makes the sum >= KEY_INF).
 __device__ __forceinline__ pkey_t step_key(pkey_t kq, unsigned long long w) {
@@ -136,9 +174,23 @@ struct PairDev {
     // boxes of the keys (u64, 68 x (tile_h + 2) from x0 - 2) and of the
     // costs (float32, 72 x (tile_h + 2) from x0 - 4), tile and ring
     int tma_warp;
+    // written on the device by the prepare kernel (zero from the host): the
+    // float bits of the pair's largest cost and the tile-step reach of its
+    // seeds, from which unit_shift() derives the distance unit
+    unsigned cmax_bits;
+    int seed_reach;
     CUtensorMap tm_warp_keys;
     CUtensorMap tm_warp_cost;
 };
+
+// The distance unit shift of a pair (0 for the sweep schedules of k_dt.cu,
+// which keep the unit 2^-31).
+__device__ __forceinline__ int unit_shift(const PairDev &P) {
+    return P.sweep == SWEEP_WARP
+               ? unit_shift_of(*(volatile const unsigned *)&P.cmax_bits,
+                               *(volatile const int *)&P.seed_reach, P.tile_w, P.tile_h)
+               : 0;
+}
 
 struct GridBarrier {
     unsigned count;
@@ -326,8 +378,10 @@ cudaError_t launch_refine(const float *I1, const float *I2, int H, int W, int C,
 // Image-gradient cost map.
 cudaError_t launch_gradcost(const float *img, int F, int H, int W, int channels, float floor_,
                             float *C, int num_sms, cudaStream_t stream);
-cudaError_t launch_split_keys(const PairDev *pair_host_copy, int *labels,
-                              float *dist, cudaStream_t stream);
+// labels / distances of one pair's keys; pair_dev is the pair's device
+// descriptor (its distance unit is recorded there on the device)
+cudaError_t launch_split_keys(const PairDev *pair_host_copy, const PairDev *pair_dev,
+                              int *labels, float *dist, cudaStream_t stream);
 cudaError_t launch_collect_edges(const PairDev *pair_host_copy, int *em,
                                  int *en, float *ew, int cap, int *count,
                                  cudaStream_t stream);

@@ -1001,7 +1001,7 @@ int epic_interp_get_labels(epic_interp_t *h, int pair, int *labels, float *dist,
                            void *stream) {
     int rc = check_pair(h, pair);
     if (rc) return rc;
-    cudaError_t e = epic::launch_split_keys(&h->pairs[pair], labels, dist,
+    cudaError_t e = epic::launch_split_keys(&h->pairs[pair], h->pairs_dev + pair, labels, dist,
                                             reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EPIC_OK : cuda_fail(h, e, "get_labels");
 }
@@ -1084,6 +1084,21 @@ int epic_interp_get_passes(epic_interp_t *h, int *passes) {
     int rc = read_state(h);
     if (rc) return rc;
     *passes = h->state_host->passes;
+    return EPIC_OK;
+}
+
+int epic_interp_get_distance_unit(epic_interp_t *h, int pair, int *shift) {
+    if (!h || !shift) return EPIC_ERR_INVALID;
+    int rc = check_pair(h, pair);
+    if (rc) return rc;
+    rc = wait_last(h);
+    if (rc) return rc;
+    PairDev d;
+    cudaError_t e = cudaMemcpy(&d, h->pairs_dev + pair, sizeof d, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pair descriptor read");
+    *shift = d.sweep == SWEEP_WARP_TILES
+                 ? epic::unit_shift_of(d.cmax_bits, d.seed_reach, d.tile_w, d.tile_h)
+                 : 0;
     return EPIC_OK;
 }
 

@@ -144,7 +144,8 @@ extern "C" int epic_geodesic_labels_noalloc(const float *cost_map, const float *
     if (epic::launch_prepare(a, dev_a, lc) != cudaSuccess ||
         epic::launch_dt(a, dev_a, lc, NA_TILE_W, NA_TILE_H, NA_APRON, false, nullptr) !=
             cudaSuccess ||
-        epic::launch_split_keys(&Pd, labels_out, dist_out, stream) != cudaSuccess)
+        epic::launch_split_keys(&Pd, reinterpret_cast<const epic::PairDev *>(base + OFF_PAIR),
+                                labels_out, dist_out, stream) != cudaSuccess)
         return EPIC_ERR_CUDA;
     int status = 0;
     if (cudaMemcpyAsync(&status, &state->status, sizeof(int), cudaMemcpyDeviceToHost, stream) ||

@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
         const int npx = P.tile_w * P.tile_h;
         const int W = P.W, H = P.H;
         const int SC = P.tile_w + 2, SR = P.tile_h + 1;   // staged columns x0-1 .. x0+tw
+        const int us = unit_shift(P);                      // the pair's distance unit
         pkey_t *skey = reinterpret_cast<pkey_t *>(edge_smem);
         unsigned *sh = reinterpret_cast<unsigned *>(skey + SC * SR);
         {
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                 const bool in = gx >= 0 && gx < W && gy < H;
                 const size_t q = (size_t)gy * W + gx;
                 skey[j] = in ? __ldg(P.keys + q) : KEY_INF;
-                sh[j] = in ? half_cost(__ldg(P.C + q), &bad) : 0u;
+                sh[j] = in ? half_cost_s(__ldg(P.C + q), us, &bad) : 0u;
             }
         }
         __syncthreads();
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                                                            : step_axis(hp, hq);
                         // exact sum in fixed point, rounded once to float32
                         const unsigned long long units = key_dunits(kp) + stp + key_dunits(kq);
-                        const float w = __fmul_rn(__ull2float_rn(units), ONE_PER_UNIT);
+                        const float w = units_dist(units, us);
                         k = lp < lq ? (((pkey_t)lp << 32) | lq) : (((pkey_t)lq << 32) | lp);
                         wb = __float_as_uint(w);
                     }
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
         const unsigned l = key_label(kp);
         if (l != (unsigned)m && l < (unsigned)P.N) {
             const unsigned lo = min(l, (unsigned)m), hi = max(l, (unsigned)m);
-            table_insert(P, ((pkey_t)lo << 32) | hi, __float_as_uint(key_dist(kp)), st);
+            table_insert(P, ((pkey_t)lo << 32) | hi,
+                         __float_as_uint(units_dist(key_dunits(kp), unit_shift(P))), st);
         }
     }
 }
@@ -366,11 +368,14 @@ __global__ void __launch_bounds__(256) bound_edge_kernel(const BatchArgs *__rest
     }
 }
 
-__global__ void split_kernel(const pkey_t *keys, int P, int *labels, float *dist) {
+__global__ void split_kernel(const pkey_t *keys, int P, int *labels, float *dist,
+                             const PairDev *pair_dev) {
+    const int us = unit_shift(*pair_dev);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
         pkey_t k = keys[i];
         if (labels) labels[i] = (int)key_label(k);
-        if (dist) dist[i] = key_dist(k);
+        if (dist) dist[i] = key_reached(k) ? units_dist(key_dunits(k), us)
+                                           : __int_as_float(0x7f800000);
     }
 }
 
@@ -424,11 +429,11 @@ cudaError_t launch_scatter(const BatchArgs &a, const BatchArgs *dev, const Launc
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_keys(const PairDev *P, int *labels, float *dist,
-                              cudaStream_t stream) {
+cudaError_t launch_split_keys(const PairDev *P, const PairDev *pair_dev, int *labels,
+                              float *dist, cudaStream_t stream) {
     int n = P->H * P->W;
     split_kernel<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, stream>>>(
-        P->keys, n, labels, dist);
+        P->keys, n, labels, dist, pair_dev);
     return cudaGetLastError();
 }
 

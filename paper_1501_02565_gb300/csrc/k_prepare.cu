@@ -8,6 +8,10 @@
 // * The match-graph edge table, the node degrees and lightest edges are
 //   reset so that the graph stage can insert with atomics.
 // * The run's grid-barrier and pass counters are reset.
+// * For the warp-tile relaxation, each pair's largest cost and the reach of
+//   its seeds over the tile grid (a Chebyshev distance transform of the
+//   seeded tiles) are recorded; they fix the pair's distance unit (see
+//   unit_shift in epic_internal.cuh).
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -63,6 +67,89 @@ __device__ __forceinline__ bool seed_pixel(float4 mt, int H, int W, int *px,
     return true;
 }
 
+// Chebyshev distance, in tile steps, from every tile to the nearest tile
+// holding a seed (the scatter cursors, no longer needed, are the scratch),
+// and its largest value in P.seed_reach.  One CTA per pair.
+__device__ void seed_reach(const PairDev &P, int T) {
+    __shared__ int s_changed;
+    int *d = P.tile_fill;
+    for (int t = threadIdx.x; t < T; t += blockDim.x)
+        d[t] = P.tile_start[t + 1] > P.tile_start[t] ? 0 : 0x3fffffff;
+    __syncthreads();
+    // at most max(tiles_x, tiles_y) rounds: every round extends the distances by a tile
+    for (int round = 0; round <= max(P.tiles_x, P.tiles_y); ++round) {
+        if (threadIdx.x == 0) s_changed = 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            const int tx = t % P.tiles_x, ty = t / P.tiles_x;
+            int best = d[t];
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = tx + dx, y = ty + dy;
+                    if (x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y)
+                        best = min(best, *(volatile int *)&d[y * P.tiles_x + x] + 1);
+                }
+            if (best < d[t]) {
+                d[t] = best;
+                s_changed = 1;
+            }
+        }
+        __syncthreads();
+        if (!s_changed) break;
+        __syncthreads();
+    }
+    int far = 0;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) far = max(far, d[t]);
+    far = __reduce_max_sync(0xffffffffu, far);
+    __shared__ int s_far;
+    if (threadIdx.x == 0) s_far = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_far, far);
+    __syncthreads();
+    if (threadIdx.x == 0) const_cast<PairDev &>(P).seed_reach = s_far;
+    __syncthreads();
+}
+
+// Largest cost of every warp-tile pair (float bits; costs are >= 0, so the
+// bits order like the values, and a NaN or negative cost shows as a value
+// above +inf).  Work items are the write-out chunks (1024 pixels); each CTA
+// takes a contiguous run, its four groups of 256 threads an item at a time
+// (four pixels a thread), and a warp's running maximum goes out with one
+// atomic whenever its pair changes.
+__device__ void cost_max(const BatchArgs &a) {
+    const int per = (a.total_chunks + gridDim.x - 1) / gridDim.x;
+    const int c0 = blockIdx.x * per, c1 = min(a.total_chunks, c0 + per);
+    const int grp = threadIdx.x >> 8, gt = threadIdx.x & 255;   // warp-uniform group
+    int pi = -1;
+    unsigned mx = 0;
+    auto flush = [&]() {
+        const unsigned wm = __reduce_max_sync(0xffffffffu, mx);
+        if (pi >= 0 && (threadIdx.x & 31) == 0)
+            atomicMax(const_cast<unsigned *>(&a.pairs[pi].cmax_bits), wm);
+        mx = 0;
+    };
+    for (int c = c0 + grp; c < c1; c += 4) {
+        const int p = find_pair(a.chunk_base, a.npairs, c);
+        if (p != pi) {
+            flush();
+            pi = p;
+        }
+        const PairDev &P = a.pairs[p];
+        if (P.sweep != SWEEP_WARP) continue;
+        const long long npx = (long long)P.H * P.W;
+        const long long i = (long long)(c - a.chunk_base[p]) * WRITEOUT_CHUNK + 4 * gt;
+        if (i + 3 < npx && ((uintptr_t)P.C & 15) == 0) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(P.C + i));
+            mx = max(max(mx, __float_as_uint(v.x)), max(__float_as_uint(v.y), max(
+                         __float_as_uint(v.z), __float_as_uint(v.w))));
+        } else {
+            for (int j = 0; j < 4 && i + j < npx; ++j)
+                mx = max(mx, __float_as_uint(__ldg(P.C + i + j)));
+        }
+    }
+    flush();
+}
+
 __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restrict__ ap) {
     const BatchArgs a = *ap;
     RunState *st = a.state;
@@ -111,6 +198,7 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
             P.tile_seeds[atomicAdd(&P.tile_fill[t], 1)] = m;
         }
         __syncthreads();
+        if (P.sweep == SWEEP_WARP) seed_reach(P, T);
     }
     // clearing: edge table slots, CLEAR_CHUNK items each (the CSR adjacency
     // is written in full by the scatter and needs no clearing)
@@ -124,6 +212,7 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
             P.hw[i] = 0xFFFFFFFFu;
         }
     }
+    cost_max(a);
 }
 
 }  // namespace

@@ -390,6 +390,7 @@ __device__ bool stage_tile(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g
         plain_stage(P, T, g, keys, lane);
     }
     bool bad = false;
+    const int us = unit_shift(P);   // the pair's distance unit
     for (int r = 0; r <= g.rv + 1; ++r) {
         const int gy = g.y0 + r - 1;
         const bool row_in = gy >= 0 && gy < P.H;
@@ -401,8 +402,8 @@ __device__ bool stage_tile(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g
         *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = kk;
         // half-costs, in place
         uint2 cc = *reinterpret_cast<const uint2 *>(&T.hC[r][CO + c]);
-        cc.x = row_in && !g.outa ? half_cost(__uint_as_float(cc.x), &bad) : 0u;
-        cc.y = row_in && !g.outb ? half_cost(__uint_as_float(cc.y), &bad) : 0u;
+        cc.x = row_in && !g.outa ? half_cost_s(__uint_as_float(cc.x), us, &bad) : 0u;
+        cc.y = row_in && !g.outb ? half_cost_s(__uint_as_float(cc.y), us, &bad) : 0u;
         *reinterpret_cast<uint2 *>(&T.hC[r][CO + c]) = cc;
     }
     for (int r = lane; r < g.rv + 2; r += 32) {
@@ -411,8 +412,8 @@ __device__ bool stage_tile(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g
         const bool lin = row_in && g.x0 > 0, rin = row_in && g.x0 + RT_COLS < P.W;
         if (!keys || !lin) T.K[r][KO - 1] = KEY_INF;
         if (!keys || !rin) T.K[r][KO + RT_COLS] = KEY_INF;
-        T.hC[r][CO - 1] = lin ? half_cost(__uint_as_float(T.hC[r][CO - 1]), &bad) : 0u;
-        T.hC[r][CO + RT_COLS] = rin ? half_cost(__uint_as_float(T.hC[r][CO + RT_COLS]), &bad) : 0u;
+        T.hC[r][CO - 1] = lin ? half_cost_s(__uint_as_float(T.hC[r][CO - 1]), us, &bad) : 0u;
+        T.hC[r][CO + RT_COLS] = rin ? half_cost_s(__uint_as_float(T.hC[r][CO + RT_COLS]), us, &bad) : 0u;
     }
     if (__any_sync(FULL, bad) && lane == 0) set_status(st, EPIC_ERR_INVALID);
     __syncwarp();

@@ -36,6 +36,7 @@ EXPORTED = (
     "epic_interp_get_labels", "epic_interp_get_edge_count",
     "epic_interp_get_graph", "epic_interp_get_knn", "epic_interp_get_models",
     "epic_interp_get_pruning", "epic_interp_get_passes", "epic_interp_get_knn_retries",
+    "epic_interp_get_distance_unit",
     "epic_interp_set_tile_rules",
     "epic_interp_enable_stage_timing",
     "epic_interp_get_stage_times", "epic_interp_request_bytes",
@@ -141,6 +142,8 @@ def load(path: str | None = None):
     lib.epic_interp_get_pruning.restype = I
     lib.epic_interp_get_passes.argtypes = [P, pi]
     lib.epic_interp_get_passes.restype = I
+    lib.epic_interp_get_distance_unit.argtypes = [P, I, pi]
+    lib.epic_interp_get_distance_unit.restype = I
     lib.epic_interp_get_knn_retries.argtypes = [P, pi]
     lib.epic_interp_get_knn_retries.restype = I
     lib.epic_interp_set_tile_rules.argtypes = [P, ctypes.POINTER(epic_tile_rule_t), I]
@@ -417,6 +420,13 @@ class EpicInterp:
     def get_passes(self):
         n = ctypes.c_int()
         self._check(self.lib.epic_interp_get_passes(self.h, ctypes.byref(n)), "get_passes")
+        return n.value
+
+    def get_distance_unit(self, pair=0):
+        """Shift s of the pair's distance unit 2^-(31 - s) in the last run."""
+        n = ctypes.c_int()
+        self._check(self.lib.epic_interp_get_distance_unit(self.h, pair, ctypes.byref(n)),
+                    "get_distance_unit")
         return n.value
 
     def get_knn_retries(self):

@@ -386,3 +386,40 @@ def test_tma_and_plain_cost_staging_agree():
         eng.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["constant_cost_few_matches", "costs_up_to_8"])
+def test_wide_range_cost_maps(case):
+    # beyond the unit 2^-31 (costs below 2, distances below 1024): a constant
+    # cost of 1 on a 2048 x 1024 frame with four matches (distances up to
+    # ~1700) and costs uniform in [0, 8]; the pair's distance unit widens and
+    # the full parity rule holds.  A Sintel-shaped pair keeps the unit 2^-31.
+    from paper_1501_02565_gb300.native import EpicInterp
+    rng = np.random.default_rng(31)
+    if case == "constant_cost_few_matches":
+        H, W = 1024, 2048
+        C = np.ones((H, W), np.float32)
+        xs = np.array([5, 2040, 1000, 300], np.float32)
+        ys = np.array([3, 1000, 500, 900], np.float32)
+        K, a = 4, 0.01
+    else:
+        H, W = 256, 320
+        C = rng.uniform(0.0, 8.0, (H, W)).astype(np.float32)
+        flat = rng.choice(H * W, 80, replace=False)
+        xs, ys = (flat % W).astype(np.float32), (flat // W).astype(np.float32)
+        K, a = 16, 0.2
+    M = np.stack([xs, ys, xs + rng.normal(0, 2, len(xs)), ys + rng.normal(0, 2, len(xs))],
+                 1).astype(np.float32)
+    eng = EpicInterp(0, keep_intermediates=1, max_H=H, max_W=W)
+    g, ref, rep = full_parity((C, M), K=K, a=a, eng=eng)
+    shift = eng.get_distance_unit(0)
+    eng.close()
+    _print(f"{case} unit 2^-(31-{shift})", rep)
+    assert shift >= 1
+    eng = EpicInterp(0)
+    p = synth.config_pair(2, 0)
+    import torch
+    eng.run(torch.from_numpy(p.C).cuda(), torch.from_numpy(p.matches).cuda(), p.K, p.a)
+    eng.sync()
+    assert eng.get_distance_unit(0) == 0
+    eng.close()
