@@ -61,7 +61,8 @@ struct WarpTile {
     alignas(128) unsigned hC[MAXR + 2][CP];
     unsigned long long bar;   // mbarrier of the warp's TMA copies
 };
-static_assert(sizeof(WarpTile<16>) % 128 == 0 && sizeof(WarpTile<32>) % 128 == 0,
+static_assert(sizeof(WarpTile<8>) % 128 == 0 && sizeof(WarpTile<16>) % 128 == 0 &&
+                  sizeof(WarpTile<32>) % 128 == 0,
               "warp tiles stay 128-byte aligned in an array");
 
 __device__ __forceinline__ pkey_t kmin(pkey_t a, pkey_t b) { return b < a ? b : a; }
@@ -145,6 +146,15 @@ __device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, con
     from_up(u, kk.x, kk.y, ha, hb, na, nb);
     if (g.outa) na = KEY_INF;
     if (g.outb) nb = KEY_INF;
+    if (!__any_sync(FULL, (na != kk.x) | (nb != kk.y))) {
+        // nothing came from the upstream row: the row is unchanged, and it
+        // was closed along itself when it was last stepped
+        u.Pa = na;
+        u.Pb = nb;
+        u.pha = ha;
+        u.phb = hb;
+        return false;
+    }
     // closure along the row: each lane sweeps its pair left to right and back
     // with its neighbours' keys of the previous round, until a round changes
     // nothing anywhere (at most one round per two columns, plus one)
@@ -619,13 +629,19 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
 }  // namespace
 
 size_t relax_smem_bytes(int max_rows) {
-    return RT_WARPS * (max_rows <= 16 ? sizeof(WarpTile<16>) : sizeof(WarpTile<32>));
+    return RT_WARPS * (max_rows <= 8    ? sizeof(WarpTile<8>)
+                       : max_rows <= 16 ? sizeof(WarpTile<16>)
+                                        : sizeof(WarpTile<32>));
 }
 
 cudaError_t launch_relax(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                          int max_rows, bool fixed_grid, int *grid_used) {
     if (max_rows < 1 || max_rows > 32) return cudaErrorInvalidValue;
-    void (*kernel)(const BatchArgs *) = max_rows <= 16 ? relax_kernel<16> : relax_kernel<32>;
+    // instances for tile heights up to 8, 16 and 32: the smaller the tile,
+    // the less shared memory a warp holds and the more warps share an SM
+    void (*kernel)(const BatchArgs *) = max_rows <= 8    ? relax_kernel<8>
+                                        : max_rows <= 16 ? relax_kernel<16>
+                                                         : relax_kernel<32>;
     const size_t smem = relax_smem_bytes(max_rows);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

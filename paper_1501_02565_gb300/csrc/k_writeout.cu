@@ -2,25 +2,27 @@
 //
 // Every pixel p takes the model of its cell's match m = L(p):
 //     flow(p) = F(p) - p = c_m + B_m (p - p_m).
-// The kernel is a single pass over the packed keys (8 B in) and the flow
-// (8 B out) of every pixel of the batch, so it is bound by HBM bandwidth:
-//   * a work item is WRITEOUT_CHUNK pixels of one pair, and each CTA takes a
-//     contiguous run of items, so the pair of an item is found once per run
-//     and then followed forward (no search per item);
-//   * a thread handles eight consecutive pixels: its four 16-byte key loads
-//     are all issued before the first model gather, so each thread keeps 64
-//     bytes of loads in flight;
+// The kernel is a single pass over the labels (4 B in, the plane the edge
+// stage writes beside the packed keys) and the flow (8 B out) of every pixel
+// of the batch, so it is bound by HBM bandwidth:
+//   * a work item is WRITEOUT_CHUNK pixels of one pair; each CTA takes a
+//     contiguous run of items, two at a time (one per half of the CTA), so
+//     the pair of an item is found once per run and followed forward;
+//   * a thread handles eight consecutive pixels: its two 16-byte label loads
+//     are issued before the first model gather;
 //   * the model table (32 bytes per match, a few MB for a batch) is read
 //     through the read-only path, where it stays cache resident; flows are
 //     written with streaming 16-byte stores.
+// The grid is one resident wave.
 #include "epic_internal.cuh"
 
 namespace epic {
 
 namespace {
 
-constexpr int WO_THREADS = 128;
-constexpr int WO_PER_THREAD = WRITEOUT_CHUNK / WO_THREADS;
+constexpr int WO_THREADS = 256;
+constexpr int WO_GROUP = 128;   // threads per work item
+constexpr int WO_PER_THREAD = WRITEOUT_CHUNK / WO_GROUP;
 static_assert(WO_PER_THREAD == 8, "eight pixels per thread");
 
 __device__ __forceinline__ float2 apply(const float4 *models, unsigned m, int n, int x,
@@ -38,13 +40,14 @@ __global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *_
     const PairDev *pairs = ap->pairs;
     const int *chunk_base = ap->chunk_base;
     const int npairs = ap->npairs, total = ap->total_chunks;
-    // contiguous runs of items per CTA
-    const int per = (total + gridDim.x - 1) / gridDim.x;
+    const int grp = threadIdx.x / WO_GROUP, gt = threadIdx.x % WO_GROUP;
+    // contiguous runs of items per CTA; the two halves take alternate items
+    const int per = ((total + gridDim.x - 1) / gridDim.x + 1) & ~1;
     const int c0 = blockIdx.x * per, c1 = min(total, c0 + per);
-    if (c0 >= c1) return;
-    int pi = find_pair(chunk_base, npairs, c0);
+    if (c0 + grp >= c1) return;
+    int pi = find_pair(chunk_base, npairs, c0 + grp);
     int next_base = __ldg(chunk_base + pi + 1);
-    for (int c = c0; c < c1; ++c) {
+    for (int c = c0 + grp; c < c1; c += 2) {
         while (c >= next_base) {
             ++pi;
             next_base = __ldg(chunk_base + pi + 1);
@@ -53,23 +56,22 @@ __global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *_
         const int W = P.W, N = P.N;
         const long long npix = (long long)P.H * W;
         const long long p0 = (long long)(c - __ldg(chunk_base + pi)) * WRITEOUT_CHUNK +
-                             (long long)threadIdx.x * WO_PER_THREAD;
+                             (long long)gt * WO_PER_THREAD;
         if (p0 >= npix) continue;
-        const pkey_t *keys = P.keys;
+        const unsigned *labels = P.labels;
         const float4 *models = P.models;
         float *flow = P.flow;
         int y = (int)(p0 / W), x = (int)(p0 - (long long)y * W);
         if (P.flow_vec_ok && p0 + WO_PER_THREAD <= npix) {
-            ulonglong2 k[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                k[i] = __ldcs(reinterpret_cast<const ulonglong2 *>(keys + p0) + i);
+            const uint4 l0 = __ldcs(reinterpret_cast<const uint4 *>(labels + p0));
+            const uint4 l1 = __ldcs(reinterpret_cast<const uint4 *>(labels + p0) + 1);
+            const unsigned ls[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
             float4 o[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float2 v0 = apply(models, key_label(k[i].x), N, x, y);
+                const float2 v0 = apply(models, ls[2 * i], N, x, y);
                 if (++x == W) { x = 0; ++y; }
-                const float2 v1 = apply(models, key_label(k[i].y), N, x, y);
+                const float2 v1 = apply(models, ls[2 * i + 1], N, x, y);
                 if (++x == W) { x = 0; ++y; }
                 o[i] = make_float4(v0.x, v0.y, v1.x, v1.y);
             }
@@ -78,8 +80,7 @@ __global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *_
             for (int i = 0; i < 4; ++i) __stcs(out + i, o[i]);
         } else {
             for (int i = 0; i < WO_PER_THREAD && p0 + i < npix; ++i) {
-                const pkey_t kk = __ldg(keys + p0 + i);
-                const float2 v = apply(models, key_label(kk), N, x, y);
+                const float2 v = apply(models, __ldg(labels + p0 + i), N, x, y);
                 flow[2 * (p0 + i)] = v.x;
                 flow[2 * (p0 + i) + 1] = v.y;
                 if (++x == W) { x = 0; ++y; }
@@ -92,8 +93,6 @@ __global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *_
 
 cudaError_t launch_writeout(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc) {
     (void)a;
-    // one resident wave: every CTA runs its contiguous share at once (a
-    // second, partial wave would leave most of the GPU idle at the end)
     int per_sm = 0;
     cudaError_t e =
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, writeout_kernel, WO_THREADS, 0);

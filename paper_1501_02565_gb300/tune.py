@@ -21,7 +21,7 @@ import os
 # tiles of 64 x tile_h (the interpolator's default relaxation); the library
 # uses them only when every rule asks for them, so a rule set is tuned from
 # one family at a time.
-CANDIDATES = ((64, 32, 0, 2), (64, 24, 0, 2), (64, 16, 0, 2))
+CANDIDATES = ((64, 32, 0, 2), (64, 16, 0, 2), (64, 12, 0, 2), (64, 8, 0, 2))
 # sweep 0 / 1: the sweep schedules of the tiled relaxation with an apron
 # (region = tile + 2 apron within shared memory at 256 threads per CTA)
 SWEEP_CANDIDATES = (
