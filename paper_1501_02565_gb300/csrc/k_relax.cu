@@ -135,10 +135,13 @@ __device__ __forceinline__ void from_up(const Up &u, pkey_t Ka, pkey_t Kb, unsig
 // Step row y from the upstream row (registers u, already with neighbours):
 // three candidates per pixel, then the closure along the row (ring columns
 // fixed).  Writes the row back if it changed; returns whether it did.  On
-// return u holds row y (for the next row of the pass).
+// return u holds row y (for the next row of the pass).  must_close: the row
+// is stepped for its own sake (seeds, ring neighbours) and may not be closed
+// along itself yet; otherwise it was closed when it was last stepped, and if
+// the upstream row improves none of its pixels nothing can change.
 template <int MAXR>
 __device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, const TileGeo &g,
-                                         Up &u) {
+                                         Up &u, bool must_close) {
     const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[y][KO + 2 * lane]);
     const uint2 hh = *reinterpret_cast<const uint2 *>(&T.hC[y][CO + 2 * lane]);
     const unsigned ha = hh.x, hb = hh.y;
@@ -146,7 +149,7 @@ __device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, con
     from_up(u, kk.x, kk.y, ha, hb, na, nb);
     if (g.outa) na = KEY_INF;
     if (g.outb) nb = KEY_INF;
-    if (!__any_sync(FULL, (na != kk.x) | (nb != kk.y))) {
+    if (!must_close && !__any_sync(FULL, (na != kk.x) | (nb != kk.y))) {
         // nothing came from the upstream row: the row is unchanged, and it
         // was closed along itself when it was last stepped
         u.Pa = na;
@@ -222,12 +225,13 @@ __device__ unsigned long long tile_passes(WarpTile<MAXR> &T, int lane, const Til
             const int yu = down ? y - 1 : y + 1;
             unsigned long long &fl = down ? forD : forU;
             unsigned long long &sf = down ? selfD : selfU;
-            if (!(((fl >> yu) | (sf >> y)) & 1ull)) continue;
+            const bool self = (sf >> y) & 1ull;
+            if (!(((fl >> yu) & 1ull) | self)) continue;
             fl &= ~(1ull << yu);
             sf &= ~(1ull << y);
             if (have != yu) load_up(T, yu, lane, u);
             neighbours_up(T, yu, lane, u);
-            if (row_step(T, y, lane, g, u)) {
+            if (row_step(T, y, lane, g, u, self)) {
                 forD |= 1ull << y;
                 forU |= 1ull << y;
                 modified |= 1ull << y;
