@@ -70,11 +70,12 @@ __device__ __forceinline__ void table_insert(const PairDev &P, pkey_t k,
 constexpr int TILE_TABLE = 1024;  // shared-memory slots per CTA (power of two)
 
 // Claim the shared-table slot of key k (or find it); -1 if the probe
-// sequence is full.
-__device__ __forceinline__ int smem_claim(pkey_t *sk, pkey_t k) {
+// sequence is full.  A newly claimed slot is counted in *fill.
+__device__ __forceinline__ int smem_claim(pkey_t *sk, pkey_t k, int *fill) {
     unsigned s = hash_slot(k, TILE_TABLE);
     for (int probe = 0; probe < 64; ++probe) {
         const pkey_t prev = atomicCAS(sk + s, EMPTY64, k);
+        if (prev == EMPTY64) atomicAdd(fill, 1);
         if (prev == EMPTY64 || prev == k) return (int)s;
         s = (s + 1) & (TILE_TABLE - 1);
     }
@@ -87,13 +88,13 @@ __device__ __forceinline__ int smem_claim(pkey_t *sk, pkey_t k) {
 // table is full, inserts straight into the global table).
 __device__ __forceinline__ void warp_insert(const PairDev &P, bool have, pkey_t k,
                                             unsigned wbits, pkey_t *sk, unsigned *sw,
-                                            RunState *st) {
+                                            int *fill, RunState *st) {
     if (!__any_sync(0xffffffffu, have)) return;
     const unsigned lane = threadIdx.x & 31;
     const unsigned grp = __match_any_sync(0xffffffffu, have ? k : EMPTY64);
     const int leader = __ffs(grp) - 1;
     int slot = -1;
-    if (have && lane == (unsigned)leader) slot = smem_claim(sk, k);
+    if (have && lane == (unsigned)leader) slot = smem_claim(sk, k, fill);
     slot = __shfl_sync(0xffffffffu, slot, leader);
     if (have) {
         if (slot >= 0)
@@ -110,6 +111,25 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
     __shared__ int s_tile, s_pair, s_local;
     __shared__ pkey_t sk[TILE_TABLE];
     __shared__ unsigned sw[TILE_TABLE];
+    // the shared table collects the edges of consecutive tiles of one pair
+    // and goes to the pair's global table when half full, when the next tile
+    // belongs to another pair, and at the end
+    __shared__ int s_fill, s_tab_pair;
+    auto clear_table = [&]() {
+        for (int i = threadIdx.x; i < TILE_TABLE; i += blockDim.x) {
+            sk[i] = EMPTY64;
+            sw[i] = 0xFFFFFFFFu;
+        }
+        if (threadIdx.x == 0) s_fill = 0;
+        __syncthreads();
+    };
+    auto flush_table = [&](const PairDev &Q) {
+        for (int i = threadIdx.x; i < TILE_TABLE; i += blockDim.x)
+            if (sk[i] != EMPTY64) table_insert(Q, sk[i], sw[i], st);
+        __syncthreads();
+    };
+    if (threadIdx.x == 0) s_tab_pair = -1;
+    clear_table();
     // the tile's keys and half-costs plus the column on each side and the
     // row below (every forward neighbour), staged with coalesced loads that
     // are all in flight at once; cells outside the image hold KEY_INF
@@ -127,10 +147,14 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
         }
         __syncthreads();
         if (s_tile >= a.total_tiles) break;
-        for (int i = threadIdx.x; i < TILE_TABLE; i += blockDim.x) {
-            sk[i] = EMPTY64;
-            sw[i] = 0xFFFFFFFFu;
+        // every thread takes the same decision from the shared values; they
+        // change only after the barrier below
+        if (s_tab_pair >= 0 && (s_tab_pair != s_pair || s_fill > TILE_TABLE / 2)) {
+            flush_table(a.pairs[s_tab_pair]);
+            clear_table();
         }
+        __syncthreads();
+        if (threadIdx.x == 0) s_tab_pair = s_pair;
         const PairDev &P = a.pairs[s_pair];
         const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
         const int npx = P.tile_w * P.tile_h;
@@ -215,14 +239,11 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                 cv[d] = have;
             }
 #pragma unroll
-            for (int d = 0; d < 4; ++d) warp_insert(P, cv[d], ck[d], cw[d], sk, sw, st);
+            for (int d = 0; d < 4; ++d) warp_insert(P, cv[d], ck[d], cw[d], sk, sw, &s_fill, st);
         }
         __syncthreads();
-        // flush the tile's unique edges to the pair's table
-        for (int i = threadIdx.x; i < TILE_TABLE; i += blockDim.x)
-            if (sk[i] != EMPTY64) table_insert(P, sk[i], sw[i], st);
-        __syncthreads();
     }
+    if (s_tab_pair >= 0) flush_table(a.pairs[s_tab_pair]);
     // duplicate source pixels: join an ownerless match to its pixel's owner
     for (int gm = blockIdx.x * blockDim.x + threadIdx.x; gm < a.total_matches;
          gm += gridDim.x * blockDim.x) {

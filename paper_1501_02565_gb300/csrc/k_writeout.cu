@@ -8,11 +8,14 @@
 //   * a work item is WRITEOUT_CHUNK pixels of one pair; each CTA takes a
 //     contiguous run of items, two at a time (one per half of the CTA), so
 //     the pair of an item is found once per run and followed forward;
-//   * a thread handles eight consecutive pixels: its two 16-byte label loads
-//     are issued before the first model gather;
+//   * a warp handles 256 consecutive pixels as four rounds of 64: in each
+//     round lane l takes pixels 2l and 2l + 1, so every label load (8 bytes
+//     a lane) and every flow store (16 bytes a lane) of the warp is one
+//     contiguous run of 256 or 512 bytes; all four label loads are issued
+//     before the first model gather;
 //   * the model table (32 bytes per match, a few MB for a batch) is read
 //     through the read-only path, where it stays cache resident; flows are
-//     written with streaming 16-byte stores.
+//     written with streaming stores.
 // The grid is one resident wave.
 #include "epic_internal.cuh"
 
@@ -21,9 +24,8 @@ namespace epic {
 namespace {
 
 constexpr int WO_THREADS = 256;
-constexpr int WO_GROUP = 128;   // threads per work item
-constexpr int WO_PER_THREAD = WRITEOUT_CHUNK / WO_GROUP;
-static_assert(WO_PER_THREAD == 8, "eight pixels per thread");
+constexpr int WO_GROUP = 128;   // threads per work item (four warps of 256 pixels)
+static_assert(WRITEOUT_CHUNK == (WO_GROUP / 32) * 256, "a work item is four warps' pixels");
 
 __device__ __forceinline__ float2 apply(const float4 *models, unsigned m, int n, int x,
                                         int y) {
@@ -55,35 +57,34 @@ __global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *_
         const PairDev &P = pairs[pi];
         const int W = P.W, N = P.N;
         const long long npix = (long long)P.H * W;
-        const long long p0 = (long long)(c - __ldg(chunk_base + pi)) * WRITEOUT_CHUNK +
-                             (long long)gt * WO_PER_THREAD;
-        if (p0 >= npix) continue;
+        // this warp's 256 pixels of the item
+        const long long pw = (long long)(c - __ldg(chunk_base + pi)) * WRITEOUT_CHUNK +
+                             (long long)(gt >> 5) * 256;
+        if (pw >= npix) continue;
+        const int lane = gt & 31;
         const unsigned *labels = P.labels;
         const float4 *models = P.models;
         float *flow = P.flow;
-        int y = (int)(p0 / W), x = (int)(p0 - (long long)y * W);
-        if (P.flow_vec_ok && p0 + WO_PER_THREAD <= npix) {
-            const uint4 l0 = __ldcs(reinterpret_cast<const uint4 *>(labels + p0));
-            const uint4 l1 = __ldcs(reinterpret_cast<const uint4 *>(labels + p0) + 1);
-            const unsigned ls[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-            float4 o[4];
+        if (P.flow_vec_ok && pw + 256 <= npix) {
+            uint2 l[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                l[i] = __ldcs(reinterpret_cast<const uint2 *>(labels + pw + 64 * i + 2 * lane));
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float2 v0 = apply(models, ls[2 * i], N, x, y);
+                const long long q = pw + 64 * i + 2 * lane;
+                int y = (int)(q / W), x = (int)(q - (long long)y * W);
+                const float2 v0 = apply(models, l[i].x, N, x, y);
                 if (++x == W) { x = 0; ++y; }
-                const float2 v1 = apply(models, ls[2 * i + 1], N, x, y);
-                if (++x == W) { x = 0; ++y; }
-                o[i] = make_float4(v0.x, v0.y, v1.x, v1.y);
+                const float2 v1 = apply(models, l[i].y, N, x, y);
+                __stcs(reinterpret_cast<float4 *>(flow + 2 * q), make_float4(v0.x, v0.y, v1.x, v1.y));
             }
-            float4 *out = reinterpret_cast<float4 *>(flow + 2 * p0);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) __stcs(out + i, o[i]);
         } else {
-            for (int i = 0; i < WO_PER_THREAD && p0 + i < npix; ++i) {
-                const float2 v = apply(models, __ldg(labels + p0 + i), N, x, y);
-                flow[2 * (p0 + i)] = v.x;
-                flow[2 * (p0 + i) + 1] = v.y;
-                if (++x == W) { x = 0; ++y; }
+            for (long long q = pw + lane; q < pw + 256 && q < npix; q += 32) {
+                const int y = (int)(q / W), x = (int)(q - (long long)y * W);
+                const float2 v = apply(models, __ldg(labels + q), N, x, y);
+                flow[2 * q] = v.x;
+                flow[2 * q + 1] = v.y;
             }
         }
     }
