@@ -130,7 +130,6 @@ struct PairDev {
     int hash_cap;           // power of two
     int flow_vec_ok;        // flow pointer is 16-byte aligned
     pkey_t *keys;            // [H*W] packed (D, L)
-    unsigned *labels;        // [H*W] L alone, written by the edge stage for the write-out
     // exact variant only (null elsewhere): a distance offset per seed (units),
     // and a key map whose distances cap the keys written back (a pixel whose
     // distance exceeds its cap is left unreached)

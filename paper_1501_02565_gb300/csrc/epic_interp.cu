@@ -177,7 +177,7 @@ bool uses_warp_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t>
 }
 
 struct Layout {
-    size_t keys, labels, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, wmin2, wnear,
+    size_t keys, tile_start, tile_fill, tile_seeds, tile_stamp, hkeys, hw, deg, wmin, wmin2, wnear,
         row, adj, models,
         fallback, knn_idx, knn_dist, knn_count, info, keep, pruned, kept_index, end;
 };
@@ -196,7 +196,6 @@ Layout layout_pair(size_t base, const PairDev &P, int max_degree, bool keep, boo
         return at;
     };
     L.keys = take(npx * sizeof(pkey_t));
-    L.labels = take(npx * sizeof(unsigned));
     L.tile_start = take((T + 1) * sizeof(int));
     L.tile_fill = take(T * sizeof(int));
     L.tile_seeds = take((size_t)P.N * sizeof(int));
@@ -577,7 +576,6 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
         encode_cost_maps(P[i]);
         char *b = h->arena;
         P[i].keys = reinterpret_cast<pkey_t *>(b + L[i].keys);
-        P[i].labels = reinterpret_cast<unsigned *>(b + L[i].labels);
         P[i].tile_start = reinterpret_cast<int *>(b + L[i].tile_start);
         P[i].tile_fill = reinterpret_cast<int *>(b + L[i].tile_fill);
         P[i].tile_seeds = reinterpret_cast<int *>(b + L[i].tile_seeds);

@@ -186,8 +186,6 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
             if (act) {
                 kp = skey[ly * SC + lx + 1];
                 hp = sh[ly * SC + lx + 1];
-                // the label plane the write-out reads (4 of the key's 8 bytes)
-                P.labels[(size_t)y * W + x] = key_label(kp);
             }
             // the four forward candidates of this pixel; a label pair seen in
             // an earlier direction is folded into that one (min weight), so

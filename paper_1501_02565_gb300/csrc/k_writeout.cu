@@ -2,17 +2,16 @@
 //
 // Every pixel p takes the model of its cell's match m = L(p):
 //     flow(p) = F(p) - p = c_m + B_m (p - p_m).
-// The kernel is a single pass over the labels (4 B in, the plane the edge
-// stage writes beside the packed keys) and the flow (8 B out) of every pixel
-// of the batch, so it is bound by HBM bandwidth:
+// The kernel is a single pass over the packed keys (8 B in, of which the
+// label is the 4 B the method needs) and the flow (8 B out) of every pixel of
+// the batch, so it is bound by HBM bandwidth:
 //   * a work item is WRITEOUT_CHUNK pixels of one pair; each CTA takes a
 //     contiguous run of items, two at a time (one per half of the CTA), so
 //     the pair of an item is found once per run and followed forward;
 //   * a warp handles 256 consecutive pixels as four rounds of 64: in each
-//     round lane l takes pixels 2l and 2l + 1, so every label load (8 bytes
-//     a lane) and every flow store (16 bytes a lane) of the warp is one
-//     contiguous run of 256 or 512 bytes; all four label loads are issued
-//     before the first model gather;
+//     round lane l takes pixels 2l and 2l + 1, so every key load and every
+//     flow store (16 bytes a lane) of the warp is one contiguous run of 512
+//     bytes; all four key loads are issued before the first model gather;
 //   * the model table (32 bytes per match, a few MB for a batch) is read
 //     through the read-only path, where it stays cache resident; flows are
 //     written with streaming stores.
@@ -62,27 +61,27 @@ __global__ void __launch_bounds__(WO_THREADS) writeout_kernel(const BatchArgs *_
                              (long long)(gt >> 5) * 256;
         if (pw >= npix) continue;
         const int lane = gt & 31;
-        const unsigned *labels = P.labels;
+        const pkey_t *keys = P.keys;
         const float4 *models = P.models;
         float *flow = P.flow;
         if (P.flow_vec_ok && pw + 256 <= npix) {
-            uint2 l[4];
+            ulonglong2 k[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                l[i] = __ldcs(reinterpret_cast<const uint2 *>(labels + pw + 64 * i + 2 * lane));
+                k[i] = __ldcs(reinterpret_cast<const ulonglong2 *>(keys + pw + 64 * i + 2 * lane));
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const long long q = pw + 64 * i + 2 * lane;
                 int y = (int)(q / W), x = (int)(q - (long long)y * W);
-                const float2 v0 = apply(models, l[i].x, N, x, y);
+                const float2 v0 = apply(models, key_label(k[i].x), N, x, y);
                 if (++x == W) { x = 0; ++y; }
-                const float2 v1 = apply(models, l[i].y, N, x, y);
+                const float2 v1 = apply(models, key_label(k[i].y), N, x, y);
                 __stcs(reinterpret_cast<float4 *>(flow + 2 * q), make_float4(v0.x, v0.y, v1.x, v1.y));
             }
         } else {
             for (long long q = pw + lane; q < pw + 256 && q < npix; q += 32) {
                 const int y = (int)(q / W), x = (int)(q - (long long)y * W);
-                const float2 v = apply(models, __ldg(labels + q), N, x, y);
+                const float2 v = apply(models, key_label(__ldg(keys + q)), N, x, y);
                 flow[2 * q] = v.x;
                 flow[2 * q + 1] = v.y;
             }

@@ -1,7 +1,7 @@
 """epic_interp_request_bytes (no GPU): the arena bytes the library reports for
 one pair equal the carve-up of its scratch arena, rebuilt here from the
 layout the library documents: every region 256-byte aligned, in the order
-keys u64 [P]; labels u32 [P]; seed bins int [T+1], [T], [N]; tile stamps [T]; edge table u64
+keys u64 [P]; seed bins int [T+1], [T], [N]; tile stamps [T]; edge table u64
 and u32 [cap] with cap = max(1024, pow2 >= 8N); degree, lightest edge,
 second-lightest edge, its other end [N] each; CSR row offsets [N+1] and
 16-byte adjacency entries [2 cap]; models 2 x float4 [N]; fallback flags [N];
@@ -25,7 +25,7 @@ def carve(H, W, N, K, tile=(64, 32), keep=False, prune=False, prune_K=25):
     while cap < 8 * N:
         cap *= 2
     Kc = max(min(prune_K, N), min(K, N)) if prune else min(K, N)
-    regions = [8 * P, 4 * P, 4 * (T + 1), 4 * T, 4 * N, 4 * T, 8 * cap, 4 * cap,
+    regions = [8 * P, 4 * (T + 1), 4 * T, 4 * N, 4 * T, 8 * cap, 4 * cap,
                4 * N, 4 * N, 4 * N, 4 * N, 4 * (N + 1), 16 * 2 * cap, 32 * N, 4 * N]
     if keep:
         regions += [4 * N * Kc, 4 * N * Kc, 4 * N]
