@@ -99,8 +99,9 @@ typedef struct {
     float fallback_eps;   /* fit is degenerate when det M <= eps (tr M/3)^3
                              or fewer than 3 neighbours; then the NW estimate
                              of Eq. 1 at p_m is used as a constant flow */
-    int tile_w, tile_h;   /* relaxation tile (0 = 64 x 32); with sweep 2 the
-                             width is always 64 and tile_h at most 32 */
+    int tile_w, tile_h;   /* relaxation tile (0 = 64 x 16 with sweep 2, else
+                             64 x 32); with sweep 2 the width is always 64
+                             and tile_h at most 32 */
     int apron;            /* sweep 0 / 1: extra context around a tile in the
                              first relaxation pass (-1 = 4); sweep 2: none */
     int keep_intermediates; /* 1: keep K-NN lists for epic_interp_get_knn */

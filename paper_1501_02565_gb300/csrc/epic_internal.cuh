@@ -202,7 +202,7 @@ struct RunState {
     int status;            // first device error (epic_status_t), 0 = OK
     int passes;            // relaxation verification passes of the last run
     unsigned changed[3];   // per-pass dirty-tile counters (rotating)
-    unsigned work[4];      // relaxation tile dispensers: passes (rotating), phase 1
+    unsigned work[5];      // relaxation tile dispensers: passes (rotating), phase 1 (two halves)
     unsigned knn_next;     // K-NN match dispenser
     unsigned knn_overflow; // matches whose search outgrew the small tables
     unsigned knn_retry;    // dispenser of the retry pass over those matches
@@ -324,6 +324,8 @@ struct LaunchCfg {
     int num_sms;
     int smem_optin;  // max dynamic shared memory per CTA (opt-in)
     cudaStream_t stream;
+    int smem_per_sm = 0;    // shared memory per SM (0: unknown)
+    int smem_reserved = 0;  // shared memory the system reserves per CTA
 };
 // Launchers: `a` is the host copy of the launch arguments (used only for
 // launch-shape decisions), `dev` the same struct in device memory (the
@@ -393,9 +395,9 @@ constexpr int RELAX_MAX_ROWS = 32;
 size_t relax_smem_bytes(int max_rows);
 cudaError_t launch_relax(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                          int max_rows, bool fixed_grid, int *grid_used);
-void knn_table_sizes(int max_K, int *hs, int *fs);
+void knn_table_sizes(int max_K, const LaunchCfg &lc, int *hs, int *fs);
 void knn_retry_table_sizes(int max_K, int smem_limit, int *hs, int *fs);
-size_t knn_smem_per_warp(int max_K);
-int knn_warps_per_cta(int max_K, int smem_limit);
+size_t knn_smem_per_warp(int max_K, const LaunchCfg &lc);
+int knn_warps_per_cta(int max_K, const LaunchCfg &lc);
 
 }  // namespace epic

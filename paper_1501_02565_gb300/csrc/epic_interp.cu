@@ -30,6 +30,7 @@ struct epic_interp {
     int device = 0;
     int num_sms = 0;
     int smem_optin = 0;
+    int smem_per_sm = 0, smem_reserved = 0;
     epic_config_t cfg{};
     char *arena = nullptr;
     size_t arena_bytes = 0;
@@ -128,6 +129,11 @@ int next_pow2(long long x) {
 // default k_dt.cu tile.
 constexpr int SWEEP_WARP_TILES = 2;
 
+// Tile height when neither the configuration nor a rule gives one: 16 rows
+// for warp tiles (what the tile autotuner picks for frames above 64 K
+// pixels), 32 for the apron tiles.
+int default_tile_h(int sweep) { return sweep == SWEEP_WARP_TILES ? 16 : 32; }
+
 void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &rules, int H,
                   int W, int *tw, int *th, int *ap, int *sweep = nullptr,
                   bool warp_tiles_ok = true) {
@@ -146,7 +152,7 @@ void choose_tiles(const epic_config_t &c, const std::vector<epic_tile_rule_t> &r
     }
     if (!found) {
         *tw = c.tile_w > 0 ? c.tile_w : 64;
-        *th = c.tile_h > 0 ? c.tile_h : 32;
+        *th = c.tile_h > 0 ? c.tile_h : default_tile_h(s);
         *ap = c.apron >= 0 ? c.apron : (s == SWEEP_WARP_TILES ? 0 : 4);
     }
     if (s == SWEEP_WARP_TILES) {
@@ -495,6 +501,8 @@ int epic_interp_create(epic_interp_t **out, int device, const epic_config_t *cfg
     if (e != cudaSuccess) { delete h; return EPIC_ERR_CUDA; }
     h->num_sms = prop.multiProcessorCount;
     h->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    h->smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
+    h->smem_reserved = (int)prop.reservedSharedMemPerBlock;
     // the run state, then a scratch counter
     e = cudaMalloc(&h->state, sizeof(RunState) + 64);
     if (e != cudaSuccess) { delete h; return EPIC_ERR_OOM; }
@@ -642,7 +650,8 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     // the configured tile counts unless a rule covers every frame size
     bool rules_cover_all = false;
     for (const auto &r : h->rules) rules_cover_all |= r.max_pixels >= (1LL << 30);
-    int cfg_tw = c.tile_w > 0 ? c.tile_w : 64, cfg_th = c.tile_h > 0 ? c.tile_h : 32;
+    int cfg_tw = c.tile_w > 0 ? c.tile_w : 64,
+        cfg_th = c.tile_h > 0 ? c.tile_h : default_tile_h(c.sweep);
     int cfg_ap = c.apron >= 0 ? c.apron : (warp_tiles ? 0 : 4);
     if (rules_cover_all) cfg_tw = cfg_th = 1, cfg_ap = 0;
     for (const auto &r : h->rules) {
@@ -686,7 +695,9 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     a.total_hash = (int)th;
     a.total_clear = (int)tcl;
     a.max_degree = c.max_degree;
-    epic::knn_table_sizes(knn_K, &a.knn_hs, &a.knn_fs);
+    const epic::LaunchCfg size_lc{h->num_sms, h->smem_optin, stream, h->smem_per_sm,
+                                  h->smem_reserved};
+    epic::knn_table_sizes(knn_K, size_lc, &a.knn_hs, &a.knn_fs);
     a.knn_kmax = knn_K;
     a.knn_retry_list = reinterpret_cast<int *>(h->arena + retry_off);
     a.max_passes = c.max_passes;
@@ -697,7 +708,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     a.write_keep = c.prune ? 1 : 0;
     a.prune_threshold = c.prune_threshold;
     a.state = h->state;
-    if (epic::knn_warps_per_cta(knn_K, h->smem_optin) < 1)
+    if (epic::knn_warps_per_cta(knn_K, size_lc) < 1)
         return fail(h, EPIC_ERR_INVALID, "K too large for the per-warp search tables");
     if ((warp_tiles ? epic::relax_smem_bytes(dt_th) : epic::dt_smem_bytes(dt_tw, dt_th, dt_ap)) >
         (size_t)h->smem_optin)
@@ -711,7 +722,7 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     for (int k = 0; k < 5; ++k) memcpy(hs + args_bytes + pd_bytes + k * pre_stride, pres[k], pre_bytes);
     const BatchArgs *dev_a = reinterpret_cast<const BatchArgs *>(sl.dev);
 
-    epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
+    epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream, h->smem_per_sm, h->smem_reserved};
     BatchArgs *dev_rw = reinterpret_cast<BatchArgs *>(sl.dev);
     auto relax = [&]() -> cudaError_t {
         return warp_tiles ? epic::launch_relax(a, dev_a, lc, dt_th, graph, nullptr)
@@ -1239,7 +1250,7 @@ int epic_exact_interp(epic_interp_t *h, const float *cost_map, const float *matc
             reinterpret_cast<char *>(vinit) + align_up((size_t)N * sizeof(unsigned long long), 256));
         int *wl = reinterpret_cast<int *>(cb + c_bytes);   // [3][Cm * T], then [Cm * T] marks
         std::vector<char> thost(t_bytes);
-        epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream};
+        epic::LaunchCfg lc{h->num_sms, h->smem_optin, stream, h->smem_per_sm, h->smem_reserved};
 
         // Cap map.  An approximate run keeps its K-NN lists: each match's
         // K-th nearest graph distance bounds its K-th nearest geodesic

@@ -615,11 +615,23 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
 
 // Main-pass tables: ~3.84 K node slots (the searches here touch about 1.5 K
 // nodes) and ~1.92 K frontier entries, so that 8 warps' tables fit four CTAs
-// on an SM; a search that outgrows them is run again with large tables.
-void knn_table_sizes(int max_K, int *hs, int *fs) {
+// on an SM up to K ~ 100.  For larger K the tables shrink to what four CTAs
+// leave (a frontier of at least 1.4 K entries and a node table twice that:
+// the largest frontier seen on these graphs is ~1.2 K); a search that
+// outgrows them is run again with large tables.
+void knn_table_sizes(int max_K, const LaunchCfg &lc, int *hs, int *fs) {
     const int k = max_K > 1 ? max_K : 1;
     *hs = std::max(64, (k * 384 / 100 + 31) / 32 * 32);
     *fs = std::max(64, (k * 192 / 100 + 31) / 32 * 32);
+    if (lc.smem_per_sm <= 0) return;
+    const long long per_warp = ((long long)lc.smem_per_sm / 4 - lc.smem_reserved) / KNN_WARPS;
+    const long long fixed = (long long)k * 8 + (((long long)k * 2 + 7) & ~7LL);
+    if ((long long)*fs * 16 + (long long)*hs * 8 + fixed <= per_warp) return;
+    const long long f = (per_warp - fixed) / 32;   // 16 B per entry + 2 slots of 8 B
+    if (f * 10 >= 14LL * k) {
+        *fs = (int)f;
+        *hs = 2 * (int)f;
+    }
 }
 
 // Retry-pass tables: the largest power-of-two node table (and a frontier
@@ -631,27 +643,27 @@ void knn_retry_table_sizes(int max_K, int smem_limit, int *hs, int *fs) {
     *fs = h / 2;
 }
 
-size_t knn_smem_per_warp(int max_K) {
+size_t knn_smem_per_warp(int max_K, const LaunchCfg &lc) {
     int hs, fs;
-    knn_table_sizes(max_K, &hs, &fs);
+    knn_table_sizes(max_K, lc, &hs, &fs);
     return knn_warp_bytes(hs, fs, max_K);
 }
 
 // Largest warps-per-CTA (<= KNN_WARPS) whose tables fit in shared memory;
 // 0 if even one warp's tables do not fit.
-int knn_warps_per_cta(int max_K, int smem_limit) {
-    size_t pw = knn_smem_per_warp(max_K);
-    int w = (int)(smem_limit / pw);
+int knn_warps_per_cta(int max_K, const LaunchCfg &lc) {
+    size_t pw = knn_smem_per_warp(max_K, lc);
+    int w = (int)(lc.smem_optin / pw);
     return w > KNN_WARPS ? KNN_WARPS : w;
 }
 
 cudaError_t launch_knn_fit(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,
                            int max_K) {
     (void)a;
-    int warps = knn_warps_per_cta(max_K, lc.smem_optin);
+    int warps = knn_warps_per_cta(max_K, lc);
     if (warps < 1) return cudaErrorInvalidValue;
     int hs, fs, rhs, rfs;
-    knn_table_sizes(max_K, &hs, &fs);
+    knn_table_sizes(max_K, lc, &hs, &fs);
     knn_retry_table_sizes(max_K, lc.smem_optin, &rhs, &rfs);
     const size_t smem = knn_warp_bytes(hs, fs, max_K) * warps;
     const size_t rsmem = knn_warp_bytes(rhs, rfs, max_K);

@@ -27,8 +27,12 @@
 //
 // One launch holds the whole relaxation (a cooperative launch, every CTA
 // resident):
-//   phase 1  every tile is solved from its own seeds, with unreached
-//            neighbours around it;
+//   phase 1  every tile is solved from its own seeds, in two halves of a
+//            chessboard: first the tiles with tx + ty even, with unreached
+//            neighbours around them, then the others, with the first half's
+//            results in their ring (so their solves start from distances
+//            that already cross the tile borders, and fewer re-solves
+//            follow);
 //   phase 2  repeated passes: a tile whose neighbour tiles were written in
 //            the previous pass (or this one) loads itself and the ring of
 //            pixels around it, sets the flags of the rows its ring can
@@ -132,64 +136,106 @@ __device__ __forceinline__ void from_up(const Up &u, pkey_t Ka, pkey_t Kb, unsig
     nb = kmin(nb, step_key(u.rK, step_diag(hb, u.rh)));
 }
 
-// Step row y from the upstream row (registers u, already with neighbours):
-// three candidates per pixel, then the closure along the row (ring columns
-// fixed).  Writes the row back if it changed; returns whether it did.  On
-// return u holds row y (for the next row of the pass).  must_close: the row
-// is stepped for its own sake (seeds, ring neighbours) and may not be closed
-// along itself yet; otherwise it was closed when it was last stepped, and if
-// the upstream row improves none of its pixels nothing can change.
+// A row as one step of a stream reads it: this lane's two keys and
+// half-costs, the half-costs of the columns on either side and the ring keys.
+struct RowIn {
+    ulonglong2 kk;
+    unsigned ha, hb, hl, hr;
+    pkey_t ringl, ringr;
+};
+
 template <int MAXR>
-__device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, const TileGeo &g,
-                                         Up &u, bool must_close) {
-    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(&T.K[y][KO + 2 * lane]);
+__device__ __forceinline__ void row_in(const WarpTile<MAXR> &T, int y, int lane, RowIn &r) {
+    r.kk = *reinterpret_cast<const ulonglong2 *>(&T.K[y][KO + 2 * lane]);
     const uint2 hh = *reinterpret_cast<const uint2 *>(&T.hC[y][CO + 2 * lane]);
-    const unsigned ha = hh.x, hb = hh.y;
-    pkey_t na, nb;
-    from_up(u, kk.x, kk.y, ha, hb, na, nb);
+    r.ha = hh.x;
+    r.hb = hh.y;
+    r.ringl = T.K[y][KO - 1];
+    r.ringr = T.K[y][KO + RT_COLS];
+    const unsigned hl0 = __shfl_up_sync(FULL, r.hb, 1);
+    const unsigned hr0 = __shfl_down_sync(FULL, r.ha, 1);
+    r.hl = lane == 0 ? T.hC[y][CO - 1] : hl0;
+    r.hr = lane == 31 ? T.hC[y][CO + RT_COLS] : hr0;
+}
+
+// The row's own step weights: left neighbour to a, a to b, b to right.
+struct RowW {
+    unsigned long long wl, wab, wr;
+};
+
+__device__ __forceinline__ RowW row_w(const RowIn &r) {
+    return RowW{step_axis(r.hl, r.ha), step_axis(r.ha, r.hb), step_axis(r.hb, r.hr)};
+}
+
+// One closure round along a row: each lane sweeps its pair left to right and
+// back with its neighbours' keys of the previous round (the ring columns
+// fixed).  Returns whether this lane's keys changed.
+__device__ __forceinline__ bool close_round(pkey_t &na, pkey_t &nb, const RowIn &r,
+                                            const RowW &w, int lane, const TileGeo &g) {
+    pkey_t left = __shfl_up_sync(FULL, nb, 1);
+    pkey_t right = __shfl_down_sync(FULL, na, 1);
+    if (lane == 0) left = r.ringl;
+    if (lane == 31) right = r.ringr;
+    pkey_t a2 = kmin(na, step_key(left, w.wl));
+    pkey_t b2 = kmin(nb, step_key(a2, w.wab));
+    b2 = kmin(b2, step_key(right, w.wr));
+    a2 = kmin(a2, step_key(b2, w.wab));
+    if (g.outa) a2 = KEY_INF;
+    if (g.outb) b2 = KEY_INF;
+    const bool ch = (a2 != na) | (b2 != nb);
+    na = a2;
+    nb = b2;
+    return ch;
+}
+
+// The vertical part of a step: this lane's two pixels take the three
+// candidates each from the upstream row u.  Returns whether the row must be
+// closed along itself: it is stepped for its own sake (must_close: seeds,
+// ring neighbours; it may not be closed yet), or the upstream row improved
+// one of its pixels (otherwise it is unchanged, and it was closed when it
+// was last stepped).
+__device__ __forceinline__ bool row_from_up(const Up &u, const RowIn &r, const TileGeo &g,
+                                            bool must_close, pkey_t &na, pkey_t &nb) {
+    from_up(u, r.kk.x, r.kk.y, r.ha, r.hb, na, nb);
     if (g.outa) na = KEY_INF;
     if (g.outb) nb = KEY_INF;
-    if (!must_close && !__any_sync(FULL, (na != kk.x) | (nb != kk.y))) {
-        // nothing came from the upstream row: the row is unchanged, and it
-        // was closed along itself when it was last stepped
-        u.Pa = na;
-        u.Pb = nb;
-        u.pha = ha;
-        u.phb = hb;
-        return false;
-    }
-    // closure along the row: each lane sweeps its pair left to right and back
-    // with its neighbours' keys of the previous round, until a round changes
-    // nothing anywhere (at most one round per two columns, plus one)
-    const unsigned hl0 = __shfl_up_sync(FULL, hb, 1);
-    const unsigned hr0 = __shfl_down_sync(FULL, ha, 1);
-    const unsigned hl = lane == 0 ? T.hC[y][CO - 1] : hl0;
-    const unsigned hr = lane == 31 ? T.hC[y][CO + RT_COLS] : hr0;
-    const pkey_t ringl = T.K[y][KO - 1], ringr = T.K[y][KO + RT_COLS];
-    const unsigned long long wl = step_axis(hl, ha), wab = step_axis(ha, hb), wr = step_axis(hb, hr);
-    for (int round = 0; round <= RT_COLS / 2 + 1; ++round) {
-        pkey_t left = __shfl_up_sync(FULL, nb, 1);
-        pkey_t right = __shfl_down_sync(FULL, na, 1);
-        if (lane == 0) left = ringl;
-        if (lane == 31) right = ringr;
-        pkey_t a2 = kmin(na, step_key(left, wl));
-        pkey_t b2 = kmin(nb, step_key(a2, wab));
-        b2 = kmin(b2, step_key(right, wr));
-        a2 = kmin(a2, step_key(b2, wab));
-        if (g.outa) a2 = KEY_INF;
-        if (g.outb) b2 = KEY_INF;
-        const bool ch = (a2 != na) | (b2 != nb);
-        na = a2;
-        nb = b2;
-        if (!__any_sync(FULL, ch)) break;
-    }
-    const bool changed = __any_sync(FULL, (na != kk.x) | (nb != kk.y));
+    return must_close || __any_sync(FULL, (na != r.kk.x) | (nb != r.kk.y));
+}
+
+// Closure rounds until a round changes nothing anywhere (at most one round
+// per two columns, plus one).
+__device__ __forceinline__ void close_row(pkey_t &na, pkey_t &nb, const RowIn &r, int lane,
+                                          const TileGeo &g) {
+    const RowW w = row_w(r);
+    for (int round = 0; round <= RT_COLS / 2 + 1; ++round)
+        if (!__any_sync(FULL, close_round(na, nb, r, w, lane, g))) break;
+}
+
+// Ends a step of row y: writes the row back if it changed and leaves it in
+// u (the upstream row of the stream's next step).  Returns whether it changed.
+template <int MAXR>
+__device__ __forceinline__ bool row_out(WarpTile<MAXR> &T, int y, int lane, const RowIn &r,
+                                        pkey_t na, pkey_t nb, Up &u) {
+    const bool changed = __any_sync(FULL, (na != r.kk.x) | (nb != r.kk.y));
     if (changed) *reinterpret_cast<ulonglong2 *>(&T.K[y][KO + 2 * lane]) = make_ulonglong2(na, nb);
     u.Pa = na;
     u.Pb = nb;
-    u.pha = ha;
-    u.phb = hb;
+    u.pha = r.ha;
+    u.phb = r.hb;
     return changed;
+}
+
+// Step row y from the upstream row (registers u, with neighbours): three
+// candidates per pixel, then the closure along the row.  Returns whether the
+// row changed; on return u holds row y.
+template <int MAXR>
+__device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, const TileGeo &g,
+                                         Up &u, bool must_close) {
+    RowIn r;
+    row_in(T, y, lane, r);
+    pkey_t na, nb;
+    if (row_from_up(u, r, g, must_close, na, nb)) close_row(na, nb, r, lane, g);
+    return row_out(T, y, lane, r, na, nb, u);
 }
 
 // Down and up passes over rows 1..rv until every flag is clear.  forD bit r:
@@ -289,6 +335,10 @@ __device__ bool tma_stage(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g,
     if (lane == 0) {
         const unsigned kbytes = (unsigned)(KP * (P.tile_h + 2) * 8);
         const unsigned cbytes = (unsigned)(CP * (P.tile_h + 2) * 4);
+        // the keys were written by other CTAs with generic stores (ordered
+        // before this point by the stamps and the grid barrier); the bulk
+        // copies read them through the async proxy
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                      "r"(cbytes + (keys ? kbytes : 0u))
@@ -434,66 +484,14 @@ __device__ bool stage_tile(const PairDev &P, WarpTile<MAXR> &T, const TileGeo &g
     return true;
 }
 
-// Phase 1: solve tile (tx, ty) from its own seeds.  A tile without seeds is
-// written unreached and stamped "never written" (-1), so that in the first
-// pass its seedless neighbours skip it.  Returns false when the staging
-// timed out.
+// Rows of the staged tile that a ring pixel can improve by one step: the top
+// row from ring row 0 (a down step of row 1), the bottom row from ring row
+// rv + 1 (an up step of row rv); the end columns of row r from the ring
+// column in rows r - 1 and r (a down step) and r + 1 (an up step).
 template <int MAXR>
-__device__ bool fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T, int lane,
-                           unsigned &phase, RunState *st) {
-    const TileGeo g = tile_geo(P, tx, ty, lane);
+__device__ void ring_flags(const WarpTile<MAXR> &T, const TileGeo &g, int lane,
+                           unsigned long long &selfD, unsigned long long &selfU) {
     const int c = 2 * lane;
-    const int s0 = P.tile_start[t], s1 = P.tile_start[t + 1];
-    const unsigned long long all = ((1ull << g.rv) - 1) << 1;
-    if (s0 == s1) {
-        __syncwarp();
-        for (int r = 1; r <= g.rv; ++r)
-            *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = make_ulonglong2(KEY_INF, KEY_INF);
-        __syncwarp();
-        write_rows(P, T, g, all, lane);
-        if (lane == 0) P.tile_stamp[t] = -1;
-        __syncwarp();
-        return true;
-    }
-    if (!stage_tile(P, T, g, false, phase, lane, st)) return false;
-    unsigned long long seeded = 0;
-    for (int s = s0 + lane; s < s1; s += 32) {
-        const int m = P.tile_seeds[s];
-        const float4 mt = __ldg(P.matches + m);
-        const int px = (int)floorf(mt.x + 0.5f) - g.x0;
-        const int py = (int)floorf(mt.y + 0.5f) - g.y0;
-        if (px >= 0 && px < g.wv && py >= 0 && py < g.rv) {
-            atomicMin(&T.K[py + 1][KO + px],
-                      make_key(P.seed_init ? P.seed_init[m] : 0ull, (unsigned)m));
-            seeded |= 1ull << (py + 1);
-        }
-    }
-    seeded = warp_or64(seeded);
-    __syncwarp();
-    tile_passes(T, lane, g, seeded, seeded, seeded, 0ull, st);
-    __syncwarp();
-    write_rows(P, T, g, all, lane);
-    __threadfence();
-    if (lane == 0) P.tile_stamp[t] = 0;
-    __syncwarp();
-    return true;
-}
-
-// Phase 2: stage tile (tx, ty) with its ring from the current key map, set
-// the flags of the rows the ring can improve and re-solve.  Returns 1 if any
-// key of the tile changed (then it was written back and stamped `stamp`),
-// 0 if none did, -1 if the staging timed out.
-template <int MAXR>
-__device__ int resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T,
-                            int lane, unsigned &phase, RunState *st, int stamp) {
-    const TileGeo g = tile_geo(P, tx, ty, lane);
-    const int c = 2 * lane;
-    if (!stage_tile(P, T, g, true, phase, lane, st)) return -1;
-    // which rows can a ring pixel improve?  The top row from ring row 0 (a
-    // down step of row 1), the bottom row from ring row rv + 1 (an up step
-    // of row rv); the end columns of row r from the ring column in rows
-    // r - 1 and r (a down step) and r + 1 (an up step).
-    unsigned long long selfD = 0, selfU = 0;
     {
         Up u;
         pkey_t na, nb;
@@ -535,6 +533,85 @@ __device__ int resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MA
         selfD |= (unsigned long long)__ballot_sync(FULL, d) << 1;
         selfU |= (unsigned long long)__ballot_sync(FULL, up) << 1;
     }
+}
+
+// Phase 1: solve tile (tx, ty) from its own seeds.  The first half of the
+// phase takes the tiles with tx + ty even, alone (an unreached ring); the
+// second half the others (ring = true), which stage the ring from their
+// four edge neighbours, solved by then (the corner pixels of the ring
+// belong to tiles of the second half and stay unreached).  A tile with
+// nothing to solve (no seeds, and for the second half no ring pixel that
+// improves it) is written unreached and stamped "never written" (-1), so
+// that in the first pass its seedless neighbours skip it.  Returns false
+// when the staging timed out.
+template <int MAXR>
+__device__ bool fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T, int lane,
+                           unsigned &phase, RunState *st, bool ring) {
+    const TileGeo g = tile_geo(P, tx, ty, lane);
+    const int c = 2 * lane;
+    const int s0 = P.tile_start[t], s1 = P.tile_start[t + 1];
+    const unsigned long long all = ((1ull << g.rv) - 1) << 1;
+    if (s0 == s1 && !ring) {
+        __syncwarp();
+        for (int r = 1; r <= g.rv; ++r)
+            *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = make_ulonglong2(KEY_INF, KEY_INF);
+        __syncwarp();
+        write_rows(P, T, g, all, lane);
+        if (lane == 0) P.tile_stamp[t] = -1;
+        __syncwarp();
+        return true;
+    }
+    if (!stage_tile(P, T, g, ring, phase, lane, st)) return false;
+    unsigned long long selfD = 0, selfU = 0;
+    if (ring) {
+        // the tile itself starts unreached, and so do the ring's corners
+        for (int r = 1; r <= g.rv; ++r)
+            *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = make_ulonglong2(KEY_INF, KEY_INF);
+        if (lane < 4) T.K[lane < 2 ? 0 : g.rv + 1][lane & 1 ? KO + RT_COLS : KO - 1] = KEY_INF;
+        __syncwarp();
+        ring_flags(T, g, lane, selfD, selfU);
+    }
+    unsigned long long seeded = 0;
+    for (int s = s0 + lane; s < s1; s += 32) {
+        const int m = P.tile_seeds[s];
+        const float4 mt = __ldg(P.matches + m);
+        const int px = (int)floorf(mt.x + 0.5f) - g.x0;
+        const int py = (int)floorf(mt.y + 0.5f) - g.y0;
+        if (px >= 0 && px < g.wv && py >= 0 && py < g.rv) {
+            atomicMin(&T.K[py + 1][KO + px],
+                      make_key(P.seed_init ? P.seed_init[m] : 0ull, (unsigned)m));
+            seeded |= 1ull << (py + 1);
+        }
+    }
+    seeded = warp_or64(seeded);
+    __syncwarp();
+    if ((seeded | selfD | selfU) == 0) {
+        // second half, no seeds, and the ring reaches nothing
+        write_rows(P, T, g, all, lane);
+        if (lane == 0) P.tile_stamp[t] = -1;
+        __syncwarp();
+        return true;
+    }
+    tile_passes(T, lane, g, seeded, seeded, seeded | selfD, selfU, st);
+    __syncwarp();
+    write_rows(P, T, g, all, lane);
+    __threadfence();
+    if (lane == 0) P.tile_stamp[t] = 0;
+    __syncwarp();
+    return true;
+}
+
+// Phase 2: stage tile (tx, ty) with its ring from the current key map, set
+// the flags of the rows the ring can improve and re-solve.  Returns 1 if any
+// key of the tile changed (then it was written back and stamped `stamp`),
+// 0 if none did, -1 if the staging timed out.
+template <int MAXR>
+__device__ int resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T,
+                            int lane, unsigned &phase, RunState *st, int stamp) {
+    const TileGeo g = tile_geo(P, tx, ty, lane);
+    if (!stage_tile(P, T, g, true, phase, lane, st)) return -1;
+    unsigned long long selfD = 0, selfU = 0;
+    ring_flags(T, g, lane, selfD, selfU);
     if ((selfD | selfU) == 0) return 0;
     const unsigned long long mod = tile_passes(T, lane, g, 0ull, 0ull, selfD, selfU, st);
     if (mod == 0) return 0;
@@ -574,15 +651,19 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
     }
     __syncwarp();
 
-    // phase 1
-    for (int t = take_tile(&st->work[3], lane); t < a.total_tiles;
-         t = take_tile(&st->work[3], lane)) {
-        const int pi = find_pair(a.tile_base, a.npairs, t);
-        const PairDev &P = a.pairs[pi];
-        const int lt = t - a.tile_base[pi];
-        if (!fresh_tile(P, lt, lt % P.tiles_x, lt / P.tiles_x, T, lane, phase, st)) return;
+    // phase 1, in two halves: the tiles with tx + ty even, then the others
+    for (int half = 0; half < 2; ++half) {
+        unsigned *disp = &st->work[3 + half];
+        for (int t = take_tile(disp, lane); t < a.total_tiles; t = take_tile(disp, lane)) {
+            const int pi = find_pair(a.tile_base, a.npairs, t);
+            const PairDev &P = a.pairs[pi];
+            const int lt = t - a.tile_base[pi];
+            const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
+            if (((tx + ty) & 1) != half) continue;
+            if (!fresh_tile(P, lt, tx, ty, T, lane, phase, st, half == 1)) return;
+        }
+        if (!grid_sync(st, nblocks)) return;
     }
-    if (!grid_sync(st, nblocks)) return;
 
     // phase 2
     for (int pass = 0;; ++pass) {

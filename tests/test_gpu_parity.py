@@ -28,7 +28,7 @@ def test_config1_polygon_pair_full_parity():
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_small_random_cases_several_tiles_ragged_tail(seed):
-    # 83 x 150: several 64x32 tiles with ragged right and bottom tails
+    # 83 x 150: several 64 x 16 tiles with ragged right and bottom tails
     C, M = random_small_case(600 + seed, H=83, W=150, N=120, c_lo=0.01, c_hi=1.0)
     g, ref, rep = full_parity((C, M), K=16, a=1.0)
     _print(f"random{seed}", rep)

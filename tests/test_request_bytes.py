@@ -18,7 +18,8 @@ def _a(x):
     return (x + 255) // 256 * 256
 
 
-def carve(H, W, N, K, tile=(64, 32), keep=False, prune=False, prune_K=25):
+def carve(H, W, N, K, tile=(64, 16), keep=False, prune=False, prune_K=25):
+    # the default configuration relaxes on warp tiles of 64 x 16
     P = H * W
     T = -(-W // tile[0]) * -(-H // tile[1])
     cap = 1024
