@@ -11,9 +11,10 @@
 //
 // edges_kernel   every pixel looks at its four forward neighbours (right,
 //                down-left, down, down-right: each unordered pixel pair once)
-//                and forms (min label, max label, weight).  Candidates are
-//                merged per tile (64 x 32 pixels hold only tens of distinct
-//                label pairs): first over the pixel's four directions, then
+//                and forms (min label, max label, weight).  A work item is
+//                a stack of relaxation tiles at least 32 rows high.
+//                Candidates are merged per item (64 x 32 pixels hold only
+//                tens of distinct label pairs): first over the pixel's four directions, then
 //                across the lanes of a warp (match.any groups), then in a
 //                shared-memory table with atomicMin on the weight; the tile's
 //                unique entries are then inserted into the pair's global
@@ -68,6 +69,14 @@ __device__ __forceinline__ void table_insert(const PairDev &P, pkey_t k,
 }
 
 constexpr int TILE_TABLE = 1024;  // shared-memory slots per CTA (power of two)
+constexpr int EDGE_ROWS = 32;     // a work item stacks relaxation tiles to this height
+
+// Relaxation tiles a work item of the edge kernel stacks vertically: short
+// tiles (the warp tiles are 64 x 16) would spend a larger share of the item
+// on its halo and on taking the item.
+__host__ __device__ __forceinline__ int edge_stack(int tile_h) {
+    return tile_h >= EDGE_ROWS ? 1 : EDGE_ROWS / tile_h;
+}
 
 // Claim the shared-table slot of key k (or find it); -1 if the probe
 // sequence is full.  A newly claimed slot is counted in *fill.
@@ -138,11 +147,20 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
     // of cell boundaries they hold
     for (;;) {
         if (threadIdx.x == 0) {
-            const int t = (int)atomicAdd(&st->edge_next, 1u);
-            s_tile = t;
-            if (t < a.total_tiles) {
-                s_pair = find_pair(a.tile_base, a.npairs, t);
-                s_local = t - a.tile_base[s_pair];
+            // an item starts at every edge_stack-th row of tiles; the tiles
+            // in between belong to the item above them
+            for (;;) {
+                const int t = (int)atomicAdd(&st->edge_next, 1u);
+                s_tile = t;
+                if (t >= a.total_tiles) break;
+                const int pi = find_pair(a.tile_base, a.npairs, t);
+                const PairDev &Q = a.pairs[pi];
+                const int lt = t - a.tile_base[pi];
+                if ((lt / Q.tiles_x) % edge_stack(Q.tile_h) == 0) {
+                    s_pair = pi;
+                    s_local = lt;
+                    break;
+                }
             }
         }
         __syncthreads();
@@ -157,9 +175,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
         if (threadIdx.x == 0) s_tab_pair = s_pair;
         const PairDev &P = a.pairs[s_pair];
         const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
-        const int npx = P.tile_w * P.tile_h;
+        const int RH = edge_stack(P.tile_h) * P.tile_h;   // rows of the item
+        const int npx = P.tile_w * RH;
         const int W = P.W, H = P.H;
-        const int SC = P.tile_w + 2, SR = P.tile_h + 1;   // staged columns x0-1 .. x0+tw
+        const int SC = P.tile_w + 2, SR = RH + 1;   // staged columns x0-1 .. x0+tw
         const int us = unit_shift(P);                      // the pair's distance unit
         pkey_t *skey = reinterpret_cast<pkey_t *>(edge_smem);
         unsigned *sh = reinterpret_cast<unsigned *>(skey + SC * SR);
@@ -236,8 +255,26 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                 cw[d] = wb;
                 cv[d] = have;
             }
+            // this pixel's distinct candidates to the front (usually one or
+            // two of the four directions), then one warp insertion round per
+            // candidate rank that any lane holds
 #pragma unroll
-            for (int d = 0; d < 4; ++d) warp_insert(P, cv[d], ck[d], cw[d], sk, sw, &s_fill, st);
+            for (int d = 1; d < 4; ++d) {
+#pragma unroll
+                for (int j = 0; j < d; ++j) {
+                    if (!cv[j] && cv[d]) {
+                        ck[j] = ck[d];
+                        cw[j] = cw[d];
+                        cv[j] = true;
+                        cv[d] = false;
+                    }
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                if (!__any_sync(0xffffffffu, cv[d])) break;
+                warp_insert(P, cv[d], ck[d], cw[d], sk, sw, &s_fill, st);
+            }
         }
         __syncthreads();
     }
@@ -418,7 +455,9 @@ __global__ void collect_kernel(const pkey_t *hkeys, const unsigned *hw, int cap_
 }  // namespace
 
 size_t edges_smem_bytes(int max_tile_w, int max_tile_h) {
-    return (size_t)(max_tile_w + 2) * (max_tile_h + 1) * (sizeof(pkey_t) + sizeof(unsigned));
+    // stacked tiles are at most EDGE_ROWS rows high (a taller tile is one item)
+    const int rows = max_tile_h > EDGE_ROWS ? max_tile_h : EDGE_ROWS;
+    return (size_t)(max_tile_w + 2) * (rows + 1) * (sizeof(pkey_t) + sizeof(unsigned));
 }
 
 cudaError_t launch_edges(const BatchArgs &a, const BatchArgs *dev, const LaunchCfg &lc,

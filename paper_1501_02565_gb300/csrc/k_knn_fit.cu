@@ -21,9 +21,9 @@
 // Per-warp shared memory holds
 //   * the frontier: packed keys (t bits << 32 | node), their table slots and
 //     t + w_x, rebuilt every step so that only current entries survive,
-//   * an open-addressing table node -> tentative distance (bit 31 =
-//     settled), updated with compare-and-swap so several lanes may relax
-//     into one node,
+//   * an open-addressing table node -> tentative distance (0 = settled):
+//     a lane claims a node's slot with compare-and-swap and lowers its
+//     distance with atomicMin, so several lanes may relax into one node,
 //   * the settled list (node, distance, start of its batch).
 // The main pass sizes these tables for the searches seen on optical-flow
 // match graphs (about 1.5 K nodes touched) so that four CTAs of eight warps
@@ -61,7 +61,13 @@ namespace epic {
 
 namespace {
 
-constexpr unsigned SETTLED = 0x80000000u;
+// Node-table distance word: the float bits of the tentative distance plus
+// one while the node is unsettled (+inf: 0x7F800001), 0 once it is settled,
+// so that one atomicMin both lowers a tentative distance and leaves a
+// settled node alone.
+constexpr unsigned SETTLED = 0u;
+constexpr unsigned DIST_INF = 0x7F800001u;
+__device__ __forceinline__ unsigned dist_word(unsigned dist_bits) { return dist_bits + 1u; }
 
 // Search key on G: float32 bits of the graph distance (non-negative, so the
 // bit pattern orders like the value) above the 32-bit node index.
@@ -109,8 +115,21 @@ __device__ __forceinline__ void acc_add(F2 &acc, float v) {
 
 __device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.lo; }
 
+// One frontier entry: packed key (t bits << 32 | node), its node-table slot
+// and t + w_x, moved as one 16-byte access.
+struct __align__(16) FEnt {
+    pkey_t k;
+    unsigned sl;
+    float tw;
+};
+
+// Per-warp tables: frontier [fs], node table [hs] x 2 words, settled list
+// [km] x (node, distance) and batch starts [km] x 2 bytes; 16-byte multiple.
+__host__ __device__ __forceinline__ size_t knn_fixed_bytes(int km) {
+    return ((size_t)km * 8 + (((size_t)km * 2 + 7) & ~(size_t)7) + 15) & ~(size_t)15;
+}
 __host__ __device__ __forceinline__ size_t knn_warp_bytes(int hs, int fs, int km) {
-    return (size_t)fs * 16 + (size_t)hs * 8 + (size_t)km * 8 + (((size_t)km * 2 + 7) & ~(size_t)7);
+    return (size_t)fs * sizeof(FEnt) + (((size_t)hs * 8 + 15) & ~(size_t)15) + knn_fixed_bytes(km);
 }
 
 // Sort the settled list (node, distance) by key (distance, node) in place.
@@ -151,12 +170,11 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
     const int KM = a.knn_kmax;
     const size_t per_warp = knn_warp_bytes(HS, FS, KM);
     unsigned char *base = smem + per_warp * wid;
-    pkey_t *fk = reinterpret_cast<pkey_t *>(base);
-    unsigned *fs = reinterpret_cast<unsigned *>(fk + FS);
-    float *fw = reinterpret_cast<float *>(fs + FS);   // t + lightest edge of each entry
-    unsigned *hk = reinterpret_cast<unsigned *>(fw + FS);   // node table: node
-    unsigned *hv = hk + HS;                                 // tentative distance | SETTLED
-    unsigned *rn = hv + HS;
+    FEnt *fe = reinterpret_cast<FEnt *>(base);              // frontier
+    unsigned *hk = reinterpret_cast<unsigned *>(fe + FS);   // node table: node
+    unsigned *hv = hk + HS;                                 // distance word (0 = settled)
+    unsigned *rn = reinterpret_cast<unsigned *>(
+        reinterpret_cast<unsigned char *>(hk) + ((((size_t)HS * 8) + 15) & ~(size_t)15));
     float *rd = reinterpret_cast<float *>(rn + KM);
     // batch start of each settled entry (K stays far below 65536: the tables of one
     // warp must fit in shared memory)
@@ -188,7 +206,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
 
         for (int i = lane; i < HS; i += 32) {
             hk[i] = EMPTY32;
-            hv[i] = 0x7F800000u;  // +inf
+            hv[i] = DIST_INF;
         }
         __syncwarp();
         // each lane's running minimum of the keys and of t + w_x over the
@@ -201,10 +219,10 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
         if (lane == 0) {
             const unsigned s0 = node_slot((unsigned)m, HS);
             hk[s0] = (unsigned)m;
-            hv[s0] = 0u;
-            fk[0] = rk = make_key(0.f, (unsigned)m);
-            fs[0] = s0;
-            fw[0] = rb = __fadd_rn(0.f, __uint_as_float(__ldg(wmin + m)));
+            hv[s0] = dist_word(0u);
+            rk = make_key(0.f, (unsigned)m);
+            rb = __fadd_rn(0.f, __uint_as_float(__ldg(wmin + m)));
+            fe[0] = FEnt{rk, s0, rb};
         }
         __syncwarp();
         int fn = 1, cnt = 0;
@@ -232,9 +250,10 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                 const int i = b0 + lane;
                 bool inb = false;
                 if (i < fn) {
-                    const pkey_t k = fk[i];
-                    const unsigned cur = hv[fs[i]];
-                    inb = !(cur & SETTLED) && cur == (unsigned)(k >> 32) &&
+                    const FEnt f = fe[i];
+                    const pkey_t k = f.k;
+                    const unsigned cur = hv[f.sl];
+                    inb = cur == dist_word((unsigned)(k >> 32)) &&
                           (key_dist(k) < bound || k == kmin);
                 }
                 nwin += __popc(__ballot_sync(0xffffffffu, inb));
@@ -253,11 +272,12 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                 float tw = 0.f;
                 bool valid = false;
                 if (i < fn) {
-                    k = fk[i];
-                    sl = fs[i];
-                    tw = fw[i];
+                    const FEnt f = fe[i];
+                    k = f.k;
+                    sl = f.sl;
+                    tw = f.tw;
                     const unsigned cur = hv[sl];
-                    valid = !(cur & SETTLED) && cur == (unsigned)(k >> 32);
+                    valid = cur == dist_word((unsigned)(k >> 32));
                 }
                 const bool inb = valid && (single ? k == kmin
                                                   : (key_dist(k) < bound || k == kmin));
@@ -267,9 +287,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                 __syncwarp();
                 if (keep) {
                     const int p = wpos + __popc(kb & lt_mask);
-                    fk[p] = k;
-                    fs[p] = sl;
-                    fw[p] = tw;
+                    fe[p] = FEnt{k, sl, tw};
                     rk = k < rk ? k : rk;
                     rb = fminf(rb, tw);
                 }
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                 } else {
                     if (inb) {
                         const int p = cnt + nb + __popc(bb & lt_mask);
-                        hv[sl] |= SETTLED;
+                        hv[sl] = SETTLED;
                         rn[p] = key_label(k);
                         rd[p] = key_dist(k);
                         bs[p] = (unsigned short)cnt;
@@ -377,13 +395,9 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                             if (++probes >= HS) { overflow = true; break; }
                         }
                         if (!overflow) {
-                            const unsigned nb_bits = __float_as_uint(nd);
-                            unsigned cur = hv[sl];
-                            while (!(cur & SETTLED) && nb_bits < cur) {
-                                const unsigned old = atomicCAS(hv + sl, cur, nb_bits);
-                                if (old == cur) { push = true; break; }
-                                cur = old;
-                            }
+                            // a settled node (word 0) is never lowered
+                            const unsigned w = dist_word(__float_as_uint(nd));
+                            push = w < atomicMin(hv + sl, w);
                         }
                         slot = sl;
                     }
@@ -400,18 +414,17 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                             float tw2 = 0.f;
                             bool keep = false;
                             if (i < fn) {
-                                k = fk[i];
-                                sl2 = fs[i];
-                                tw2 = fw[i];
+                                const FEnt f = fe[i];
+                                k = f.k;
+                                sl2 = f.sl;
+                                tw2 = f.tw;
                                 const unsigned cur = hv[sl2];
-                                keep = !(cur & SETTLED) && cur == (unsigned)(k >> 32);
+                                keep = cur == dist_word((unsigned)(k >> 32));
                             }
                             const unsigned kb = __ballot_sync(0xffffffffu, keep);
                             __syncwarp();
                             if (keep) {
-                                fk[w2 + __popc(kb & lt_mask)] = k;
-                                fs[w2 + __popc(kb & lt_mask)] = sl2;
-                                fw[w2 + __popc(kb & lt_mask)] = tw2;
+                                fe[w2 + __popc(kb & lt_mask)] = FEnt{k, sl2, tw2};
                             }
                             w2 += __popc(kb);
                             __syncwarp();
@@ -423,9 +436,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
                         const int p = fn + __popc(bal & lt_mask);
                         const pkey_t nk = make_key(nd, u);
                         const float tw = __fadd_rn(nd, __uint_as_float(uw));
-                        fk[p] = nk;
-                        fs[p] = slot;
-                        fw[p] = tw;
+                        fe[p] = FEnt{nk, slot, tw};
                         rk = nk < rk ? nk : rk;
                         rb = fminf(rb, tw);
                     }
@@ -459,7 +470,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
         // of the adjacency rows (filled with atomics); sorting each batch by
         // key restores Dijkstra's settle order, so the fit below sums in a
         // canonical order and the result is bit-for-bit reproducible
-        sort_settled(rn, rd, bs, cnt, fk, lane);
+        sort_settled(rn, rd, bs, cnt, reinterpret_cast<pkey_t *>(fe), lane);
 
         // locally-weighted affine fit over the cnt settled neighbours
         const float4 pm = __ldg(P.matches + m);
@@ -625,7 +636,7 @@ void knn_table_sizes(int max_K, const LaunchCfg &lc, int *hs, int *fs) {
     *fs = std::max(64, (k * 192 / 100 + 31) / 32 * 32);
     if (lc.smem_per_sm <= 0) return;
     const long long per_warp = ((long long)lc.smem_per_sm / 4 - lc.smem_reserved) / KNN_WARPS;
-    const long long fixed = (long long)k * 8 + (((long long)k * 2 + 7) & ~7LL);
+    const long long fixed = (long long)knn_fixed_bytes(k);
     if ((long long)*fs * 16 + (long long)*hs * 8 + fixed <= per_warp) return;
     const long long f = (per_warp - fixed) / 32;   // 16 B per entry + 2 slots of 8 B
     if (f * 10 >= 14LL * k) {

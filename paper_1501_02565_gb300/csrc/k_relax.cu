@@ -55,6 +55,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int KP = 68, KO = 2;
 constexpr int CP = 72, CO = 4;
 constexpr unsigned long long TMA_LIMIT_NS = 1000000000ull;  // 1 s
+constexpr int SCAN_CHUNK = 4;   // most tiles a warp takes at once in the passes of phase 2
 
 // One warp's tile in shared memory.  Row r is image row y0 - 1 + r, so rows
 // 0 and R + 1 are the ring rows above and below.  hC holds the costs as
@@ -665,7 +666,11 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
         if (!grid_sync(st, nblocks)) return;
     }
 
-    // phase 2
+    // phase 2.  A warp takes up to SCAN_CHUNK tiles at once (fewer counter
+    // atomics and stamp reads, and neighbouring tiles re-solved in turn see
+    // each other's results), but only while that leaves every warp several
+    // chunks of a pass to balance the load.
+    const int chunk = max(1, min(SCAN_CHUNK, a.total_tiles / (4 * (int)nblocks * RT_WARPS)));
     for (int pass = 0;; ++pass) {
         if (pass >= a.max_passes) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -676,25 +681,38 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
         }
         unsigned *cnt = &st->changed[pass % 3];
         unsigned *disp = &st->work[pass % 3];
-        for (int t = take_tile(disp, lane); t < a.total_tiles; t = take_tile(disp, lane)) {
-            const int pi = find_pair(a.tile_base, a.npairs, t);
-            const PairDev &P = a.pairs[pi];
-            const int lt = t - a.tile_base[pi];
-            const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
-            // lanes 0-7 read the eight neighbour stamps: a tile is looked at
-            // only if a neighbour was written since the previous pass began
+        // tiles are handed out `chunk` at a time; quarter q of the warp
+        // (lanes 8q .. 8q + 7) reads the eight neighbour stamps of the
+        // chunk's tile q: a tile is looked at only if a neighbour was written
+        // since the previous pass began
+        for (int c = take_tile(disp, lane); c < (a.total_tiles + chunk - 1) / chunk;
+             c = take_tile(disp, lane)) {
+            const int q = lane >> 3, k = lane & 7;
+            const int t = c * chunk + q;
+            int pi = 0, lt = 0, tx = 0, ty = 0;
             bool nb = false;
-            if (lane < 8) {
-                const int k = lane;
+            if (q < chunk && t < a.total_tiles) {
+                pi = find_pair(a.tile_base, a.npairs, t);
+                const PairDev &P = a.pairs[pi];
+                lt = t - a.tile_base[pi];
+                tx = lt % P.tiles_x;
+                ty = lt / P.tiles_x;
                 const int x = tx + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
                 const int y = ty + (k < 3 ? -1 : k < 5 ? 0 : 1);
                 nb = x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
                      __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass;
             }
-            if (!__any_sync(FULL, nb)) continue;
-            const int r = resolve_tile(P, lt, tx, ty, T, lane, phase, st, pass + 1);
-            if (r < 0) return;
-            if (r > 0 && lane == 0) atomicAdd(cnt, 1u);
+            unsigned look = __ballot_sync(FULL, nb);
+            while (look) {
+                const int src = (__ffs(look) - 1) & ~7;   // first lane of that tile's quarter
+                look &= ~(0xFFu << src);
+                const int tpi = __shfl_sync(FULL, pi, src), tlt = __shfl_sync(FULL, lt, src);
+                const int ttx = __shfl_sync(FULL, tx, src), tty = __shfl_sync(FULL, ty, src);
+                const int r =
+                    resolve_tile(a.pairs[tpi], tlt, ttx, tty, T, lane, phase, st, pass + 1);
+                if (r < 0) return;
+                if (r > 0 && lane == 0) atomicAdd(cnt, 1u);
+            }
         }
         if (!grid_sync(st, nblocks)) return;
         const unsigned dirty = ld_acquire(cnt);
