@@ -73,7 +73,7 @@ HEADLINE_CONFIG = 4
 PAPER_MPIX_S = 1024 * 436 / 0.25 / 1e6   # Sec. 5.4: 0.25 s per 1024x436 pair, 1 core
 STAGES = ("prepare", "relax", "edges", "scatter", "knn_fit", "writeout")
 KERNEL_SRC = {
-    "prepare": "k_prepare.cu", "relax": "k_dt.cu", "edges": "k_graph.cu",
+    "prepare": "k_prepare.cu", "relax": "k_relax.cu", "edges": "k_graph.cu",
     "scatter": "k_graph.cu", "knn_fit": "k_knn_fit.cu", "writeout": "k_writeout.cu",
 }
 

@@ -83,6 +83,7 @@ __device__ __forceinline__ unsigned half_cost(float c, bool *bad) {
 // (reach + 1) (max(tw, th) + (sqrt 2 - 1) min(tw, th)) pixels of a seed, and
 // its geodesic distance is at most the largest cost times that.  Every kernel
 // derives s from these two fields with this function, so they agree.
+constexpr int STAMP_PENDING = (int)0x80000000;   // a warp tile not yet written this run
 constexpr int MAX_UNIT_SHIFT = 20;
 constexpr int SWEEP_WARP = 2;   // relaxation schedule of the warp tiles
 __host__ __device__ __forceinline__ int unit_shift_of(unsigned cmax_bits, int reach, int tw,
@@ -139,6 +140,7 @@ struct PairDev {
     int *tile_fill;         // [tiles] scatter cursors
     int *tile_seeds;        // [N] match indices grouped by tile
     int *tile_stamp;        // [tiles] last relaxation pass that wrote the tile
+                            // (STAMP_PENDING: not yet in this run; warp tiles)
     pkey_t *hkeys;           // [hash_cap] (m << 32 | n), m < n
     unsigned *hw;           // [hash_cap] float bits of the edge weight
     int *deg;               // [N] node degree in G, then the CSR fill cursor

@@ -171,7 +171,10 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
     for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {
         const PairDev &P = a.pairs[p];
         const int T = P.tiles_x * P.tiles_y;
-        for (int t = threadIdx.x; t < T; t += blockDim.x) P.tile_start[t] = 0;
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            P.tile_start[t] = 0;
+            if (P.sweep == SWEEP_WARP) P.tile_stamp[t] = STAMP_PENDING;
+        }
         for (int m = threadIdx.x; m < P.N; m += blockDim.x) {
             P.deg[m] = 0;
             P.wmin[m] = 0x7F800000u;  // +inf

@@ -558,6 +558,7 @@ __device__ bool fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAX
             *reinterpret_cast<ulonglong2 *>(&T.K[r][KO + c]) = make_ulonglong2(KEY_INF, KEY_INF);
         __syncwarp();
         write_rows(P, T, g, all, lane);
+        __threadfence();
         if (lane == 0) P.tile_stamp[t] = -1;
         __syncwarp();
         return true;
@@ -589,6 +590,7 @@ __device__ bool fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAX
     if ((seeded | selfD | selfU) == 0) {
         // second half, no seeds, and the ring reaches nothing
         write_rows(P, T, g, all, lane);
+        __threadfence();
         if (lane == 0) P.tile_stamp[t] = -1;
         __syncwarp();
         return true;
@@ -624,6 +626,30 @@ __device__ int resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MA
     return 1;
 }
 
+// Waits until the four edge neighbours of tile (tx, ty) (those inside the
+// tile grid) carry a stamp of this run, i.e. are written; lane k < 4 watches
+// one.  Gives up after TMA_LIMIT_NS with EPIC_ERR_TIMEOUT (false in every
+// lane).
+__device__ bool wait_edge_neighbours(const PairDev &P, int tx, int ty, int lane, RunState *st) {
+    bool gave_up = false;
+    if (lane < 4) {
+        const int x = tx + (lane == 0 ? -1 : lane == 1 ? 1 : 0);
+        const int y = ty + (lane == 2 ? -1 : lane == 3 ? 1 : 0);
+        if (x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y) {
+            const unsigned *sp = reinterpret_cast<const unsigned *>(P.tile_stamp + y * P.tiles_x + x);
+            const unsigned long long t0 = warp_ns();
+            while (ld_acquire(sp) == (unsigned)STAMP_PENDING) {
+                if (warp_ns() - t0 > TMA_LIMIT_NS) {
+                    set_status(st, EPIC_ERR_TIMEOUT);
+                    gave_up = true;
+                    break;
+                }
+            }
+        }
+    }
+    return !__any_sync(FULL, gave_up);
+}
+
 __device__ __forceinline__ int take_tile(unsigned *dispenser, int lane) {
     int t = 0;
     if (lane == 0) t = (int)atomicAdd(dispenser, 1u);
@@ -652,19 +678,25 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
     }
     __syncwarp();
 
-    // phase 1, in two halves: the tiles with tx + ty even, then the others
-    for (int half = 0; half < 2; ++half) {
-        unsigned *disp = &st->work[3 + half];
-        for (int t = take_tile(disp, lane); t < a.total_tiles; t = take_tile(disp, lane)) {
-            const int pi = find_pair(a.tile_base, a.npairs, t);
-            const PairDev &P = a.pairs[pi];
-            const int lt = t - a.tile_base[pi];
-            const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
-            if (((tx + ty) & 1) != half) continue;
-            if (!fresh_tile(P, lt, tx, ty, T, lane, phase, st, half == 1)) return;
-        }
-        if (!grid_sync(st, nblocks)) return;
+    // phase 1, in two halves handed out by one counter: index u < T is tile
+    // u of the first half (tx + ty even), index T + u tile u of the second.
+    // Every first-half tile is taken before any second-half tile, so a
+    // second-half tile only waits (bounded) for its four edge neighbours,
+    // each already held by a running warp; no grid barrier divides the
+    // halves.
+    for (int u = take_tile(&st->work[3], lane); u < 2 * a.total_tiles;
+         u = take_tile(&st->work[3], lane)) {
+        const int half = u >= a.total_tiles;
+        const int t = u - (half ? a.total_tiles : 0);
+        const int pi = find_pair(a.tile_base, a.npairs, t);
+        const PairDev &P = a.pairs[pi];
+        const int lt = t - a.tile_base[pi];
+        const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
+        if (((tx + ty) & 1) != half) continue;
+        if (half && !wait_edge_neighbours(P, tx, ty, lane, st)) return;
+        if (!fresh_tile(P, lt, tx, ty, T, lane, phase, st, half == 1)) return;
     }
+    if (!grid_sync(st, nblocks)) return;
 
     // phase 2.  A warp takes up to SCAN_CHUNK tiles at once (fewer counter
     // atomics and stamp reads, and neighbouring tiles re-solved in turn see
