@@ -387,8 +387,8 @@ int epic_selftest_wait_timeout(epic_interp_t *h, int which, int limit_ms);
 /* Device scratch one pair of H x W pixels, N matches and neighbourhood size
  * K takes in the handle's arena when it runs in a batch (its packed keys,
  * seed bins, edge table, CSR rows, models, optional K-NN lists and pruning
- * buffers, and its K-NN retry-list slots), in *bytes; a batch needs the sum
- * over its pairs plus 256 bytes.  The caller's own buffers (cost map,
+ * buffers, its K-NN retry-list slots and its relaxation tiles' work-queue
+ * slots), in *bytes; a batch needs the sum over its pairs plus 512 bytes.  The caller's own buffers (cost map,
  * matches, flow) are not included.  Uses the configuration and tile rules of
  * `h`; with h = NULL, those of *cfg and no tile rules (cfg = NULL: the
  * defaults).  A host computation: needs no device and enqueues nothing.

@@ -211,6 +211,11 @@ struct RunState {
     unsigned edge_next;    // boundary-edge tile dispenser
     unsigned wl_count[3];  // worklist lengths of the chunked relaxation passes (rotating)
     unsigned compact_done; // CTAs finished in the pruning compaction
+    // the warp-tile relaxation's work queue (phase 2): tickets taken, items
+    // pushed, items pushed or held but not finished, items taken
+    unsigned q_head, q_tail;
+    int q_busy;
+    unsigned q_items;
     GridBarrier barrier;
 };
 
@@ -229,6 +234,8 @@ struct BatchArgs {
     int *wl_queued;          // [total_tiles] last pass + 1 a tile was queued for (0 = never)
     int max_degree;
     int knn_hs, knn_fs, knn_kmax;  // main-pass K-NN table sizes per warp, and K bound
+    int *relax_queue;      // [total_tiles] warp-tile relaxation work queue (-1 = empty slot)
+    int *relax_queued;     // [total_tiles] 1 while a tile is queued or not yet taken
     int *knn_retry_list;   // global match indices to search again; holds every match of
                            // the batch (a match is queued at most once per pass)
     int max_passes;

@@ -576,6 +576,11 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     // queued at most once per pass
     const size_t retry_off = align_up(off, 256);
     off = retry_off + sizeof(int) * total_N;
+    // the relaxation's work queue and queued flags: one slot each per tile
+    size_t total_T = 0;
+    for (int i = 0; i < n; ++i) total_T += (size_t)P[i].tiles_x * P[i].tiles_y;
+    const size_t rq_off = align_up(off, 256);
+    off = rq_off + 2 * sizeof(int) * total_T;
     if (max_K > EPIC_MAX_K)
         return fail(h, EPIC_ERR_INVALID, "K (clamped to N) above EPIC_MAX_K");
     int rc = ensure_arena(h, off);
@@ -700,6 +705,8 @@ int epic_interp_run_batch(epic_interp_t *h, const epic_pair_desc_t *descs, int n
     epic::knn_table_sizes(knn_K, size_lc, &a.knn_hs, &a.knn_fs);
     a.knn_kmax = knn_K;
     a.knn_retry_list = reinterpret_cast<int *>(h->arena + retry_off);
+    a.relax_queue = reinterpret_cast<int *>(h->arena + rq_off);
+    a.relax_queued = a.relax_queue + total_T;
     a.max_passes = c.max_passes;
     a.weight_squared = c.weight_squared ? 1 : 0;
     a.fallback_eps = c.fallback_eps;
@@ -1514,10 +1521,12 @@ int epic_interp_request_bytes(const epic_interp_t *h, const epic_config_t *cfg, 
     d.a = 1.f;
     const PairDev P = make_pair_desc(c, h ? h->rules : no_rules, d);
     // the pair's arena regions (each 256-byte aligned, so a pair placed after
-    // any other needs at most its aligned size) and its K-NN retry-list slots
+    // any other needs at most its aligned size), its K-NN retry-list slots
+    // and its tiles' slots in the relaxation's work queue and queued flags
     const size_t per = layout_pair(0, P, c.max_degree, c.keep_intermediates != 0,
                                    c.prune != 0).end;
-    *bytes = (long long)(per + sizeof(int) * (size_t)N);
+    *bytes = (long long)(per + sizeof(int) * (size_t)N +
+                         2 * sizeof(int) * (size_t)P.tiles_x * P.tiles_y);
     return EPIC_OK;
 }
 

@@ -166,6 +166,15 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
         st->wl_count[0] = st->wl_count[1] = st->wl_count[2] = 0;
         st->barrier.count = 0;
         st->compact_done = 0;
+        st->q_head = st->q_tail = st->q_items = 0;
+        st->q_busy = a.total_tiles;   // the initial sweep's items
+    }
+    // the relaxation's work queue: empty slots; every tile counts as queued
+    // until the initial sweep of phase 2 takes it
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.total_tiles;
+         i += gridDim.x * blockDim.x) {
+        a.relax_queue[i] = -1;
+        a.relax_queued[i] = 1;
     }
     // seed binning: one CTA per pair at a time
     for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {

@@ -33,12 +33,14 @@
 //            results in their ring (so their solves start from distances
 //            that already cross the tile borders, and fewer re-solves
 //            follow);
-//   phase 2  repeated passes: a tile whose neighbour tiles were written in
-//            the previous pass (or this one) loads itself and the ring of
-//            pixels around it, sets the flags of the rows its ring can
-//            improve, and re-solves if any; the passes end when no tile
-//            changed, i.e. no step improves any key anywhere.  Passes are
-//            separated by the bounded grid barrier.
+//   phase 2  a work queue of tiles: every tile once (the sweep), then every
+//            tile asked for by a neighbour whose border keys changed.  A
+//            solve loads the tile and the ring of pixels around it, sets the
+//            flags of the rows its ring can improve and re-solves if any.
+//            The phase ends when nothing is queued or being solved, i.e. no
+//            step improves any key anywhere; no grid barrier divides it, so
+//            a front of changes moves on through the tiles as soon as each
+//            one is solved.
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -216,9 +218,14 @@ __device__ __forceinline__ void close_row(pkey_t &na, pkey_t &nb, const RowIn &r
 // u (the upstream row of the stream's next step).  Returns whether it changed.
 template <int MAXR>
 __device__ __forceinline__ bool row_out(WarpTile<MAXR> &T, int y, int lane, const RowIn &r,
-                                        pkey_t na, pkey_t nb, Up &u) {
+                                        pkey_t na, pkey_t nb, Up &u, unsigned &edges) {
     const bool changed = __any_sync(FULL, (na != r.kk.x) | (nb != r.kk.y));
-    if (changed) *reinterpret_cast<ulonglong2 *>(&T.K[y][KO + 2 * lane]) = make_ulonglong2(na, nb);
+    if (changed) {
+        *reinterpret_cast<ulonglong2 *>(&T.K[y][KO + 2 * lane]) = make_ulonglong2(na, nb);
+        // bit 0: column 0 changed; bit 1: column 63
+        edges |= (__ballot_sync(FULL, na != r.kk.x) & 1u) |
+                 ((__ballot_sync(FULL, nb != r.kk.y) >> 30) & 2u);
+    }
     u.Pa = na;
     u.Pb = nb;
     u.pha = r.ha;
@@ -231,24 +238,24 @@ __device__ __forceinline__ bool row_out(WarpTile<MAXR> &T, int y, int lane, cons
 // row changed; on return u holds row y.
 template <int MAXR>
 __device__ __forceinline__ bool row_step(WarpTile<MAXR> &T, int y, int lane, const TileGeo &g,
-                                         Up &u, bool must_close) {
+                                         Up &u, bool must_close, unsigned &edges) {
     RowIn r;
     row_in(T, y, lane, r);
     pkey_t na, nb;
     if (row_from_up(u, r, g, must_close, na, nb)) close_row(na, nb, r, lane, g);
-    return row_out(T, y, lane, r, na, nb, u);
+    return row_out(T, y, lane, r, na, nb, u, edges);
 }
 
 // Down and up passes over rows 1..rv until every flag is clear.  forD bit r:
 // row r changed since row r + 1 was last stepped downwards (forU: upwards,
 // row r - 1); selfD / selfU bit r: row r must be stepped in the next down /
 // up pass for its own sake (seeds, ring neighbours).  Returns the mask of
-// rows that changed.
+// rows that changed; `edges` gains bit 0 (1) if column 0 (63) changed.
 template <int MAXR>
 __device__ unsigned long long tile_passes(WarpTile<MAXR> &T, int lane, const TileGeo &g,
                                           unsigned long long forD, unsigned long long forU,
                                           unsigned long long selfD, unsigned long long selfU,
-                                          RunState *st) {
+                                          RunState *st, unsigned &edges) {
     const int rv = g.rv;
     const unsigned long long ring = 1ull | (1ull << (rv + 1));
     unsigned long long modified = 0;
@@ -278,7 +285,7 @@ __device__ unsigned long long tile_passes(WarpTile<MAXR> &T, int lane, const Til
             sf &= ~(1ull << y);
             if (have != yu) load_up(T, yu, lane, u);
             neighbours_up(T, yu, lane, u);
-            if (row_step(T, y, lane, g, u, self)) {
+            if (row_step(T, y, lane, g, u, self, edges)) {
                 forD |= 1ull << y;
                 forU |= 1ull << y;
                 modified |= 1ull << y;
@@ -595,7 +602,8 @@ __device__ bool fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAX
         __syncwarp();
         return true;
     }
-    tile_passes(T, lane, g, seeded, seeded, seeded | selfD, selfU, st);
+    unsigned edges = 0;
+    tile_passes(T, lane, g, seeded, seeded, seeded | selfD, selfU, st, edges);
     __syncwarp();
     write_rows(P, T, g, all, lane);
     __threadfence();
@@ -607,16 +615,22 @@ __device__ bool fresh_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAX
 // Phase 2: stage tile (tx, ty) with its ring from the current key map, set
 // the flags of the rows the ring can improve and re-solve.  Returns 1 if any
 // key of the tile changed (then it was written back and stamped `stamp`),
-// 0 if none did, -1 if the staging timed out.
+// 0 if none did, -1 if the staging timed out; *modified gets the mask of
+// changed tile rows (bit r = row r), *edges bit 0 (1) whether column 0 (63)
+// changed.
 template <int MAXR>
 __device__ int resolve_tile(const PairDev &P, int t, int tx, int ty, WarpTile<MAXR> &T,
-                            int lane, unsigned &phase, RunState *st, int stamp) {
+                            int lane, unsigned &phase, RunState *st, int stamp,
+                            unsigned long long *modified, unsigned *edges) {
+    *modified = 0;
+    *edges = 0;
     const TileGeo g = tile_geo(P, tx, ty, lane);
     if (!stage_tile(P, T, g, true, phase, lane, st)) return -1;
     unsigned long long selfD = 0, selfU = 0;
     ring_flags(T, g, lane, selfD, selfU);
     if ((selfD | selfU) == 0) return 0;
-    const unsigned long long mod = tile_passes(T, lane, g, 0ull, 0ull, selfD, selfU, st);
+    const unsigned long long mod = tile_passes(T, lane, g, 0ull, 0ull, selfD, selfU, st, *edges);
+    *modified = mod;
     if (mod == 0) return 0;
     __syncwarp();
     write_rows(P, T, g, mod, lane);
@@ -650,10 +664,148 @@ __device__ bool wait_edge_neighbours(const PairDev &P, int tx, int ty, int lane,
     return !__any_sync(FULL, gave_up);
 }
 
+constexpr unsigned long long QUEUE_LIMIT_NS = 2000000000ull;  // 2 s
+
+// Lane 0: the item of push p (pushes count from 0; the tickets after the
+// sweep's take them in order), once pushed; -1 if none will come (nothing
+// queued or being solved); -2 if a wait gave up (EPIC_ERR_TIMEOUT recorded)
+// or another warp recorded an error.
+__device__ int queue_wait(const BatchArgs &a, RunState *st, unsigned p) {
+    const unsigned cap = (unsigned)a.total_tiles;
+    const unsigned long long t0 = warp_ns();
+    for (;;) {
+        if (ld_acquire(&st->q_tail) > p) {
+            // pushed: the value follows the ticket
+            int *slot = a.relax_queue + p % cap;
+            for (;;) {
+                const int v = (int)ld_acquire(reinterpret_cast<const unsigned *>(slot));
+                if (v >= 0) {
+                    *(volatile int *)slot = -1;
+                    return v;
+                }
+                if (warp_ns() - t0 > QUEUE_LIMIT_NS) {
+                    set_status(st, EPIC_ERR_TIMEOUT);
+                    return -2;
+                }
+            }
+        }
+        // q_busy counts every pushed item until its solve and pushes are
+        // done, so when it reads 0 the tail read after it is final
+        if (ld_acquire(reinterpret_cast<const unsigned *>(&st->q_busy)) == 0u &&
+            ld_acquire(&st->q_tail) <= p)
+            return -1;
+        if (get_status(st) != 0) return -2;
+        if (warp_ns() - t0 > QUEUE_LIMIT_NS) {
+            set_status(st, EPIC_ERR_TIMEOUT);
+            return -2;
+        }
+        __nanosleep(256);
+    }
+}
+
+// Per-tile queue state (relax_queued): TILE_REQUESTED while the tile is
+// queued, or while a solve of it has been asked for during its running solve
+// (TILE_RUNNING), which then solves it again; 0 when idle.  So a tile is
+// never solved by two warps at once, and a change next door is never lost.
+constexpr int TILE_REQUESTED = 1, TILE_RUNNING = 2;
+
+// Ask for a solve of tile nt (flat index): pushed if it is idle, else marked
+// (queued already, or running: its warp solves it again).  Lane-local: called
+// by the lane that watches nt.  Returns false if the slot wait gave up.
+__device__ bool queue_push(const BatchArgs &a, RunState *st, int nt) {
+    if (atomicOr(&a.relax_queued[nt], TILE_REQUESTED) != 0) return true;
+    atomicAdd(&st->q_busy, 1);   // counted before it becomes visible
+    const unsigned cap = (unsigned)a.total_tiles;
+    const unsigned p = atomicAdd(&st->q_tail, 1u);
+    int *slot = a.relax_queue + p % cap;
+    // the slot's previous item (p - cap) may not have been taken yet
+    const unsigned long long t0 = warp_ns();
+    while (*(volatile int *)slot >= 0) {
+        if (warp_ns() - t0 > QUEUE_LIMIT_NS) {
+            set_status(st, EPIC_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    __threadfence();
+    *(volatile int *)slot = nt;
+    return true;
+}
+
+// After tile (tx, ty) of pair P changed (rows `mod`, bit r = tile row r of
+// rv; `edges` bit 0 / 1: column 0 / 63 changed in some row): lane k < 8
+// asks for a solve of neighbour k if the change can border on it.  The tile's keys are written and fenced
+// already.  Returns false in every lane if a push gave up.
+__device__ bool queue_neighbours(const BatchArgs &a, int pi, RunState *st, int tx, int ty,
+                                 int rv, unsigned long long mod, unsigned edges, int lane) {
+    const PairDev &P = a.pairs[pi];
+    bool ok = true;
+    if (lane < 8) {
+        const int dx = lane < 3 ? lane - 1 : lane < 5 ? 2 * lane - 7 : lane - 6;
+        const int dy = lane < 3 ? -1 : lane < 5 ? 0 : 1;
+        const int x = tx + dx, y = ty + dy;
+        // a neighbour's ring holds the tile's border next to it: the top row
+        // above, the bottom row below, column 0 (63) to the left (right),
+        // and the corner pixels diagonally (whose change implies both)
+        const bool rows = dy < 0 ? (mod & 2ull) != 0 : dy > 0 ? ((mod >> rv) & 1ull) != 0 : true;
+        const bool cols = dx < 0 ? (edges & 1u) != 0 : dx > 0 ? (edges & 2u) != 0 : true;
+        const bool near = rows && cols;
+        if (near && x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y) {
+            ok = queue_push(a, st, a.tile_base[pi] + y * P.tiles_x + x);
+        }
+    }
+    return !__any_sync(FULL, !ok);
+}
+
 __device__ __forceinline__ int take_tile(unsigned *dispenser, int lane) {
     int t = 0;
     if (lane == 0) t = (int)atomicAdd(dispenser, 1u);
     return __shfl_sync(FULL, t, 0);
+}
+
+// One queue item: tile t (flat index), solved (if `look`) and solved again
+// while a neighbour asked for it during the solve; then its completion is
+// counted.  Returns false when the warp must leave (a wait gave up, or the
+// run recorded an error).
+template <int MAXR>
+__device__ bool solve_item(const BatchArgs &a, RunState *st, WarpTile<MAXR> &T, int lane,
+                           unsigned &phase, int t, bool look, unsigned long long item_cap) {
+    const int pi = find_pair(a.tile_base, a.npairs, t);
+    const PairDev &P = a.pairs[pi];
+    const int lt = t - a.tile_base[pi];
+    const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
+    for (;;) {
+        // running, not requested: from here on a change next door asks for
+        // another solve.  A neighbour that found the tile queued or running
+        // wrote its keys (and fenced them) before its atomic, so they are
+        // visible after ours.
+        if (lane == 0) {
+            atomicExch(&a.relax_queued[t], TILE_RUNNING);
+            __threadfence();
+        }
+        __syncwarp();
+        if (look) {
+            unsigned long long mod = 0;
+            unsigned edges = 0;
+            const int r = resolve_tile(P, lt, tx, ty, T, lane, phase, st, 1, &mod, &edges);
+            if (r < 0) return false;
+            if (r > 0 && !queue_neighbours(a, pi, st, tx, ty, tile_geo(P, tx, ty, lane).rv, mod,
+                                           edges, lane))
+                return false;
+        }
+        int again = 0;
+        if (lane == 0) {
+            again = atomicCAS(&a.relax_queued[t], TILE_RUNNING, 0) != TILE_RUNNING;
+            atomicAdd(&st->q_items, 1u);
+        }
+        if (!__shfl_sync(FULL, again, 0)) break;
+        look = true;
+    }
+    if (lane == 0) {
+        __threadfence();   // this item's pushes before its completion
+        atomicSub(&st->q_busy, 1);
+        if (ld_acquire(&st->q_items) >= item_cap) set_status(st, EPIC_ERR_NOT_CONVERGED);
+    }
+    return get_status(st) == 0;
 }
 
 template <int MAXR>
@@ -698,66 +850,64 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
     }
     if (!grid_sync(st, nblocks)) return;
 
-    // phase 2.  A warp takes up to SCAN_CHUNK tiles at once (fewer counter
-    // atomics and stamp reads, and neighbouring tiles re-solved in turn see
-    // each other's results), but only while that leaves every warp several
-    // chunks of a pass to balance the load.
-    const int chunk = max(1, min(SCAN_CHUNK, a.total_tiles / (4 * (int)nblocks * RT_WARPS)));
-    for (int pass = 0;; ++pass) {
-        if (pass >= a.max_passes) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                set_status(st, EPIC_ERR_NOT_CONVERGED);
-                st->passes = pass;
-            }
-            return;
-        }
-        unsigned *cnt = &st->changed[pass % 3];
-        unsigned *disp = &st->work[pass % 3];
-        // tiles are handed out `chunk` at a time; quarter q of the warp
-        // (lanes 8q .. 8q + 7) reads the eight neighbour stamps of the
-        // chunk's tile q: a tile is looked at only if a neighbour was written
-        // since the previous pass began
-        for (int c = take_tile(disp, lane); c < (a.total_tiles + chunk - 1) / chunk;
-             c = take_tile(disp, lane)) {
+    // phase 2: a work queue of tiles whose ring may have changed.  Ticket
+    // h < T (the tile count) is tile h, the initial sweep; later tickets
+    // take the tiles pushed since, in order.  A tile whose keys change
+    // pushes the neighbours its changed rows border on (unless they are
+    // already queued), and is pushed again itself if a neighbour changes
+    // while it is being solved.  q_busy counts the items pushed (or of the
+    // sweep) that are not finished; a warp whose ticket has no item while
+    // q_busy is 0 knows that none will come, since only the solve of an
+    // unfinished item pushes.  So the phase needs no grid barrier: a front
+    // of changes runs on through the tiles as soon as each is solved.
+    const int Tt = a.total_tiles;
+    const unsigned long long item_cap = (unsigned long long)a.max_passes * (unsigned)Tt;
+    // the sweep hands out `chunk` consecutive tiles per ticket while that
+    // leaves every warp several tickets (fewer counter atomics, and a chunk's
+    // tiles solved in turn see each other's results)
+    const int chunk = max(1, min(SCAN_CHUNK, Tt / (4 * (int)nblocks * RT_WARPS)));
+    const unsigned n0 = (unsigned)((Tt + chunk - 1) / chunk);   // tickets of the sweep
+    for (;;) {
+        unsigned h = 0;
+        if (lane == 0) h = atomicAdd(&st->q_head, 1u);
+        h = __shfl_sync(FULL, h, 0);
+        if (h < n0) {
+            // the sweep: quarter q of the warp reads the eight neighbour stamps
+            // of the chunk's tile q; a tile whose neighbours were all left
+            // unreached is only counted
             const int q = lane >> 3, k = lane & 7;
-            const int t = c * chunk + q;
-            int pi = 0, lt = 0, tx = 0, ty = 0;
+            const int t = (int)h * chunk + q;
             bool nb = false;
-            if (q < chunk && t < a.total_tiles) {
-                pi = find_pair(a.tile_base, a.npairs, t);
+            if (q < chunk && t < Tt) {
+                const int pi = find_pair(a.tile_base, a.npairs, t);
                 const PairDev &P = a.pairs[pi];
-                lt = t - a.tile_base[pi];
-                tx = lt % P.tiles_x;
-                ty = lt / P.tiles_x;
+                const int lt = t - a.tile_base[pi];
+                const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
                 const int x = tx + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
                 const int y = ty + (k < 3 ? -1 : k < 5 ? 0 : 1);
                 nb = x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
-                     __ldcg(P.tile_stamp + y * P.tiles_x + x) >= pass;
+                     __ldcg(P.tile_stamp + y * P.tiles_x + x) >= 0;
             }
-            unsigned look = __ballot_sync(FULL, nb);
-            while (look) {
-                const int src = (__ffs(look) - 1) & ~7;   // first lane of that tile's quarter
-                look &= ~(0xFFu << src);
-                const int tpi = __shfl_sync(FULL, pi, src), tlt = __shfl_sync(FULL, lt, src);
-                const int ttx = __shfl_sync(FULL, tx, src), tty = __shfl_sync(FULL, ty, src);
-                const int r =
-                    resolve_tile(a.pairs[tpi], tlt, ttx, tty, T, lane, phase, st, pass + 1);
-                if (r < 0) return;
-                if (r > 0 && lane == 0) atomicAdd(cnt, 1u);
-            }
+            const unsigned look = __ballot_sync(FULL, nb);
+            for (int q2 = 0; q2 < chunk && (int)h * chunk + q2 < Tt; ++q2)
+                if (!solve_item(a, st, T, lane, phase, (int)h * chunk + q2,
+                                ((look >> (8 * q2)) & 0xFFu) != 0, item_cap))
+                    return;
+        } else {
+            // wait for the ticket's item, or for the end of the work
+            int got = -1;
+            if (lane == 0) got = queue_wait(a, st, h - n0);
+            got = __shfl_sync(FULL, got, 0);
+            if (got == -2) return;   // a wait gave up or another warp failed
+            if (got < 0) break;      // no item will come
+            if (!solve_item(a, st, T, lane, phase, got, true, item_cap)) return;
         }
-        if (!grid_sync(st, nblocks)) return;
-        const unsigned dirty = ld_acquire(cnt);
-        // the counters of pass - 1 (== pass + 2 mod 3) were last used before
-        // this barrier; clear them for pass + 2
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            st->changed[(pass + 2) % 3] = 0;
-            st->work[(pass + 2) % 3] = 0;
-        }
-        if (dirty == 0) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) st->passes = pass + 1;
-            return;
-        }
+    }
+    // every item is finished: report the re-solves as equivalent passes
+    if (lane == 0) {
+        const unsigned items = ld_acquire(&st->q_items);
+        st->passes = 1 + (int)(((unsigned long long)items - (unsigned)Tt + (unsigned)Tt - 1) /
+                               (unsigned)Tt);
     }
 }
 

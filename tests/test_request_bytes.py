@@ -7,7 +7,8 @@ second-lightest edge, its other end [N] each; CSR row offsets [N+1] and
 16-byte adjacency entries [2 cap]; models 2 x float4 [N]; fallback flags [N];
 K-NN lists idx/dist [N x Kc] and counts [N] (only when intermediates are
 kept); info int [4]; pruning buffers keep [N], float4 [N], int [N] (only when
-pruning); plus one int per match in the batch's K-NN retry list."""
+pruning); plus one int per match in the batch's K-NN retry list and two ints
+per relaxation tile (the relaxation's work queue and its queued flags)."""
 
 import pytest
 
@@ -33,7 +34,7 @@ def carve(H, W, N, K, tile=(64, 16), keep=False, prune=False, prune_K=25):
     regions += [16]
     if prune:
         regions += [4 * N, 16 * N, 4 * N]
-    return sum(_a(r) for r in regions) + 4 * N
+    return sum(_a(r) for r in regions) + 4 * N + 8 * T
 
 
 @pytest.mark.parametrize("H, W, N, K", [(436, 1024, 5000, 100), (375, 1242, 8000, 100),
