@@ -260,7 +260,9 @@ int epic_interp_get_pruning(epic_interp_t *h, int pair, int *keep,
                             int *kept_index, int *n_kept);
 
 /* Number of relaxation verification passes the last run needed for its
- * whole batch (waits for the stream). */
+ * whole batch (waits for the stream).  The warp-tile relaxation (schedule 2)
+ * has no passes: it reports its tile solves divided by the batch's tile
+ * count, rounded up, as equivalent passes. */
 int epic_interp_get_passes(epic_interp_t *h, int *passes);
 
 /* Distance unit of pair `pair` of the last run: its keys count distance in
