@@ -664,6 +664,35 @@ __device__ bool wait_edge_neighbours(const PairDev &P, int tx, int ty, int lane,
     return !__any_sync(FULL, gave_up);
 }
 
+// Waits until tile (tx, ty) and its eight neighbours (those inside the tile
+// grid) carry a stamp of this run (phase 1 has written them); lane k < 8
+// watches neighbour k, lane 8 the tile.  Then, for the sweep (`any_written`
+// not null), tells whether any neighbour was reached (stamp >= 0).  Gives up
+// after TMA_LIMIT_NS with EPIC_ERR_TIMEOUT (false in every lane).
+__device__ bool wait_tile_and_ring(const PairDev &P, int tx, int ty, int lane, RunState *st,
+                                   bool *any_written) {
+    bool gave_up = false, written = false;
+    if (lane < 9) {
+        const int x = lane == 8 ? tx : tx + (lane < 3 ? lane - 1 : lane < 5 ? 2 * lane - 7 : lane - 6);
+        const int y = lane == 8 ? ty : ty + (lane < 3 ? -1 : lane < 5 ? 0 : 1);
+        if (x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y) {
+            const unsigned *sp = reinterpret_cast<const unsigned *>(P.tile_stamp + y * P.tiles_x + x);
+            const unsigned long long t0 = warp_ns();
+            unsigned v;
+            while ((v = ld_acquire(sp)) == (unsigned)STAMP_PENDING) {
+                if (warp_ns() - t0 > TMA_LIMIT_NS) {
+                    set_status(st, EPIC_ERR_TIMEOUT);
+                    gave_up = true;
+                    break;
+                }
+            }
+            written = lane < 8 && (int)v >= 0;
+        }
+    }
+    if (any_written) *any_written = __any_sync(FULL, written);
+    return !__any_sync(FULL, gave_up);
+}
+
 constexpr unsigned long long QUEUE_LIMIT_NS = 2000000000ull;  // 2 s
 
 // Lane 0: the item of push p (pushes count from 0; the tickets after the
@@ -762,17 +791,22 @@ __device__ __forceinline__ int take_tile(unsigned *dispenser, int lane) {
     return __shfl_sync(FULL, t, 0);
 }
 
-// One queue item: tile t (flat index), solved (if `look`) and solved again
-// while a neighbour asked for it during the solve; then its completion is
-// counted.  Returns false when the warp must leave (a wait gave up, or the
+// One queue item: tile t (flat index; `sweep`: the item of the sweep),
+// solved and solved again while a neighbour asked for it during the solve;
+// then its completion is counted.  Returns false when the warp must leave (a wait gave up, or the
 // run recorded an error).
 template <int MAXR>
 __device__ bool solve_item(const BatchArgs &a, RunState *st, WarpTile<MAXR> &T, int lane,
-                           unsigned &phase, int t, bool look, unsigned long long item_cap) {
+                           unsigned &phase, int t, bool sweep, unsigned long long item_cap) {
     const int pi = find_pair(a.tile_base, a.npairs, t);
     const PairDev &P = a.pairs[pi];
     const int lt = t - a.tile_base[pi];
     const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
+    // phase 1 may still be writing the tile or its ring (no grid barrier
+    // divides the phases); the sweep skips a tile whose neighbours were all
+    // left unreached
+    bool look = true;
+    if (!wait_tile_and_ring(P, tx, ty, lane, st, sweep ? &look : nullptr)) return false;
     for (;;) {
         // running, not requested: from here on a change next door asks for
         // another solve.  A neighbour that found the tile queued or running
@@ -848,7 +882,6 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
         if (half && !wait_edge_neighbours(P, tx, ty, lane, st)) return;
         if (!fresh_tile(P, lt, tx, ty, T, lane, phase, st, half == 1)) return;
     }
-    if (!grid_sync(st, nblocks)) return;
 
     // phase 2: a work queue of tiles whose ring may have changed.  Ticket
     // h < T (the tile count) is tile h, the initial sweep; later tickets
@@ -872,26 +905,8 @@ __global__ void __launch_bounds__(RT_WARPS * 32) relax_kernel(const BatchArgs *_
         if (lane == 0) h = atomicAdd(&st->q_head, 1u);
         h = __shfl_sync(FULL, h, 0);
         if (h < n0) {
-            // the sweep: quarter q of the warp reads the eight neighbour stamps
-            // of the chunk's tile q; a tile whose neighbours were all left
-            // unreached is only counted
-            const int q = lane >> 3, k = lane & 7;
-            const int t = (int)h * chunk + q;
-            bool nb = false;
-            if (q < chunk && t < Tt) {
-                const int pi = find_pair(a.tile_base, a.npairs, t);
-                const PairDev &P = a.pairs[pi];
-                const int lt = t - a.tile_base[pi];
-                const int tx = lt % P.tiles_x, ty = lt / P.tiles_x;
-                const int x = tx + (k < 3 ? k - 1 : k < 5 ? 2 * k - 7 : k - 6);
-                const int y = ty + (k < 3 ? -1 : k < 5 ? 0 : 1);
-                nb = x >= 0 && x < P.tiles_x && y >= 0 && y < P.tiles_y &&
-                     __ldcg(P.tile_stamp + y * P.tiles_x + x) >= 0;
-            }
-            const unsigned look = __ballot_sync(FULL, nb);
-            for (int q2 = 0; q2 < chunk && (int)h * chunk + q2 < Tt; ++q2)
-                if (!solve_item(a, st, T, lane, phase, (int)h * chunk + q2,
-                                ((look >> (8 * q2)) & 0xFFu) != 0, item_cap))
+            for (int q = 0; q < chunk && (int)h * chunk + q < Tt; ++q)
+                if (!solve_item(a, st, T, lane, phase, (int)h * chunk + q, true, item_cap))
                     return;
         } else {
             // wait for the ticket's item, or for the end of the work
