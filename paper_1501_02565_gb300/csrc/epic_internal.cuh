@@ -234,8 +234,9 @@ struct BatchArgs {
     int *wl_queued;          // [total_tiles] last pass + 1 a tile was queued for (0 = never)
     int max_degree;
     int knn_hs, knn_fs, knn_kmax;  // main-pass K-NN table sizes per warp, and K bound
-    int *relax_queue;      // [total_tiles] warp-tile relaxation work queue (-1 = empty slot)
-    int *relax_queued;     // [total_tiles] 1 while a tile is queued or not yet taken
+    int *relax_queue;      // [total_tiles] warp-tile relaxation work queue (-1 = empty slot);
+                           // null for runs of the apron-tile relaxation
+    int *relax_queued;     // [total_tiles] per-tile queue state (see k_relax.cu)
     int *knn_retry_list;   // global match indices to search again; holds every match of
                            // the batch (a match is queued at most once per pass)
     int max_passes;

@@ -117,8 +117,13 @@ __device__ void seed_reach(const PairDev &P, int T) {
 // (four pixels a thread), and a warp's running maximum goes out with one
 // atomic whenever its pair changes.
 __device__ void cost_max(const BatchArgs &a) {
-    const int per = (a.total_chunks + gridDim.x - 1) / gridDim.x;
-    const int c0 = blockIdx.x * per, c1 = min(a.total_chunks, c0 + per);
+    // the CTAs that binned a pair's seeds take no part when enough others
+    // are left (they would finish last)
+    const int first = a.npairs < (int)gridDim.x / 2 ? a.npairs : 0;
+    if ((int)blockIdx.x < first) return;
+    const int nb = (int)gridDim.x - first, b = (int)blockIdx.x - first;
+    const int per = (a.total_chunks + nb - 1) / nb;
+    const int c0 = b * per, c1 = min(a.total_chunks, c0 + per);
     const int grp = threadIdx.x >> 8, gt = threadIdx.x & 255;   // warp-uniform group
     int pi = -1;
     unsigned mx = 0;
@@ -169,9 +174,11 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
         st->q_head = st->q_tail = st->q_items = 0;
         st->q_busy = a.total_tiles;   // the initial sweep's items
     }
-    // the relaxation's work queue: empty slots; every tile counts as queued
-    // until the initial sweep of phase 2 takes it
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.total_tiles;
+    // the warp-tile relaxation's work queue: empty slots; every tile counts
+    // as queued until the sweep of phase 2 takes it.  Runs of the apron-tile
+    // relaxation (the exact variant's, the no-allocation entry point's) have
+    // no queue.
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; a.relax_queue && i < a.total_tiles;
          i += gridDim.x * blockDim.x) {
         a.relax_queue[i] = -1;
         a.relax_queued[i] = 1;
