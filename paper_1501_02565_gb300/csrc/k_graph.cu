@@ -174,31 +174,43 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
         __syncthreads();
         if (threadIdx.x == 0) s_tab_pair = s_pair;
         const PairDev &P = a.pairs[s_pair];
-        const int tx = s_local % P.tiles_x, ty = s_local / P.tiles_x;
-        const int RH = edge_stack(P.tile_h) * P.tile_h;   // rows of the item
-        const int npx = P.tile_w * RH;
-        const int W = P.W, H = P.H;
-        const int SC = P.tile_w + 2, SR = RH + 1;   // staged columns x0-1 .. x0+tw
+        // the pair's fields in registers (the table atomics below would
+        // otherwise make every use a reload)
+        const int TW = P.tile_w, TH = P.tile_h, TX = P.tiles_x, W = P.W, H = P.H;
+        const unsigned NM = (unsigned)P.N;
+        const pkey_t *keys = P.keys;
+        const float *C = P.C;
+        const int tx = s_local % TX, ty = s_local / TX;
+        const int RH = edge_stack(TH) * TH;   // rows of the item
+        const int npx = TW * RH;
+        const int SC = TW + 2, SR = RH + 1;   // staged columns x0-1 .. x0+tw
         const int us = unit_shift(P);                      // the pair's distance unit
+        const float unit = ldexpf(ONE_PER_UNIT, us);       // the distance of one unit
         pkey_t *skey = reinterpret_cast<pkey_t *>(edge_smem);
         unsigned *sh = reinterpret_cast<unsigned *>(skey + SC * SR);
         {
-            const int x0 = tx * P.tile_w - 1, y0 = ty * P.tile_h;
+            // warp w stages rows w, w + 8, ...; its lanes take consecutive columns
+            const int x0 = tx * TW - 1, y0 = ty * TH;
+            const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
             bool bad = false;
-            for (int j = threadIdx.x; j < SC * SR; j += blockDim.x) {
-                const int r = j / SC, c = j - r * SC;
-                const int gx = x0 + c, gy = y0 + r;
-                const bool in = gx >= 0 && gx < W && gy < H;
-                const size_t q = (size_t)gy * W + gx;
-                skey[j] = in ? __ldg(P.keys + q) : KEY_INF;
-                sh[j] = in ? half_cost_s(__ldg(P.C + q), us, &bad) : 0u;
+            for (int r = wid; r < SR; r += nw) {
+                const int gy = y0 + r;
+                for (int c = lane; c < SC; c += 32) {
+                    const int gx = x0 + c;
+                    const bool in = gx >= 0 && gx < W && gy < H;
+                    const size_t q = (size_t)gy * W + gx;
+                    skey[r * SC + c] = in ? __ldg(keys + q) : KEY_INF;
+                    sh[r * SC + c] = in ? half_cost_s(__ldg(C + q), us, &bad) : 0u;
+                }
             }
         }
         __syncthreads();
+        // tile widths are powers of two for the warp tiles (64): a shift
+        const int tws = (TW & (TW - 1)) == 0 ? __ffs(TW) - 1 : -1;
         for (int i0 = 0; i0 < npx; i0 += blockDim.x) {  // warp-uniform trip count
             const int i = i0 + threadIdx.x;
-            const int ly = i / P.tile_w, lx = i - ly * P.tile_w;
-            const int x = tx * P.tile_w + lx, y = ty * P.tile_h + ly;
+            const int ly = tws >= 0 ? i >> tws : i / TW, lx = i - ly * TW;
+            const int x = tx * TW + lx, y = ty * TH + ly;
             const bool act = i < npx && x < W && y < H;
             pkey_t kp = 0;
             unsigned hp = 0;
@@ -225,7 +237,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                     const pkey_t kq = skey[sq];
                     const unsigned lp = key_label(kp), lq = key_label(kq);
                     have = lp != lq;
-                    if (have && (lp >= (unsigned)P.N || lq >= (unsigned)P.N ||
+                    if (have && (lp >= NM || lq >= NM ||
                                  !key_reached(kp) || !key_reached(kq))) {
                         // an unreached pixel (or a distance beyond the fixed-
                         // point range): the cost map was not in [0, C_MAX)
@@ -239,7 +251,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) edges_kernel(const BatchArgs *__
                                                            : step_axis(hp, hq);
                         // exact sum in fixed point, rounded once to float32
                         const unsigned long long units = key_dunits(kp) + stp + key_dunits(kq);
-                        const float w = units_dist(units, us);
+                        const float w = __fmul_rn(__ull2float_rn(units), unit);   // units_dist
                         k = lp < lq ? (((pkey_t)lp << 32) | lq) : (((pkey_t)lq << 32) | lp);
                         wb = __float_as_uint(w);
                     }
