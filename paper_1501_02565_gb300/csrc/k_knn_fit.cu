@@ -624,25 +624,32 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 4)
 
 }  // namespace
 
-// Main-pass tables: ~3.84 K node slots (the searches here touch about 1.5 K
-// nodes) and ~1.92 K frontier entries, so that 8 warps' tables fit four CTAs
-// on an SM up to K ~ 100.  For larger K the tables shrink to what four CTAs
-// leave (a frontier of at least 1.4 K entries and a node table twice that:
-// the largest frontier seen on these graphs is ~1.2 K); a search that
-// outgrows them is run again with large tables.
+// Main-pass tables: ~4.48 K node slots (the searches here touch about 1.5 K
+// nodes; a sparse table keeps the probe sequences short) and ~1.6 K frontier
+// entries (the largest frontier seen on these graphs is ~1.2 K), so that 8
+// warps' tables fit four CTAs on an SM up to K ~ 100.  For larger K the
+// tables shrink to what four CTAs leave: 7/8 of an equal split to the
+// frontier (at least 1.4 K entries), the rest to the node table; beyond
+// that (K above ~160) they keep the proportions ~3.84 K and ~1.92 K at fewer
+// CTAs per SM.  A search that outgrows them is run again with large tables.
 void knn_table_sizes(int max_K, const LaunchCfg &lc, int *hs, int *fs) {
     const int k = max_K > 1 ? max_K : 1;
-    *hs = std::max(64, (k * 384 / 100 + 31) / 32 * 32);
-    *fs = std::max(64, (k * 192 / 100 + 31) / 32 * 32);
+    *hs = std::max(64, (k * 448 / 100 + 31) / 32 * 32);
+    *fs = std::max(64, (k * 160 / 100 + 31) / 32 * 32);
     if (lc.smem_per_sm <= 0) return;
     const long long per_warp = ((long long)lc.smem_per_sm / 4 - lc.smem_reserved) / KNN_WARPS;
     const long long fixed = (long long)knn_fixed_bytes(k);
     if ((long long)*fs * 16 + (long long)*hs * 8 + fixed <= per_warp) return;
     const long long f = (per_warp - fixed) / 32;   // 16 B per entry + 2 slots of 8 B
     if (f * 10 >= 14LL * k) {
-        *fs = (int)f;
-        *hs = 2 * (int)f;
+        *fs = (int)(f * 7 / 8);
+        *hs = (int)((per_warp - fixed - (long long)*fs * 16) / 8);
+        return;
     }
+    // fewer CTAs per SM: tables in proportion to K (~3.84 K slots, ~1.92 K
+    // entries), which stay below the retry pass's up to EPIC_MAX_K
+    *hs = std::max(64, (k * 384 / 100 + 31) / 32 * 32);
+    *fs = std::max(64, (k * 192 / 100 + 31) / 32 * 32);
 }
 
 // Retry-pass tables: the largest power-of-two node table (and a frontier
