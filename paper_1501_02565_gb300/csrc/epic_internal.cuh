@@ -204,7 +204,7 @@ struct RunState {
     int status;            // first device error (epic_status_t), 0 = OK
     int passes;            // relaxation verification passes of the last run
     unsigned changed[3];   // per-pass dirty-tile counters (rotating)
-    unsigned work[5];      // relaxation tile dispensers: passes (rotating), phase 1 (two halves)
+    unsigned work[4];      // relaxation tile dispensers: passes (rotating), phase 1
     unsigned knn_next;     // K-NN match dispenser
     unsigned knn_overflow; // matches whose search outgrew the small tables
     unsigned knn_retry;    // dispenser of the retry pass over those matches

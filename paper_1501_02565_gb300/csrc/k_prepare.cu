@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const BatchArgs *__restri
         // which is stream-ordered after this one.
         st->passes = 0;
         st->changed[0] = st->changed[1] = st->changed[2] = 0;
-        st->work[0] = st->work[1] = st->work[2] = st->work[3] = st->work[4] = 0;
+        st->work[0] = st->work[1] = st->work[2] = st->work[3] = 0;
         st->knn_next = 0;
         st->knn_overflow = 0;
         st->knn_retry = 0;
