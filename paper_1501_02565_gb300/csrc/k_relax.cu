@@ -41,6 +41,10 @@
 //            step improves any key anywhere; no grid barrier divides it, so
 //            a front of changes moves on through the tiles as soon as each
 //            one is solved.
+// Nor does a grid barrier divide the phases or the halves: a second-half
+// tile waits for its four edge neighbours' stamps, and a phase-2 solve for
+// the stamps of the tile and its eight neighbours (every wait bounded; the
+// prepare kernel marks the tiles pending at the start of a run).
 #include "epic_internal.cuh"
 
 namespace epic {
